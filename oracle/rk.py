@@ -17,7 +17,9 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
   with delta = 0.8, dmax = 2, dmin = 0.01, q = 4 the embedded order.  err <= 1 accepts;
   otherwise the step is redone with h_new.  dmax = 1 for the step that follows a rejection.
   Readings (listed in the design notes): the last step is clipped to end exactly at t_end
-  and h is the clipped step; a non-finite err rejects with factor dmin; err = 0 takes dmax.
+  and h is the clipped step (a step h >= (t_end - t)(1 - 1e-10) counts as the last one, so
+  fixed steps that divide the interval end on t_end despite rounding of t); a non-finite err
+  rejects with factor dmin; err = 0 takes dmax.
 """
 from __future__ import annotations
 
@@ -210,7 +212,8 @@ def integrate(f: Callable, u0: np.ndarray, t0: float, t_end: float, method: str,
     steps = 0
     while t < t_end and steps < max_steps:
         steps += 1
-        clipped = h >= t_end - t
+        # last step: land exactly on t_end (also when h falls short of it by rounding only)
+        clipped = h >= (t_end - t) * (1.0 - 1e-10)
         h_step = t_end - t if clipped else h
         if h_step < 1e-12 * max(1.0, abs(t)):
             res.status = "step_underflow"
