@@ -1,0 +1,164 @@
+/*
+ * dns.h -- C ABI of libdns: a GB300 (sm_103a) implementation of the Fourier pseudo-spectral
+ * incompressible Navier-Stokes right-hand side in rotational form, integrated with the
+ * Bogacki-Shampine 5(4) pair under embedded local-error step control, or with classical RK4.
+ *
+ * Method: Ketcheson, Mortensen, Parsani & Schilling, "More efficient time integration for
+ * Fourier pseudo-spectral DNS of incompressible turbulence", arXiv:1810.10197.
+ *
+ * Conventions used by every call
+ *   - Grid nx x ny x nz (each even, from the supported set below) on [0,lx) x [0,ly) x [0,lz);
+ *     wavenumber kappa_a = 2 pi m / l_a for integer mode number m.
+ *   - A spectral field is the half spectrum of a real 3D DFT taken along z:
+ *     complex128 (interleaved re, im doubles), layout [3][nx][ny][nz/2+1], component-major,
+ *     kz contiguous; kx, ky in FFT order (0..n/2-1, -n/2..-1).
+ *   - Forward DFT unnormalised: uhat_k = sum_x u(x) exp(-i kappa.x); the inverse carries
+ *     1/(nx ny nz) (the convention behind E = ||uhat||^2 / (2 N^6), Section 3.1).
+ *   - 2/3-rule dealiasing: a mode is kept iff |m_a| <= K_a = floor((n_a - 1)/3) on every axis.
+ *     Fields passed in are truncated to that box; fields returned are zero outside it.
+ *
+ * Ownership and errors
+ *   - Every pointer argument stays owned by the caller; the library copies in and out and
+ *     never frees or retains caller memory past the call.  Device pointers must come from
+ *     cudaMalloc (e.g. a torch CUDA tensor's data_ptr()) on the context's device; host
+ *     pointers may be pageable or pinned (pinned is faster).
+ *   - Calls return a dns_status; no exception or longjmp crosses the ABI.  DNS_ERR_ARG leaves
+ *     the context usable.  A CUDA error or a device-side failure makes the context "failed":
+ *     every later call except dns_last_error/dns_destroy returns DNS_ERR_STATE.
+ *   - The context owns all its device work buffers (allocated in dns_create).
+ *   - Work is enqueued on the context's stream (dns_set_stream; default: the legacy default
+ *     stream).  Calls documented as "synchronous" wait for that stream before returning.
+ *   - A context is not thread-safe: use one context per host thread.
+ *
+ * Supported sizes: nx, ny in {8,12,16,24,32,48,64,96,128,256,512};
+ *                  nz in {8,12,16,24,32,48,64,96,128,256,512}.
+ */
+#ifndef DNS_H
+#define DNS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dns_ctx dns_ctx;
+
+typedef enum {
+    DNS_OK = 0,
+    DNS_ERR_ARG = 1,             /* invalid argument; context unchanged                     */
+    DNS_ERR_CUDA = 2,            /* a CUDA call failed; context is failed                    */
+    DNS_ERR_OOM = 3,             /* device allocation failed in dns_create                   */
+    DNS_ERR_NONFINITE = 4,       /* the error estimate stayed non-finite through max rejects */
+    DNS_ERR_STEP_UNDERFLOW = 5,  /* step size fell below 1e-12 max(1,|t|)                   */
+    DNS_ERR_MAX_REJECTS = 6,     /* more than max_rejects rejections in a row               */
+    DNS_ERR_TIMEOUT = 7,         /* reserved: a bounded device wait ran out                  */
+    DNS_ERR_STATE = 8,           /* context failed earlier, or no state was set             */
+    DNS_ERR_UNSUPPORTED = 9      /* grid size outside the supported set                     */
+} dns_status;
+
+/* Time integrators of Section 2.2.  BS5 is the Bogacki-Shampine 5(4) pair of Appendix A with
+ * the b-hat error estimator; BS5_FIXED takes fixed steps and still evaluates the error norm. */
+typedef enum { DNS_RK4 = 0, DNS_BS5_FIXED = 1, DNS_BS5_ADAPTIVE = 2 } dns_method;
+
+/* DNS_FP64: every step in double precision.  DNS_FP32_MIXED: the transforms and the
+ * nonlinear term in single precision; state, stage sums, projection, viscous term, error
+ * norm and step control in double precision. */
+typedef enum { DNS_FP64 = 0, DNS_FP32_MIXED = 1 } dns_precision;
+
+/* Forcing (Section 3.3.1 injects energy into 0 < |kappa| <= kf).  kind 0: none.  kind 1:
+ * constant power as a right-hand-side term F_k = power/(2 E_f) uhat_k on 0 < |kappa| <= kf,
+ * E_f the band energy, so that dE/dt gains exactly `power`. */
+typedef struct {
+    int kind;
+    double kf;
+    double power;
+} dns_forcing;
+
+typedef struct {
+    int nx, ny, nz;
+    double lx, ly, lz;           /* domain lengths; 0 means 2 pi                             */
+    double nu;                   /* kinematic viscosity, 1/Re                                 */
+    int precision;               /* dns_precision                                             */
+    dns_forcing forcing;
+} dns_config;
+
+/* Outcome of the last attempt and running counters since the last dns_set_state. */
+typedef struct {
+    int accepted;                /* last attempt accepted                                     */
+    int status;                  /* device status word (a dns_status value)                   */
+    double err;                  /* last embedded error norm (0 for RK4)                      */
+    double h_used;               /* step size of the last attempt (after clipping to t_end)   */
+    double h_next;               /* controller's proposal for the next attempt                */
+    double t;                    /* current time of the state                                 */
+    long long n_rhs;             /* right-hand-side evaluations                               */
+    long long n_acc, n_rej;      /* accepted / rejected attempts                              */
+} dns_step_info;
+
+/* Create a context for an nx x ny x nz grid on the current CUDA device (Eq. ufdef with
+ * viscosity nu, optional forcing, precision a dns_precision).  Domain [0, 2 pi)^3. */
+dns_status dns_create(int nx, int ny, int nz, double nu, const dns_forcing* forcing,
+                      int precision, dns_ctx** out);
+/* As dns_create, with domain lengths from cfg. */
+dns_status dns_create_ex(const dns_config* cfg, dns_ctx** out);
+void dns_destroy(dns_ctx* ctx);
+/* Message for the last non-OK status of this context ("" if none).  Valid until next call. */
+const char* dns_last_error(const dns_ctx* ctx);
+
+/* Stream for all later work (a cudaStream_t as void*; NULL = legacy default stream). */
+dns_status dns_set_stream(dns_ctx* ctx, void* stream);
+
+/* Load the state uhat (layout above) at time t; where = 0: device pointer, 1: host pointer.
+ * Truncates to the 2/3 box, resets the step counters and the controller (next h comes from
+ * dns_integrate's h0).  Asynchronous for device input, synchronous for host input. */
+dns_status dns_set_state(dns_ctx* ctx, const void* uhat, int where, double t);
+/* Write the current state (zero outside the 2/3 box); where as above.  Synchronous. */
+dns_status dns_get_state(dns_ctx* ctx, void* uhat, int where);
+
+/* Eq. (ufdef), once: f = P(kappa) [u x omega]^ - nu |kappa|^2 uhat (+ forcing), evaluated
+ * pseudo-spectrally with 2/3 dealiasing (Section 2.1).  uhat and f are device pointers in the
+ * layout above (may not alias).  Asynchronous on the context's stream. */
+dns_status dns_rhs(dns_ctx* ctx, const void* uhat_dev, void* f_dev);
+
+/* One attempted step from the current state with step size h (clipped to t_end if t_end >
+ * t), embedded error norm with (rtol, atol) and the controller of Section 2.2.1 (adaptive
+ * methods accept iff err <= 1 and propose h_new).  Synchronous; fills info if non-NULL. */
+dns_status dns_step(dns_ctx* ctx, int method, double h, double rtol, double atol,
+                    double t_end, dns_step_info* info);
+
+/* Integrate from the current time to t_end.  h0 > 0 sets the step (fixed methods) or the
+ * first proposal (adaptive); h0 <= 0 keeps the controller's current proposal.  The last step
+ * is clipped to land on t_end.  max_rejects consecutive rejections (default 30 when <= 0)
+ * end the run with DNS_ERR_MAX_REJECTS (DNS_ERR_NONFINITE if err was not finite).
+ * Synchronous; fills info if non-NULL. */
+dns_status dns_integrate(dns_ctx* ctx, double t_end, int method, double rtol, double atol,
+                         double h0, int max_rejects, dns_step_info* info);
+
+/* Enqueue exactly n step attempts toward t_end without waiting (for timing loops); attempts
+ * after t_end is reached do nothing on the device.  Read the outcome with dns_get_info. */
+dns_status dns_enqueue_attempts(dns_ctx* ctx, int n, int method, double rtol, double atol,
+                                double t_end, double h0);
+/* Synchronous read of the controller state and counters. */
+dns_status dns_get_info(dns_ctx* ctx, dns_step_info* info);
+
+/* Kinetic energy E, enstrophy Omega and dissipation rate eps = -dE/dt of the current state
+ * (Section 3.1, half-spectrum weights).  eps uses one right-hand-side evaluation.
+ * Synchronous. */
+dns_status dns_diagnostics(dns_ctx* ctx, double* E, double* Omega, double* eps);
+
+/* Per-kernel timing with CUDA events on the context's stream.  enable != 0 starts recording
+ * (and clears earlier records).  dns_profile_get returns, for kernel index i < count, its
+ * name, number of launches and summed duration in ms (synchronous). */
+dns_status dns_profile_enable(dns_ctx* ctx, int enable);
+int dns_profile_count(dns_ctx* ctx);
+dns_status dns_profile_get(dns_ctx* ctx, int i, const char** name, long long* launches,
+                           double* total_ms);
+
+/* Grid facts: retained cut-offs K[3] and the number of device bytes the context holds. */
+dns_status dns_query(const dns_ctx* ctx, int* K3, size_t* device_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DNS_H */

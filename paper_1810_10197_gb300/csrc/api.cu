@@ -1,0 +1,602 @@
+// C ABI of libdns (include/dns.h): context, device buffers and the orchestration of one
+// right-hand-side evaluation (five passes) and of one Runge-Kutta attempt (stage sums, right-
+// hand sides, error norm, controller), all enqueued on the context's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dns.h"
+#include "common.cuh"
+#include "passes.cuh"
+#include "stepper.cuh"
+
+using namespace dns;
+
+namespace {
+
+struct Frac { long long p, q; };
+
+// Bogacki-Shampine 5(4) pair, Appendix A of arXiv:1810.10197 (rows 2..8 of A, b, b-hat).
+const Frac kBS5A[8][7] = {
+    {},
+    {{1, 6}},
+    {{2, 27}, {4, 27}},
+    {{183, 1372}, {-162, 343}, {1053, 1372}},
+    {{68, 297}, {-4, 11}, {42, 143}, {1960, 3861}},
+    {{597, 22528}, {81, 352}, {63099, 585728}, {58653, 366080}, {4617, 20480}},
+    {{174197, 959244}, {-30942, 79937}, {8152137, 19744439}, {666106, 1039181}, {-29421, 29068},
+     {482048, 414219}},
+    {{587, 8064}, {0, 1}, {4440339, 15491840}, {24353, 124800}, {387, 44800}, {2152, 5985},
+     {7267, 94080}},
+};
+const Frac kBS5B[8] = {{587, 8064}, {0, 1}, {4440339, 15491840}, {24353, 124800},
+                       {387, 44800}, {2152, 5985}, {7267, 94080}, {0, 1}};
+const Frac kBS5Bh[8] = {{2479, 34992}, {0, 1}, {123, 416}, {612941, 3411720},
+                        {43, 1440}, {2272, 6561}, {79937, 1113912}, {3293, 556956}};
+// Classical RK4.
+const Frac kRK4A[4][3] = {{}, {{1, 2}}, {{0, 1}, {1, 2}}, {{0, 1}, {0, 1}, {1, 1}}};
+const Frac kRK4B[4] = {{1, 6}, {1, 3}, {1, 3}, {1, 6}};
+
+long long gcdll(long long a, long long b) {
+  a = a < 0 ? -a : a; b = b < 0 ? -b : b;
+  while (b) { long long t = a % b; a = b; b = t; }
+  return a ? a : 1;
+}
+// exact difference of two fractions, then one correctly rounded division
+double frac_diff(Frac a, Frac b) {
+  long long p = a.p * b.q - b.p * a.q, q = a.q * b.q, g = gcdll(p, q);
+  return (double)(p / g) / (double)(q / g);
+}
+double frac_val(Frac a) { return (double)a.p / (double)a.q; }
+
+bool supported(int n) {
+  switch (n) {
+    case 8: case 12: case 16: case 24: case 32: case 48: case 64: case 96: case 128: case 256:
+    case 512: return true;
+  }
+  return false;
+}
+
+const char* kPassNames[] = {"begin_attempt", "stage_sum", "p1_x_inverse_curl", "p2_y_inverse",
+                            "p3_z_c2r_cross_r2c", "p4_y_forward", "p5_x_forward_project",
+                            "err_norm_partials", "controller", "forcing_coef"};
+enum ProfId { PR_BEGIN = 0, PR_STAGE, PR_P1, PR_P2, PR_P3, PR_P4, PR_P5, PR_ERR, PR_CTRL, PR_FORCE, PR_N };
+
+struct ProfRec { int id; cudaEvent_t a, b; };
+
+}  // namespace
+
+struct dns_ctx {
+  Geom g{};
+  int precision = 0;
+  double nu = 0;
+  dns_forcing forcing{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  double2* uu[2] = {nullptr, nullptr};
+  double2* kk[2] = {nullptr, nullptr};
+  double2* kfix[9] = {};
+  double2* ystage = nullptr;
+  double2* rhs_in = nullptr;
+  double2* rhs_out = nullptr;
+  double2* full_stage = nullptr;   // half-spectrum staging for host copies (lazy)
+  void* bufA = nullptr;
+  void* bufB = nullptr;
+  void* tw[3] = {nullptr, nullptr, nullptr};
+  DnsCtrl* ctrl = nullptr;         // integrator
+  DnsCtrl* ctrl_rhs = nullptr;     // plain right-hand side
+  double* partials = nullptr;
+  DnsCtrl* host_ctrl = nullptr;    // pinned mirror
+  double* host_partials = nullptr; // pinned
+  size_t device_bytes = 0;
+  bool failed = false;
+  bool has_state = false;
+  std::string err;
+  bool prof = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+};
+
+namespace {
+
+dns_status fail(dns_ctx* c, dns_status s, const std::string& msg) {
+  if (c) {
+    c->err = msg;
+    if (s == DNS_ERR_CUDA || s == DNS_ERR_OOM) c->failed = true;
+  }
+  return s;
+}
+dns_status cuda_fail(dns_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, DNS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define CK(call, what)                                      \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, what);   \
+  } while (0)
+
+cudaEvent_t pool_event(dns_ctx* c) {
+  if (c->pool_used == c->pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->pool.push_back(e);
+  }
+  return c->pool[c->pool_used++];
+}
+
+// run `launch` bracketed by profiling events when enabled
+template <typename F>
+cudaError_t timed(dns_ctx* c, int id, F&& launch) {
+  if (!c->prof) return launch();
+  cudaEvent_t a = pool_event(c), b = pool_event(c);
+  if (!a || !b) return cudaErrorMemoryAllocation;
+  cudaEventRecord(a, c->stream);
+  cudaError_t e = launch();
+  cudaEventRecord(b, c->stream);
+  c->recs.push_back({id, a, b});
+  return e;
+}
+
+dns_status alloc(dns_ctx* c, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, DNS_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  }
+  c->device_bytes += bytes;
+  return DNS_OK;
+}
+
+// twiddle table exp(-2 pi i m / n), m < n, rounded once from long double
+dns_status make_twiddles(dns_ctx* c, int n, void** out) {
+  const bool f32 = c->precision == DNS_FP32_MIXED;
+  const size_t esz = f32 ? sizeof(float2) : sizeof(double2);
+  std::vector<unsigned char> host(n * esz);
+  const long double twopi = 6.283185307179586476925286766559005768L;
+  for (int m = 0; m < n; ++m) {
+    const long double ang = twopi * (long double)m / (long double)n;
+    const long double cr = cosl(ang), ci = -sinl(ang);
+    if (f32) reinterpret_cast<float2*>(host.data())[m] = make_float2((float)cr, (float)ci);
+    else reinterpret_cast<double2*>(host.data())[m] = make_double2((double)cr, (double)ci);
+  }
+  dns_status s = alloc(c, out, n * esz);
+  if (s != DNS_OK) return s;
+  CK(cudaMemcpy(*out, host.data(), n * esz, cudaMemcpyHostToDevice), "twiddle upload");
+  return DNS_OK;
+}
+
+cudaError_t pass(dns_ctx* c, int which, const PassArgs& a) {
+  return c->precision == DNS_FP32_MIXED ? launch_pass<float>(which, a, c->stream)
+                                        : launch_pass<double>(which, a, c->stream);
+}
+
+// One evaluation of Eq. (ufdef) on the stage input in `yslot`, result to `kslot`.
+dns_status enqueue_rhs(dns_ctx* c, DnsCtrl* ctrl, int yslot, int kslot, int gate_k1) {
+  if (c->forcing.kind == 1) {
+    CK(timed(c, PR_FORCE, [&] {
+         return launch_forcing_coef(c->g, ctrl, yslot, c->forcing.kf, c->forcing.power, gate_k1, c->stream);
+       }), "forcing coefficient");
+  }
+  PassArgs a{};
+  a.g = c->g;
+  a.ctrl = ctrl;
+  a.gate_k1 = gate_k1;
+  a.yslot = yslot;
+  a.kslot = kslot;
+  a.nu = c->nu;
+  a.kf2 = c->forcing.kind == 1 ? c->forcing.kf * c->forcing.kf : 0.0;
+  a.out = c->bufA; a.tw = c->tw[0];
+  CK(timed(c, PR_P1, [&] { return pass(c, 1, a); }), "pass P1");
+  a.in = c->bufA; a.out = c->bufB; a.tw = c->tw[1];
+  CK(timed(c, PR_P2, [&] { return pass(c, 2, a); }), "pass P2");
+  a.in = c->bufB; a.out = c->bufA; a.tw = c->tw[2];
+  CK(timed(c, PR_P3, [&] { return pass(c, 3, a); }), "pass P3");
+  a.in = c->bufA; a.out = c->bufB; a.tw = c->tw[1];
+  CK(timed(c, PR_P4, [&] { return pass(c, 4, a); }), "pass P4");
+  a.in = c->bufB; a.out = nullptr; a.tw = c->tw[0];
+  CK(timed(c, PR_P5, [&] { return pass(c, 5, a); }), "pass P5");
+  return DNS_OK;
+}
+
+dns_status enqueue_stage(dns_ctx* c, int nterms, const int* kslots, const double* coef, int yslot) {
+  StageArgs s{};
+  s.ctrl = c->ctrl;
+  s.gate_k1 = 0;
+  s.nterms = nterms;
+  for (int j = 0; j < nterms; ++j) { s.kslot[j] = kslots[j]; s.coef[j] = coef[j]; }
+  s.uslot = SLOT_U;
+  s.yslot = yslot;
+  s.n2 = 3 * c->g.M;
+  CK(timed(c, PR_STAGE, [&] { return launch_stage_sum(s, c->stream); }), "stage sum");
+  return DNS_OK;
+}
+
+// One attempted step (Section 2.2): all stages, error norm and the controller decision.
+dns_status enqueue_attempt(dns_ctx* c, int method) {
+  dns_status st;
+  CK(timed(c, PR_BEGIN, [&] { return launch_begin_attempt(c->ctrl, method, c->stream); }), "begin");
+  if (method == DNS_RK4) {
+    if ((st = enqueue_rhs(c, c->ctrl, SLOT_U, SLOT_K1, 0)) != DNS_OK) return st;
+    for (int i = 1; i < 4; ++i) {
+      int ks[3]; double cf[3]; int n = 0;
+      for (int j = 0; j < i; ++j)
+        if (kRK4A[i][j].p != 0) { ks[n] = SLOT_K1 + j; cf[n] = frac_val(kRK4A[i][j]); ++n; }
+      if ((st = enqueue_stage(c, n, ks, cf, SLOT_Y)) != DNS_OK) return st;
+      if ((st = enqueue_rhs(c, c->ctrl, SLOT_Y, SLOT_K1 + i, 0)) != DNS_OK) return st;
+    }
+    int ks[4]; double cf[4];
+    for (int j = 0; j < 4; ++j) { ks[j] = SLOT_K1 + j; cf[j] = frac_val(kRK4B[j]); }
+    if ((st = enqueue_stage(c, 4, ks, cf, SLOT_UNEW)) != DNS_OK) return st;
+    CK(timed(c, PR_CTRL, [&] {
+         return launch_controller(c->ctrl, c->partials, 0, 4, c->g.nmodes_half, c->stream);
+       }), "controller");
+    return DNS_OK;
+  }
+  // BS5: k_1 only when not carried over (first same as last)
+  if ((st = enqueue_rhs(c, c->ctrl, SLOT_U, SLOT_K1, 1)) != DNS_OK) return st;
+  for (int i = 1; i < 8; ++i) {
+    int ks[7]; double cf[7]; int n = 0;
+    for (int j = 0; j < i; ++j)
+      if (kBS5A[i][j].p != 0) { ks[n] = SLOT_K1 + j; cf[n] = frac_val(kBS5A[i][j]); ++n; }
+    const int ys = (i == 7) ? SLOT_UNEW : SLOT_Y;
+    if ((st = enqueue_stage(c, n, ks, cf, ys)) != DNS_OK) return st;
+    if ((st = enqueue_rhs(c, c->ctrl, ys, SLOT_K1 + i, 0)) != DNS_OK) return st;
+  }
+  ErrArgs e{};
+  e.ctrl = c->ctrl;
+  e.M = c->g.M;
+  e.partials = c->partials;
+  int n = 0;
+  for (int j = 0; j < 8; ++j) {
+    if (kBS5B[j].p * kBS5Bh[j].q == kBS5Bh[j].p * kBS5B[j].q) continue;
+    e.kslot[n] = SLOT_K1 + j;
+    e.coef[n] = frac_diff(kBS5B[j], kBS5Bh[j]);
+    ++n;
+  }
+  e.nterms = n;
+  CK(timed(c, PR_ERR, [&] { return launch_err_partials(e, c->stream); }), "error norm");
+  CK(timed(c, PR_CTRL, [&] {
+       return launch_controller(c->ctrl, c->partials, method, 8, c->g.nmodes_half, c->stream);
+     }), "controller");
+  return DNS_OK;
+}
+
+dns_status check_ctx(dns_ctx* c) {
+  if (!c) return DNS_ERR_ARG;
+  if (c->failed) return DNS_ERR_STATE;
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, DNS_ERR_CUDA, "cudaSetDevice");
+  return DNS_OK;
+}
+
+dns_status read_ctrl(dns_ctx* c) {
+  CK(cudaMemcpyAsync(c->host_ctrl, c->ctrl, sizeof(DnsCtrl), cudaMemcpyDeviceToHost, c->stream), "ctrl read");
+  CK(cudaStreamSynchronize(c->stream), "synchronize");
+  return DNS_OK;
+}
+
+void fill_info(dns_ctx* c, dns_step_info* info) {
+  if (!info) return;
+  const DnsCtrl& h = *c->host_ctrl;
+  info->accepted = h.accepted;
+  info->status = h.status;
+  info->err = h.err;
+  info->h_used = h.h_try;
+  info->h_next = h.h;
+  info->t = h.t;
+  info->n_rhs = h.n_rhs;
+  info->n_acc = h.n_acc;
+  info->n_rej = h.n_rej;
+}
+
+dns_status status_from_ctrl(dns_ctx* c) {
+  switch (c->host_ctrl->status) {
+    case ST_OK: return DNS_OK;
+    case ST_NONFINITE: return fail(c, DNS_ERR_NONFINITE, "error estimate not finite through max_rejects retries");
+    case ST_UNDERFLOW: return fail(c, DNS_ERR_STEP_UNDERFLOW, "step size underflow");
+    case ST_MAX_REJECTS: return fail(c, DNS_ERR_MAX_REJECTS, "too many rejected steps in a row");
+  }
+  return fail(c, DNS_ERR_STATE, "unknown device status");
+}
+
+dns_status ensure_stage(dns_ctx* c) {
+  if (c->full_stage) return DNS_OK;
+  const size_t bytes = (size_t)3 * c->g.nx * c->g.ny * c->g.nzh * sizeof(double2);
+  return alloc(c, (void**)&c->full_stage, bytes);
+}
+
+}  // namespace
+
+extern "C" {
+
+dns_status dns_create(int nx, int ny, int nz, double nu, const dns_forcing* forcing, int precision,
+                      dns_ctx** out) {
+  dns_config cfg{};
+  cfg.nx = nx; cfg.ny = ny; cfg.nz = nz; cfg.nu = nu; cfg.precision = precision;
+  if (forcing) cfg.forcing = *forcing;
+  return dns_create_ex(&cfg, out);
+}
+
+dns_status dns_create_ex(const dns_config* cfg, dns_ctx** out) {
+  if (!cfg || !out) return DNS_ERR_ARG;
+  *out = nullptr;
+  if (!supported(cfg->nx) || !supported(cfg->ny) || !supported(cfg->nz)) return DNS_ERR_UNSUPPORTED;
+  if (cfg->precision != DNS_FP64 && cfg->precision != DNS_FP32_MIXED) return DNS_ERR_ARG;
+  if (!(cfg->nu >= 0.0) || !std::isfinite(cfg->nu)) return DNS_ERR_ARG;
+  if (cfg->forcing.kind != 0 && cfg->forcing.kind != 1) return DNS_ERR_ARG;
+  dns_ctx* c = new dns_ctx();
+  c->precision = cfg->precision;
+  c->nu = cfg->nu;
+  c->forcing = cfg->forcing;
+  cudaGetDevice(&c->device);
+  Geom& g = c->g;
+  g.nx = cfg->nx; g.ny = cfg->ny; g.nz = cfg->nz; g.nzh = cfg->nz / 2 + 1;
+  g.Kx = (g.nx - 1) / 3; g.Ky = (g.ny - 1) / 3; g.Kz = (g.nz - 1) / 3;
+  g.Mx = 2 * g.Kx + 1; g.My = 2 * g.Ky + 1; g.Mz = g.Kz + 1;
+  g.MyMz = g.My * g.Mz;
+  g.M = (long long)g.Mx * g.MyMz;
+  const double twopi = 6.283185307179586476925286766559;
+  const double lx = cfg->lx > 0 ? cfg->lx : twopi, ly = cfg->ly > 0 ? cfg->ly : twopi;
+  const double lz = cfg->lz > 0 ? cfg->lz : twopi;
+  g.sx = cfg->lx > 0 ? twopi / lx : 1.0;
+  g.sy = cfg->ly > 0 ? twopi / ly : 1.0;
+  g.sz = cfg->lz > 0 ? twopi / lz : 1.0;
+  g.inv_n3 = 1.0 / ((double)g.nx * g.ny * g.nz);
+  g.nmodes_half = (double)g.nx * g.ny * g.nzh;
+
+  const size_t vbytes = (size_t)3 * g.M * sizeof(double2);
+  const size_t esz = c->precision == DNS_FP32_MIXED ? sizeof(float2) : sizeof(double2);
+  const size_t nA = std::max((size_t)6 * g.nx * g.My * g.Mz, (size_t)3 * g.nx * g.ny * g.Mz);
+  const size_t nB = std::max((size_t)6 * g.nx * g.ny * g.Mz, (size_t)3 * g.nx * g.My * g.Mz);
+  dns_status s = DNS_OK;
+  auto A = [&](void** p, size_t b) { if (s == DNS_OK) s = alloc(c, p, b); };
+  A((void**)&c->uu[0], vbytes); A((void**)&c->uu[1], vbytes);
+  A((void**)&c->kk[0], vbytes); A((void**)&c->kk[1], vbytes);
+  for (int i = 2; i <= 7; ++i) A((void**)&c->kfix[i], vbytes);
+  A((void**)&c->ystage, vbytes);
+  A((void**)&c->rhs_in, vbytes); A((void**)&c->rhs_out, vbytes);
+  A(&c->bufA, nA * esz); A(&c->bufB, nB * esz);
+  A((void**)&c->ctrl, sizeof(DnsCtrl)); A((void**)&c->ctrl_rhs, sizeof(DnsCtrl));
+  A((void**)&c->partials, (size_t)kRedBlocks * 3 * sizeof(double));
+  if (s == DNS_OK) s = make_twiddles(c, g.nx, &c->tw[0]);
+  if (s == DNS_OK) s = make_twiddles(c, g.ny, &c->tw[1]);
+  if (s == DNS_OK) s = make_twiddles(c, g.nz, &c->tw[2]);
+  if (s == DNS_OK && cudaMallocHost((void**)&c->host_ctrl, sizeof(DnsCtrl)) != cudaSuccess) s = DNS_ERR_OOM;
+  if (s == DNS_OK && cudaMallocHost((void**)&c->host_partials, (size_t)kRedBlocks * 3 * sizeof(double)) != cudaSuccess)
+    s = DNS_ERR_OOM;
+  if (s == DNS_OK) {
+    DnsCtrl h{};
+    h.uu[0] = c->uu[0]; h.uu[1] = c->uu[1];
+    h.kk[0] = c->kk[0]; h.kk[1] = c->kk[1];
+    for (int i = 2; i <= 7; ++i) h.kfix[i] = c->kfix[i];
+    h.slot[SLOT_Y] = c->ystage;
+    h.slot[SLOT_U] = c->uu[0];
+    h.slot[SLOT_UNEW] = c->uu[1];
+    h.slot[SLOT_K1] = c->kk[0];
+    for (int i = 2; i <= 7; ++i) h.slot[SLOT_K1 + i - 1] = c->kfix[i];
+    h.slot[SLOT_K1 + 7] = c->kk[1];
+    h.done = 1; h.max_rejects = 30; h.method = DNS_BS5_ADAPTIVE;
+    DnsCtrl r{};
+    r.slot[SLOT_Y] = c->rhs_in;
+    r.slot[SLOT_K1] = c->rhs_out;
+    r.need_k1 = 1;
+    if (cudaMemcpy(c->ctrl, &h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->ctrl_rhs, &r, sizeof(r), cudaMemcpyHostToDevice) != cudaSuccess)
+      s = DNS_ERR_CUDA;
+  }
+  if (s != DNS_OK) {
+    dns_destroy(c);
+    return s;
+  }
+  *out = c;
+  return DNS_OK;
+}
+
+void dns_destroy(dns_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  void* ptrs[] = {c->uu[0], c->uu[1], c->kk[0], c->kk[1], c->ystage, c->rhs_in, c->rhs_out,
+                  c->full_stage, c->bufA, c->bufB, c->tw[0], c->tw[1], c->tw[2], c->ctrl,
+                  c->ctrl_rhs, c->partials};
+  for (void* p : ptrs) if (p) cudaFree(p);
+  for (int i = 2; i <= 7; ++i) if (c->kfix[i]) cudaFree(c->kfix[i]);
+  if (c->host_ctrl) cudaFreeHost(c->host_ctrl);
+  if (c->host_partials) cudaFreeHost(c->host_partials);
+  for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+  delete c;
+}
+
+const char* dns_last_error(const dns_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+dns_status dns_set_stream(dns_ctx* c, void* stream) {
+  if (!c) return DNS_ERR_ARG;
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  return DNS_OK;
+}
+
+dns_status dns_set_state(dns_ctx* c, const void* uhat, int where, double t) {
+  dns_status s = check_ctx(c);
+  if (s != DNS_OK) return s;
+  if (!uhat || (where != 0 && where != 1) || !std::isfinite(t)) return fail(c, DNS_ERR_ARG, "dns_set_state: bad argument");
+  const double2* src = reinterpret_cast<const double2*>(uhat);
+  if (where == 1) {
+    if ((s = ensure_stage(c)) != DNS_OK) return s;
+    const size_t bytes = (size_t)3 * c->g.nx * c->g.ny * c->g.nzh * sizeof(double2);
+    CK(cudaMemcpyAsync(c->full_stage, uhat, bytes, cudaMemcpyHostToDevice, c->stream), "state upload");
+    src = c->full_stage;
+  }
+  CK(launch_gather(c->g, src, c->uu[0], c->stream), "gather");
+  CK(launch_ctrl_reset(c->ctrl, t, c->stream), "controller reset");
+  if (where == 1) CK(cudaStreamSynchronize(c->stream), "synchronize");
+  c->has_state = true;
+  return DNS_OK;
+}
+
+dns_status dns_get_state(dns_ctx* c, void* uhat, int where) {
+  dns_status s = check_ctx(c);
+  if (s != DNS_OK) return s;
+  if (!uhat || (where != 0 && where != 1)) return fail(c, DNS_ERR_ARG, "dns_get_state: bad argument");
+  if (!c->has_state) return fail(c, DNS_ERR_STATE, "no state set");
+  const size_t bytes = (size_t)3 * c->g.nx * c->g.ny * c->g.nzh * sizeof(double2);
+  double2* dst = reinterpret_cast<double2*>(uhat);
+  if (where == 1) {
+    if ((s = ensure_stage(c)) != DNS_OK) return s;
+    dst = c->full_stage;
+  }
+  CK(cudaMemsetAsync(dst, 0, bytes, c->stream), "memset");
+  s = read_ctrl(c);
+  if (s != DNS_OK) return s;
+  const double2* cur = c->uu[c->host_ctrl->parity];
+  CK(launch_scatter(c->g, cur, dst, c->stream), "scatter");
+  if (where == 1) CK(cudaMemcpyAsync(uhat, c->full_stage, bytes, cudaMemcpyDeviceToHost, c->stream), "state download");
+  CK(cudaStreamSynchronize(c->stream), "synchronize");
+  return DNS_OK;
+}
+
+dns_status dns_rhs(dns_ctx* c, const void* uhat_dev, void* f_dev) {
+  dns_status s = check_ctx(c);
+  if (s != DNS_OK) return s;
+  if (!uhat_dev || !f_dev || uhat_dev == f_dev) return fail(c, DNS_ERR_ARG, "dns_rhs: bad pointers");
+  const size_t bytes = (size_t)3 * c->g.nx * c->g.ny * c->g.nzh * sizeof(double2);
+  CK(launch_gather(c->g, reinterpret_cast<const double2*>(uhat_dev), c->rhs_in, c->stream), "gather");
+  if ((s = enqueue_rhs(c, c->ctrl_rhs, SLOT_Y, SLOT_K1, 0)) != DNS_OK) return s;
+  CK(cudaMemsetAsync(f_dev, 0, bytes, c->stream), "memset");
+  CK(launch_scatter(c->g, c->rhs_out, reinterpret_cast<double2*>(f_dev), c->stream), "scatter");
+  return DNS_OK;
+}
+
+static dns_status config(dns_ctx* c, double t_end, int method, double rtol, double atol, double h0,
+                         int max_rejects) {
+  if (method < 0 || method > 2) return fail(c, DNS_ERR_ARG, "unknown method");
+  if (!(t_end == t_end)) return fail(c, DNS_ERR_ARG, "t_end is NaN");
+  if (method != DNS_RK4 && (!(rtol >= 0) || !(atol >= 0) || (rtol == 0 && atol == 0)))
+    return fail(c, DNS_ERR_ARG, "tolerances must be >= 0 and not both 0");
+  if (!(h0 == h0)) return fail(c, DNS_ERR_ARG, "h0 is NaN");
+  CK(launch_ctrl_config(c->ctrl, t_end, method, rtol, atol, h0, max_rejects > 0 ? max_rejects : 30,
+                        c->stream), "controller config");
+  return DNS_OK;
+}
+
+dns_status dns_step(dns_ctx* c, int method, double h, double rtol, double atol, double t_end,
+                    dns_step_info* info) {
+  dns_status s = check_ctx(c);
+  if (s != DNS_OK) return s;
+  if (!c->has_state) return fail(c, DNS_ERR_STATE, "no state set");
+  if (!(h > 0)) return fail(c, DNS_ERR_ARG, "h must be > 0");
+  if ((s = read_ctrl(c)) != DNS_OK) return s;
+  if (!(t_end > c->host_ctrl->t)) t_end = INFINITY;
+  if ((s = config(c, t_end, method, rtol, atol, h, 0)) != DNS_OK) return s;
+  if ((s = enqueue_attempt(c, method)) != DNS_OK) return s;
+  if ((s = read_ctrl(c)) != DNS_OK) return s;
+  fill_info(c, info);
+  return status_from_ctrl(c);
+}
+
+dns_status dns_integrate(dns_ctx* c, double t_end, int method, double rtol, double atol, double h0,
+                         int max_rejects, dns_step_info* info) {
+  dns_status s = check_ctx(c);
+  if (s != DNS_OK) return s;
+  if (!c->has_state) return fail(c, DNS_ERR_STATE, "no state set");
+  if ((s = read_ctrl(c)) != DNS_OK) return s;
+  if (!(h0 > 0) && !(c->host_ctrl->h > 0)) return fail(c, DNS_ERR_ARG, "no step size: pass h0 > 0");
+  if ((s = config(c, t_end, method, rtol, atol, h0, max_rejects)) != DNS_OK) return s;
+  const double cells = (double)c->g.nx * c->g.ny * c->g.nz;
+  int chunk = (int)std::max(1.0, std::min(32.0, 4.0 * 1048576.0 / cells));
+  long long guard = 0;
+  for (;;) {
+    for (int i = 0; i < chunk; ++i)
+      if ((s = enqueue_attempt(c, method)) != DNS_OK) return s;
+    if ((s = read_ctrl(c)) != DNS_OK) return s;
+    if (c->host_ctrl->done || c->host_ctrl->status != 0) break;
+    if (++guard > 100000000LL / chunk) return fail(c, DNS_ERR_STATE, "step limit reached");
+  }
+  fill_info(c, info);
+  return status_from_ctrl(c);
+}
+
+dns_status dns_enqueue_attempts(dns_ctx* c, int n, int method, double rtol, double atol,
+                                double t_end, double h0) {
+  dns_status s = check_ctx(c);
+  if (s != DNS_OK) return s;
+  if (!c->has_state) return fail(c, DNS_ERR_STATE, "no state set");
+  if (n < 0) return fail(c, DNS_ERR_ARG, "n < 0");
+  if ((s = config(c, t_end, method, rtol, atol, h0, 0)) != DNS_OK) return s;
+  for (int i = 0; i < n; ++i)
+    if ((s = enqueue_attempt(c, method)) != DNS_OK) return s;
+  return DNS_OK;
+}
+
+dns_status dns_get_info(dns_ctx* c, dns_step_info* info) {
+  dns_status s = check_ctx(c);
+  if (s != DNS_OK) return s;
+  if ((s = read_ctrl(c)) != DNS_OK) return s;
+  fill_info(c, info);
+  return status_from_ctrl(c);
+}
+
+dns_status dns_diagnostics(dns_ctx* c, double* E, double* Omega, double* eps) {
+  dns_status s = check_ctx(c);
+  if (s != DNS_OK) return s;
+  if (!c->has_state) return fail(c, DNS_ERR_STATE, "no state set");
+  if ((s = read_ctrl(c)) != DNS_OK) return s;
+  const double2* cur = c->uu[c->host_ctrl->parity];
+  CK(cudaMemcpyAsync(c->rhs_in, cur, (size_t)3 * c->g.M * sizeof(double2), cudaMemcpyDeviceToDevice,
+                     c->stream), "copy");
+  if ((s = enqueue_rhs(c, c->ctrl_rhs, SLOT_Y, SLOT_K1, 0)) != DNS_OK) return s;
+  CK(launch_diag_partials(c->g, c->rhs_in, c->rhs_out, c->partials, c->stream), "diagnostics");
+  CK(cudaMemcpyAsync(c->host_partials, c->partials, (size_t)kRedBlocks * 3 * sizeof(double),
+                     cudaMemcpyDeviceToHost, c->stream), "read partials");
+  CK(cudaStreamSynchronize(c->stream), "synchronize");
+  double v[3] = {0, 0, 0};
+  for (int b = 0; b < kRedBlocks; ++b)
+    for (int q = 0; q < 3; ++q) v[q] += c->host_partials[b * 3 + q];
+  const double n6 = c->g.inv_n3 * c->g.inv_n3;
+  if (E) *E = 0.5 * v[0] * n6;
+  if (Omega) *Omega = 0.5 * v[1] * n6;
+  if (eps) *eps = -v[2] * n6;
+  return DNS_OK;
+}
+
+dns_status dns_profile_enable(dns_ctx* c, int enable) {
+  if (!c) return DNS_ERR_ARG;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  c->recs.clear();
+  c->pool_used = 0;
+  c->prof = enable != 0;
+  return DNS_OK;
+}
+
+int dns_profile_count(dns_ctx* c) { return c ? PR_N : 0; }
+
+dns_status dns_profile_get(dns_ctx* c, int i, const char** name, long long* launches, double* total_ms) {
+  if (!c || i < 0 || i >= PR_N) return DNS_ERR_ARG;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  long long n = 0;
+  double ms = 0.0;
+  for (const ProfRec& r : c->recs) {
+    if (r.id != i) continue;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) ms += t;
+    ++n;
+  }
+  if (name) *name = kPassNames[i];
+  if (launches) *launches = n;
+  if (total_ms) *total_ms = ms;
+  return DNS_OK;
+}
+
+dns_status dns_query(const dns_ctx* c, int* K3, size_t* device_bytes) {
+  if (!c) return DNS_ERR_ARG;
+  if (K3) { K3[0] = c->g.Kx; K3[1] = c->g.Ky; K3[2] = c->g.Kz; }
+  if (device_bytes) *device_bytes = c->device_bytes;
+  return DNS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,97 @@
+// Shared device-side definitions: complex helpers, grid geometry, the controller record.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dns {
+
+template <typename T> struct V2;
+template <> struct V2<double> { using type = double2; };
+template <> struct V2<float> { using type = float2; };
+template <typename T> using v2_t = typename V2<T>::type;
+
+template <typename V> __device__ __forceinline__ V mk(decltype(V::x) a, decltype(V::x) b) {
+  V r; r.x = a; r.y = b; return r;
+}
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return mk<V>(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return mk<V>(a.x - b.x, a.y - b.y); }
+// a * b
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+  return mk<V>(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+template <typename V> __device__ __forceinline__ V cmulc(V a, V b) {
+  return mk<V>(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+}
+// s * i * a for s = +1 / -1
+template <int S, typename V> __device__ __forceinline__ V mul_si(V a) {
+  return S > 0 ? mk<V>(-a.y, a.x) : mk<V>(a.y, -a.x);
+}
+template <typename V> __device__ __forceinline__ V cscale(V a, decltype(V::x) s) { return mk<V>(a.x * s, a.y * s); }
+template <typename V> __device__ __forceinline__ V cconj(V a) { return mk<V>(a.x, -a.y); }
+
+// Grid geometry shared by every kernel.  Retained ("compact") spectral arrays are
+// [3][Mx][My][Mz] with Mx = 2Kx+1 (kx = i for i <= Kx, i - Mx above), Mz = Kz+1.
+struct Geom {
+  int nx, ny, nz, nzh;
+  int Kx, Ky, Kz;
+  int Mx, My, Mz;
+  int MyMz;
+  long long M;          // Mx*My*Mz
+  double sx, sy, sz;    // 2 pi / L per axis
+  double inv_n3;        // 1 / (nx ny nz)
+  double nmodes_half;   // nx ny (nz/2+1), divisor of the error norm
+};
+
+__host__ __device__ __forceinline__ int signed_mode(int i, int K, int Mc) { return i <= K ? i : i - Mc; }
+
+// Buffer slots resolved at the start of each attempt (ping-pong for first-same-as-last).
+enum Slot : int {
+  SLOT_U = 0,        // u_n
+  SLOT_K1 = 1,       // k_1 .. k_8 at SLOT_K1 + (i-1)
+  SLOT_Y = 9,        // scratch stage input
+  SLOT_UNEW = 10,    // u_{n+1} (last stage input of an FSAL pair)
+  SLOT_COUNT = 16
+};
+
+// Device-resident step controller state.  One writer (the controller kernel, one thread).
+struct DnsCtrl {
+  double2* slot[SLOT_COUNT];
+  double2* uu[2];
+  double2* kk[2];
+  double2* kfix[9];     // fixed stage buffers k_2..k_7 (index = stage number)
+  double t, t_end, h, h_try, err, rtol, atol;
+  double errc[3];
+  double forcing_coef;  // power / (2 E_f) of the current stage input
+  int method;
+  int parity;
+  int skip;             // this attempt does nothing (finished or failed)
+  int need_k1;          // k_1 must be evaluated in this attempt
+  int k1_valid;
+  int done;
+  int status;
+  int clipped;
+  int after_reject;
+  int accepted;
+  int max_rejects;
+  int pad_;
+  long long n_rhs, n_acc, n_rej, n_attempts, rejects_in_row;
+};
+
+__device__ __forceinline__ const double2* resolve_in(const double2* p, const DnsCtrl* c, int slot) {
+  return (c && slot >= 0) ? c->slot[slot] : p;
+}
+__device__ __forceinline__ double2* resolve_out(double2* p, const DnsCtrl* c, int slot) {
+  return (c && slot >= 0) ? c->slot[slot] : p;
+}
+// gate: skip flags a launch may check (the k_1 evaluation runs only when needed)
+__device__ __forceinline__ bool gated_off(const DnsCtrl* c, int only_if_need_k1) {
+  if (!c) return false;
+  if (c->skip) return true;
+  return only_if_need_k1 && !c->need_k1;
+}
+
+enum DnsStatusDev : int { ST_OK = 0, ST_NONFINITE = 4, ST_UNDERFLOW = 5, ST_MAX_REJECTS = 6 };
+
+}  // namespace dns

@@ -1,0 +1,189 @@
+// Batched line FFTs in shared memory: mixed-radix (2,3,4,8,16) Stockham auto-sort stages,
+// each thread doing whole radix-R butterflies in registers.
+//
+// A CTA holds several lines of length N in shared memory; G threads cooperate on one line.
+// Stage s (radix R, NS = product of the earlier radices) reads R elements of butterfly j at
+// stride N/R, applies twiddles W_N^{(j mod NS) r N/(NS R)}, does an R-point DFT in registers
+// and writes them to (j - j mod NS) R + j mod NS + r NS.  All reads of a stage finish
+// (barrier) before any write, so one buffer suffices.  SIGN = -1 forward, +1 inverse
+// (unnormalised both ways).
+#pragma once
+
+#include "common.cuh"
+
+namespace dns {
+
+template <int N> struct FftPlan;
+// S stages of radices R0, R1, R2; G threads per line.
+template <> struct FftPlan<4>   { static constexpr int S = 1, R0 = 4,  R1 = 1,  R2 = 1, G = 1;  };
+template <> struct FftPlan<6>   { static constexpr int S = 2, R0 = 2,  R1 = 3,  R2 = 1, G = 3;  };
+template <> struct FftPlan<8>   { static constexpr int S = 1, R0 = 8,  R1 = 1,  R2 = 1, G = 1;  };
+template <> struct FftPlan<12>  { static constexpr int S = 2, R0 = 4,  R1 = 3,  R2 = 1, G = 4;  };
+template <> struct FftPlan<16>  { static constexpr int S = 2, R0 = 4,  R1 = 4,  R2 = 1, G = 4;  };
+template <> struct FftPlan<24>  { static constexpr int S = 2, R0 = 8,  R1 = 3,  R2 = 1, G = 8;  };
+template <> struct FftPlan<32>  { static constexpr int S = 2, R0 = 8,  R1 = 4,  R2 = 1, G = 8;  };
+template <> struct FftPlan<48>  { static constexpr int S = 3, R0 = 4,  R1 = 4,  R2 = 3, G = 16; };
+template <> struct FftPlan<64>  { static constexpr int S = 2, R0 = 8,  R1 = 8,  R2 = 1, G = 8;  };
+template <> struct FftPlan<96>  { static constexpr int S = 3, R0 = 8,  R1 = 4,  R2 = 3, G = 16; };
+template <> struct FftPlan<128> { static constexpr int S = 2, R0 = 16, R1 = 8,  R2 = 1, G = 8;  };
+template <> struct FftPlan<256> { static constexpr int S = 2, R0 = 16, R1 = 16, R2 = 1, G = 16; };
+template <> struct FftPlan<512> { static constexpr int S = 3, R0 = 8,  R1 = 8,  R2 = 8, G = 32; };
+
+template <int N, int s> struct StageInfo {
+  static constexpr int R = s == 0 ? FftPlan<N>::R0 : (s == 1 ? FftPlan<N>::R1 : FftPlan<N>::R2);
+  static constexpr int NS = s == 0 ? 1 : (s == 1 ? FftPlan<N>::R0 : FftPlan<N>::R0 * FftPlan<N>::R1);
+};
+
+// ---- R-point DFTs in registers: X_k = sum_r v_r exp(SIGN 2 pi i r k / R) -------------------
+
+template <int R, int SIGN, typename V> struct Dft;
+
+template <int SIGN, typename V> struct Dft<2, SIGN, V> {
+  static __device__ __forceinline__ void run(V* v) {
+    V a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  }
+};
+
+template <int SIGN, typename V> struct Dft<3, SIGN, V> {
+  static __device__ __forceinline__ void run(V* v) {
+    using T = decltype(V::x);
+    const T h3 = (T)0.86602540378443864676;   // sqrt(3)/2
+    V a = v[0], t = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+    V s = mk<V>(fma((T)-0.5, t.x, a.x), fma((T)-0.5, t.y, a.y));
+    V q = mul_si<SIGN>(cscale(d, h3));
+    v[0] = cadd(a, t);
+    v[1] = cadd(s, q);
+    v[2] = csub(s, q);
+  }
+};
+
+template <int SIGN, typename V> struct Dft<4, SIGN, V> {
+  static __device__ __forceinline__ void run(V* v) {
+    V s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    V s13 = cadd(v[1], v[3]), d13 = mul_si<SIGN>(csub(v[1], v[3]));
+    v[0] = cadd(s02, s13);
+    v[2] = csub(s02, s13);
+    v[1] = cadd(d02, d13);
+    v[3] = csub(d02, d13);
+  }
+};
+
+// multiply by W8^1 = (1 + SIGN i)/sqrt2 and W8^3 = (-1 + SIGN i)/sqrt2
+template <int SIGN, typename V> __device__ __forceinline__ V w8_1(V a) {
+  using T = decltype(V::x);
+  const T r = (T)0.70710678118654752440;
+  return SIGN < 0 ? mk<V>((a.x + a.y) * r, (a.y - a.x) * r) : mk<V>((a.x - a.y) * r, (a.y + a.x) * r);
+}
+template <int SIGN, typename V> __device__ __forceinline__ V w8_3(V a) {
+  using T = decltype(V::x);
+  const T r = (T)0.70710678118654752440;
+  return SIGN < 0 ? mk<V>((a.y - a.x) * r, -(a.x + a.y) * r) : mk<V>(-(a.x + a.y) * r, (a.x - a.y) * r);
+}
+
+template <int SIGN, typename V> struct Dft<8, SIGN, V> {
+  // 8 = 4 x 2: n = 2 n1 + n2, k = k1 + 4 k2
+  static __device__ __forceinline__ void run(V* v) {
+    V e[4] = {v[0], v[2], v[4], v[6]};
+    V o[4] = {v[1], v[3], v[5], v[7]};
+    Dft<4, SIGN, V>::run(e);
+    Dft<4, SIGN, V>::run(o);
+    o[1] = w8_1<SIGN>(o[1]);
+    o[2] = mul_si<SIGN>(o[2]);
+    o[3] = w8_3<SIGN>(o[3]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[k] = cadd(e[k], o[k]);
+      v[k + 4] = csub(e[k], o[k]);
+    }
+  }
+};
+
+template <int SIGN, typename V> struct Dft<16, SIGN, V> {
+  // 16 = 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2; inner twiddle W16^{n2 k1}
+  static __device__ __forceinline__ void run(V* v) {
+    using T = decltype(V::x);
+    const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;
+    V y[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+      y[n2][0] = v[n2]; y[n2][1] = v[4 + n2]; y[n2][2] = v[8 + n2]; y[n2][3] = v[12 + n2];
+      Dft<4, SIGN, V>::run(y[n2]);
+    }
+    const T sg = (T)SIGN;
+    // n2 = 1: W^0, W^1, W^2, W^3
+    y[1][1] = cmul(y[1][1], mk<V>(c1, sg * s1));
+    y[1][2] = w8_1<SIGN>(y[1][2]);
+    y[1][3] = cmul(y[1][3], mk<V>(s1, sg * c1));
+    // n2 = 2: W^0, W^2, W^4, W^6
+    y[2][1] = w8_1<SIGN>(y[2][1]);
+    y[2][2] = mul_si<SIGN>(y[2][2]);
+    y[2][3] = w8_3<SIGN>(y[2][3]);
+    // n2 = 3: W^0, W^3, W^6, W^9
+    y[3][1] = cmul(y[3][1], mk<V>(s1, sg * c1));
+    y[3][2] = w8_3<SIGN>(y[3][2]);
+    y[3][3] = cmul(y[3][3], mk<V>(-c1, -sg * s1));
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      V z[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+      Dft<4, SIGN, V>::run(z);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = z[k2];
+    }
+  }
+};
+
+// ---- one Stockham stage and the whole line transform ------------------------------------
+
+// tw: table of N*TWS entries, tw[m] = exp(-2 pi i m / (N TWS)); the stage uses tw[m TWS].
+template <typename V, int N, int SIGN, int TWS, int s>
+__device__ __forceinline__ void fft_stage(V* x, int g, const V* tw, bool active) {
+  constexpr int R = StageInfo<N, s>::R;
+  constexpr int NS = StageInfo<N, s>::NS;
+  constexpr int B = N / R;
+  constexpr int G = FftPlan<N>::G;
+  constexpr int PER = (B + G - 1) / G;
+  V v[PER][R];
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int j = g + p * G;
+    if (active && ((B % G == 0) || j < B)) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[p][r] = x[j + r * B];
+      if (NS > 1) {
+        const int jm = j % NS;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const V w = tw[(jm * r * (N / (NS * R))) * TWS];
+          v[p][r] = SIGN < 0 ? cmul(v[p][r], w) : cmulc(v[p][r], w);
+        }
+      }
+      Dft<R, SIGN, V>::run(v[p]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int j = g + p * G;
+    if (active && ((B % G == 0) || j < B)) {
+      const int jm = j % NS;
+      const int base = (j - jm) * R + jm;
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[base + r * NS] = v[p][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Transform the line at x (contiguous, length N) with G = FftPlan<N>::G threads (g = 0..G-1).
+// Every thread of the CTA must call this (it contains barriers); the caller syncs before.
+// Threads with active = false only take part in the barriers.
+template <typename V, int N, int SIGN, int TWS>
+__device__ __forceinline__ void line_fft(V* x, int g, const V* tw, bool active = true) {
+  fft_stage<V, N, SIGN, TWS, 0>(x, g, tw, active);
+  if constexpr (FftPlan<N>::S > 1) fft_stage<V, N, SIGN, TWS, 1>(x, g, tw, active);
+  if constexpr (FftPlan<N>::S > 2) fft_stage<V, N, SIGN, TWS, 2>(x, g, tw, active);
+}
+
+}  // namespace dns

@@ -1,0 +1,103 @@
+// Launchers for the five passes: pick the kernel instantiation for the run-time line length
+// and size the grid and the dynamic shared memory.
+#pragma once
+
+#include "passes.cuh"
+
+namespace dns {
+
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T, int N>
+static cudaError_t launch_p1(const PassArgs& a, cudaStream_t s) {
+  constexpr int TC = p1_cols<N>();
+  const size_t smem = (size_t)(N + 3 * TC * (N + 1)) * sizeof(v2_t<T>);
+  cudaError_t e = set_smem(k_p1<T, N>, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.g.MyMz + TC - 1) / TC, 2);
+  k_p1<T, N><<<grid, FftPlan<N>::G * 3 * TC, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int N>
+static cudaError_t launch_p5(const PassArgs& a, cudaStream_t s) {
+  constexpr int TC = p1_cols<N>();
+  const size_t smem = (size_t)(N + 3 * TC * (N + 1)) * sizeof(v2_t<T>);
+  cudaError_t e = set_smem(k_p5<T, N>, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.g.MyMz + TC - 1) / TC);
+  k_p5<T, N><<<grid, FftPlan<N>::G * 3 * TC, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int N, bool INV>
+static cudaError_t launch_py(const PassArgs& a, cudaStream_t s) {
+  const size_t smem = (size_t)(N + kTZ * (N + 1)) * sizeof(v2_t<T>);
+  cudaError_t e = set_smem(k_py<T, N, INV>, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.g.Mz + kTZ - 1) / kTZ, a.g.nx, INV ? 6 : 3);
+  k_py<T, N, INV><<<grid, FftPlan<N>::G * kTZ, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int MZ>
+static cudaError_t launch_p3(const PassArgs& a, cudaStream_t s) {
+  constexpr int TL = p3_lines<MZ>();
+  const size_t smem = (size_t)(2 * MZ + 6 * TL * (MZ + 1)) * sizeof(v2_t<T>);
+  cudaError_t e = set_smem(k_p3<T, MZ>, smem);
+  if (e != cudaSuccess) return e;
+  const long long nxy = (long long)a.g.nx * a.g.ny;
+  dim3 grid((unsigned)((nxy + TL - 1) / TL));
+  k_p3<T, MZ><<<grid, FftPlan<MZ>::G * 6 * TL, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+#define DNS_XY_SIZES(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(256) X(512)
+#define DNS_ZH_SIZES(X) X(4) X(6) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(128) X(256)
+
+template <typename T>
+cudaError_t launch_pass(int which, const PassArgs& a, cudaStream_t s) {
+  switch (which) {
+    case 1:
+      switch (a.g.nx) {
+#define C1(N) case N: return launch_p1<T, N>(a, s);
+        DNS_XY_SIZES(C1)
+#undef C1
+      }
+      break;
+    case 2:
+      switch (a.g.ny) {
+#define C2(N) case N: return launch_py<T, N, true>(a, s);
+        DNS_XY_SIZES(C2)
+#undef C2
+      }
+      break;
+    case 3:
+      switch (a.g.nz / 2) {
+#define C3(N) case N: return launch_p3<T, N>(a, s);
+        DNS_ZH_SIZES(C3)
+#undef C3
+      }
+      break;
+    case 4:
+      switch (a.g.ny) {
+#define C4(N) case N: return launch_py<T, N, false>(a, s);
+        DNS_XY_SIZES(C4)
+#undef C4
+      }
+      break;
+    case 5:
+      switch (a.g.nx) {
+#define C5(N) case N: return launch_p5<T, N>(a, s);
+        DNS_XY_SIZES(C5)
+#undef C5
+      }
+      break;
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace dns

@@ -1,0 +1,393 @@
+// Runge-Kutta stage sums, embedded error norm and the device step controller (Section 2.2 of
+// arXiv:1810.10197), plus the copies between the half-spectrum layout and the retained box.
+#include "stepper.cuh"
+
+namespace dns {
+
+namespace {
+
+inline int grid_for(long long n, int threads, int cap) {
+  long long b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  return (int)(b < cap ? b : cap);
+}
+
+// Y = u + h * sum_j coef_j k_j, terms added in ascending j; products and sums rounded
+// separately (no contraction) so the value is the plain left-to-right evaluation.
+template <int NT>
+__global__ void k_stage_sum(const StageArgs a) {
+  const DnsCtrl* c = a.ctrl;
+  if (gated_off(c, a.gate_k1)) return;
+  const double h = c->h_try;
+  const double2* __restrict__ u = c->slot[a.uslot];
+  double2* __restrict__ y = c->slot[a.yslot];
+  const double2* k[NT];
+#pragma unroll
+  for (int j = 0; j < NT; ++j) k[j] = c->slot[a.kslot[j]];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n2; i += stride) {
+    double2 kv = k[0][i];
+    double ar = __dmul_rn(a.coef[0], kv.x), ai = __dmul_rn(a.coef[0], kv.y);
+#pragma unroll
+    for (int j = 1; j < NT; ++j) {
+      kv = k[j][i];
+      ar = __dadd_rn(ar, __dmul_rn(a.coef[j], kv.x));
+      ai = __dadd_rn(ai, __dmul_rn(a.coef[j], kv.y));
+    }
+    const double2 uv = u[i];
+    y[i] = make_double2(__dadd_rn(uv.x, __dmul_rn(h, ar)), __dadd_rn(uv.y, __dmul_rn(h, ai)));
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block sum of three values (fixed tree), result valid in thread 0.
+__device__ __forceinline__ void block_sum3(double v[3], double* sh /* 3*32 */) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) v[q] = warp_sum(v[q]);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) sh[q * 32 + w] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      double s = 0.0;
+      for (int i = 0; i < nw; ++i) s += sh[q * 32 + i];
+      v[q] = s;
+    }
+  }
+}
+
+// Per-block partial sums of (|e| / sc)^2 per component, e = h sum_j (b_j - bhat_j) k_j,
+// sc = atol + rtol max(|u_n|, |u_{n+1}|)  (Section 2.2.1).
+template <int NT>
+__global__ void __launch_bounds__(kRedThreads) k_err_partials(const ErrArgs a) {
+  __shared__ double sh[3 * 32];
+  const DnsCtrl* c = a.ctrl;
+  if (c->skip) return;
+  const double h = c->h_try, rtol = c->rtol, atol = c->atol;
+  const double2* __restrict__ u0 = c->slot[SLOT_U];
+  const double2* __restrict__ u1 = c->slot[SLOT_UNEW];
+  const double2* k[NT];
+#pragma unroll
+  for (int j = 0; j < NT; ++j) k[j] = c->slot[a.kslot[j]];
+  double acc[3] = {0.0, 0.0, 0.0};
+  const long long stride = (long long)gridDim.x * blockDim.x;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.M; i += stride) {
+      const long long idx = q * a.M + i;
+      double2 kv = k[0][idx];
+      double er = __dmul_rn(a.coef[0], kv.x), ei = __dmul_rn(a.coef[0], kv.y);
+#pragma unroll
+      for (int j = 1; j < NT; ++j) {
+        kv = k[j][idx];
+        er = __dadd_rn(er, __dmul_rn(a.coef[j], kv.x));
+        ei = __dadd_rn(ei, __dmul_rn(a.coef[j], kv.y));
+      }
+      er = __dmul_rn(h, er);
+      ei = __dmul_rn(h, ei);
+      const double2 a0 = u0[idx], a1 = u1[idx];
+      const double sc = atol + rtol * fmax(hypot(a0.x, a0.y), hypot(a1.x, a1.y));
+      const double r = hypot(er, ei) / sc;
+      acc[q] += r * r;
+    }
+  }
+  block_sum3(acc, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) a.partials[blockIdx.x * 3 + q] = acc[q];
+  }
+}
+
+__global__ void k_begin_attempt(DnsCtrl* c, int method) {
+  if (c->done || c->status != 0) { c->skip = 1; return; }
+  const double rem = c->t_end - c->t;
+  if (!(rem > 0.0)) { c->done = 1; c->skip = 1; return; }
+  const double h = c->h;
+  // the last step lands exactly on t_end, also when h falls short of it by rounding only
+  c->clipped = h >= rem * (1.0 - 1e-10);
+  c->h_try = c->clipped ? rem : h;
+  if (!(c->h_try >= 1e-12 * fmax(1.0, fabs(c->t)))) {
+    c->status = ST_UNDERFLOW; c->done = 1; c->skip = 1; return;
+  }
+  c->skip = 0;
+  const int p = c->parity;
+  c->slot[SLOT_U] = c->uu[p];
+  c->slot[SLOT_UNEW] = c->uu[1 - p];
+  c->slot[SLOT_K1] = c->kk[p];
+  for (int i = 2; i <= 7; ++i) c->slot[SLOT_K1 + i - 1] = c->kfix[i];
+  if (method != 0) c->slot[SLOT_K1 + 7] = c->kk[1 - p];   // k_8 of an FSAL pair
+  c->need_k1 = (method == 0) ? 1 : !c->k1_valid;
+}
+
+// Section 2.2.1: err = max_j sqrt(S_j / (nx ny (nz/2+1))); accept iff err <= 1;
+// h_new = h min(dmax, max(dmin, 0.8 err^(-1/5))), dmax = 1 right after a rejection.
+__global__ void __launch_bounds__(kRedThreads) k_controller(DnsCtrl* c, const double* partials,
+                                                            int method, int nstages, int nblk,
+                                                            double nmodes) {
+  __shared__ double sh[3][kRedThreads];
+  if (c->skip) return;
+  const int tid = threadIdx.x;
+  double s[3] = {0.0, 0.0, 0.0};
+  if (method != 0) {
+    for (int b = tid; b < nblk; b += blockDim.x) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) s[q] += partials[b * 3 + q];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) sh[q][tid] = s[q];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (tid < w) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) sh[q][tid] += sh[q][tid + w];
+    }
+    __syncthreads();
+  }
+  if (tid != 0) return;
+  c->n_attempts += 1;
+  c->n_rhs += (nstages - 1) + c->need_k1;
+  double err = 0.0;
+  bool nan = false;
+  if (method != 0) {
+    for (int q = 0; q < 3; ++q) {
+      const double e = sqrt(sh[q][0] / nmodes);
+      c->errc[q] = e;
+      if (e != e) nan = true;
+      err = e > err ? e : err;
+    }
+    if (nan) err = __longlong_as_double(0x7ff8000000000000ULL);
+    c->k1_valid = 1;
+  }
+  c->err = err;
+  bool accept = true;
+  double h_new = c->h;
+  if (method == 2) {
+    const bool fin = isfinite(err);
+    accept = fin && err <= 1.0;
+    const double dmax = c->after_reject ? 1.0 : 2.0;
+    double fac;
+    if (!fin) fac = 0.01;
+    else if (err == 0.0) fac = dmax;
+    else fac = fmin(dmax, fmax(0.01, 0.8 * pow(err, -1.0 / 5.0)));
+    h_new = c->h_try * fac;
+  }
+  if (accept) {
+    c->t = c->clipped ? c->t_end : c->t + c->h_try;
+    c->parity ^= 1;
+    c->after_reject = 0;
+    c->rejects_in_row = 0;
+    c->n_acc += 1;
+    if (method == 0) c->k1_valid = 0;
+  } else {
+    c->after_reject = 1;
+    c->rejects_in_row += 1;
+    c->n_rej += 1;
+    if (c->rejects_in_row > c->max_rejects) {
+      c->status = isfinite(err) ? ST_MAX_REJECTS : ST_NONFINITE;
+      c->done = 1;
+    }
+  }
+  c->accepted = accept ? 1 : 0;
+  c->h = h_new;
+  if (c->t >= c->t_end) c->done = 1;
+}
+
+__global__ void k_ctrl_reset(DnsCtrl* c, double t) {
+  c->t = t; c->t_end = t; c->h = 0.0; c->h_try = 0.0; c->err = 0.0;
+  c->errc[0] = c->errc[1] = c->errc[2] = 0.0;
+  c->parity = 0; c->skip = 0; c->need_k1 = 1; c->k1_valid = 0; c->done = 1; c->status = 0;
+  c->clipped = 0; c->after_reject = 0; c->accepted = 0;
+  c->n_rhs = c->n_acc = c->n_rej = c->n_attempts = c->rejects_in_row = 0;
+}
+
+__global__ void k_ctrl_config(DnsCtrl* c, double t_end, int method, double rtol, double atol,
+                              double h0, int max_rejects) {
+  c->method = method;
+  c->t_end = t_end; c->rtol = rtol; c->atol = atol;
+  if (h0 > 0.0) { c->h = h0; c->after_reject = 0; }
+  c->max_rejects = max_rejects;
+  c->rejects_in_row = 0;
+  c->done = (c->status != 0) || !(c->t < t_end);
+}
+
+__global__ void k_gather(const Geom g, const double2* __restrict__ full, double2* __restrict__ cmp) {
+  const long long n = 3 * g.M;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const long long q = i / g.M, r = i - q * g.M;
+    const int ix = (int)(r / g.MyMz), rem = (int)(r - (long long)ix * g.MyMz);
+    const int jy = rem / g.Mz, kz = rem - jy * g.Mz;
+    const int fx = ix <= g.Kx ? ix : g.nx - g.Mx + ix;
+    const int fy = jy <= g.Ky ? jy : g.ny - g.My + jy;
+    cmp[i] = full[((q * g.nx + fx) * g.ny + fy) * (long long)g.nzh + kz];
+  }
+}
+
+__global__ void k_scatter(const Geom g, const double2* __restrict__ cmp, double2* __restrict__ full) {
+  const long long n = 3 * g.M;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const long long q = i / g.M, r = i - q * g.M;
+    const int ix = (int)(r / g.MyMz), rem = (int)(r - (long long)ix * g.MyMz);
+    const int jy = rem / g.Mz, kz = rem - jy * g.Mz;
+    const int fx = ix <= g.Kx ? ix : g.nx - g.Mx + ix;
+    const int fy = jy <= g.Ky ? jy : g.ny - g.My + jy;
+    full[((q * g.nx + fx) * g.ny + fy) * (long long)g.nzh + kz] = cmp[i];
+  }
+}
+
+__global__ void k_copy_slot(const DnsCtrl* c, int slot, double2* __restrict__ dst, long long n) {
+  const double2* __restrict__ src = c->slot[slot];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
+}
+
+// Constant-power forcing coefficient power / (2 E_f), E_f = sum_{0<|kappa|<=kf} w |Y|^2 / (2 N^6).
+__global__ void __launch_bounds__(kRedThreads) k_forcing_coef(const Geom g, DnsCtrl* c, int yslot,
+                                                              double kf, double power, int gate_k1) {
+  __shared__ double sh[3 * 32];
+  if (gated_off(c, gate_k1)) return;
+  const double2* __restrict__ Y = c->slot[yslot];
+  const int bx = min(g.Kx, (int)floor(kf / g.sx)), by = min(g.Ky, (int)floor(kf / g.sy));
+  const int bz = min(g.Kz, (int)floor(kf / g.sz));
+  const int nxb = 2 * bx + 1, nyb = 2 * by + 1, nzb = bz + 1;
+  double v[3] = {0.0, 0.0, 0.0};
+  const double kf2 = kf * kf;
+  for (int i = threadIdx.x; i < nxb * nyb * nzb; i += blockDim.x) {
+    const int mx = i / (nyb * nzb) - bx, r = i % (nyb * nzb), my = r / nzb - by, mz = r % nzb;
+    const double kx = g.sx * mx, ky = g.sy * my, kz = g.sz * mz;
+    const double k2 = kx * kx + ky * ky + kz * kz;
+    if (!(k2 > 0.0 && k2 <= kf2)) continue;
+    const int ix = mx >= 0 ? mx : mx + g.Mx, jy = my >= 0 ? my : my + g.My;
+    const long long off = ((long long)ix * g.My + jy) * g.Mz + mz;
+    const double w = mz == 0 ? 1.0 : 2.0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const double2 y = Y[q * g.M + off];
+      v[q] += w * (y.x * y.x + y.y * y.y);
+    }
+  }
+  block_sum3(v, sh);
+  if (threadIdx.x == 0) {
+    const double ef = (v[0] + v[1] + v[2]) * g.inv_n3 * g.inv_n3 * 0.5;
+    c->forcing_coef = ef > 0.0 ? power / (2.0 * ef) : 0.0;
+  }
+}
+
+// Partial sums for E, Omega, eps: sum w |u|^2, sum w |kappa|^2 |u|^2, sum w Re(conj(u).f).
+__global__ void __launch_bounds__(kRedThreads) k_diag_partials(const Geom g, const double2* __restrict__ u,
+                                                               const double2* __restrict__ f,
+                                                               double* partials) {
+  __shared__ double sh[3 * 32];
+  double v[3] = {0.0, 0.0, 0.0};
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < g.M; r += stride) {
+    const int ix = (int)(r / g.MyMz), rem = (int)(r - (long long)ix * g.MyMz);
+    const int jy = rem / g.Mz, kz = rem - jy * g.Mz;
+    const double kx = g.sx * signed_mode(ix, g.Kx, g.Mx), ky = g.sy * signed_mode(jy, g.Ky, g.My);
+    const double kzz = g.sz * kz;
+    const double k2 = kx * kx + ky * ky + kzz * kzz;
+    const double w = kz == 0 ? 1.0 : 2.0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const double2 a = u[q * g.M + r], b = f[q * g.M + r];
+      const double m2 = a.x * a.x + a.y * a.y;
+      v[0] += w * m2;
+      v[1] += w * k2 * m2;
+      v[2] += w * (a.x * b.x + a.y * b.y);
+    }
+  }
+  block_sum3(v, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) partials[blockIdx.x * 3 + q] = v[q];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_stage_sum(const StageArgs& a, cudaStream_t s) {
+  const int blocks = grid_for(a.n2, 256, 152 * 16);
+  switch (a.nterms) {
+    case 1: k_stage_sum<1><<<blocks, 256, 0, s>>>(a); break;
+    case 2: k_stage_sum<2><<<blocks, 256, 0, s>>>(a); break;
+    case 3: k_stage_sum<3><<<blocks, 256, 0, s>>>(a); break;
+    case 4: k_stage_sum<4><<<blocks, 256, 0, s>>>(a); break;
+    case 5: k_stage_sum<5><<<blocks, 256, 0, s>>>(a); break;
+    case 6: k_stage_sum<6><<<blocks, 256, 0, s>>>(a); break;
+    case 7: k_stage_sum<7><<<blocks, 256, 0, s>>>(a); break;
+    case 8: k_stage_sum<8><<<blocks, 256, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_err_partials(const ErrArgs& a, cudaStream_t s) {
+  switch (a.nterms) {
+    case 6: k_err_partials<6><<<kRedBlocks, kRedThreads, 0, s>>>(a); break;
+    case 7: k_err_partials<7><<<kRedBlocks, kRedThreads, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_begin_attempt(DnsCtrl* c, int method, cudaStream_t s) {
+  k_begin_attempt<<<1, 1, 0, s>>>(c, method);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_controller(DnsCtrl* c, const double* partials, int method, int nstages,
+                              double nmodes, cudaStream_t s) {
+  k_controller<<<1, kRedThreads, 0, s>>>(c, partials, method, nstages, kRedBlocks, nmodes);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ctrl_reset(DnsCtrl* c, double t, cudaStream_t s) {
+  k_ctrl_reset<<<1, 1, 0, s>>>(c, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ctrl_config(DnsCtrl* c, double t_end, int method, double rtol, double atol,
+                               double h0, int max_rejects, cudaStream_t s) {
+  k_ctrl_config<<<1, 1, 0, s>>>(c, t_end, method, rtol, atol, h0, max_rejects);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const Geom& g, const double2* full, double2* compact, cudaStream_t s) {
+  k_gather<<<grid_for(3 * g.M, 256, 152 * 16), 256, 0, s>>>(g, full, compact);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const Geom& g, const double2* compact, double2* full, cudaStream_t s) {
+  k_scatter<<<grid_for(3 * g.M, 256, 152 * 16), 256, 0, s>>>(g, compact, full);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_slot(DnsCtrl* c, int slot, double2* dst, long long n2, cudaStream_t s) {
+  k_copy_slot<<<grid_for(n2, 256, 152 * 16), 256, 0, s>>>(c, slot, dst, n2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_forcing_coef(const Geom& g, DnsCtrl* c, int yslot, double kf, double power,
+                                int gate_k1, cudaStream_t s) {
+  k_forcing_coef<<<1, kRedThreads, 0, s>>>(g, c, yslot, kf, power, gate_k1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag_partials(const Geom& g, const double2* u, const double2* f,
+                                 double* partials, cudaStream_t s) {
+  k_diag_partials<<<kRedBlocks, kRedThreads, 0, s>>>(g, u, f, partials);
+  return cudaGetLastError();
+}
+
+}  // namespace dns

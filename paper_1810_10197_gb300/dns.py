@@ -1,0 +1,254 @@
+"""ctypes binding for libdns (include/dns.h).  Argument marshalling only: every step of the
+right-hand side and of the time integration runs in the library's CUDA kernels.
+
+Module-level functions carry the C names (``dns_create``, ``dns_rhs``, ...).  The ``Dns``
+class wraps one context.  torch tensors are passed by ``data_ptr()``; numpy arrays (host) by
+their buffer address.  Spectral fields are complex128 arrays of shape (3, nx, ny, nz//2+1).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdns.so")
+HEADER_PATH = os.path.join(os.path.dirname(_PKG), "include", "dns.h")
+
+DNS_OK = 0
+STATUS_NAMES = {0: "DNS_OK", 1: "DNS_ERR_ARG", 2: "DNS_ERR_CUDA", 3: "DNS_ERR_OOM",
+                4: "DNS_ERR_NONFINITE", 5: "DNS_ERR_STEP_UNDERFLOW", 6: "DNS_ERR_MAX_REJECTS",
+                7: "DNS_ERR_TIMEOUT", 8: "DNS_ERR_STATE", 9: "DNS_ERR_UNSUPPORTED"}
+DNS_RK4, DNS_BS5_FIXED, DNS_BS5_ADAPTIVE = 0, 1, 2
+METHODS = {"RK4": DNS_RK4, "BS5_FIXED": DNS_BS5_FIXED, "BS5_ADAPTIVE": DNS_BS5_ADAPTIVE}
+DNS_FP64, DNS_FP32_MIXED = 0, 1
+SUPPORTED_N = (8, 12, 16, 24, 32, 48, 64, 96, 128, 256, 512)
+
+
+class dns_forcing(C.Structure):
+    _fields_ = [("kind", C.c_int), ("kf", C.c_double), ("power", C.c_double)]
+
+
+class dns_config(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("lx", C.c_double), ("ly", C.c_double), ("lz", C.c_double),
+                ("nu", C.c_double), ("precision", C.c_int), ("forcing", dns_forcing)]
+
+
+class dns_step_info(C.Structure):
+    _fields_ = [("accepted", C.c_int), ("status", C.c_int), ("err", C.c_double),
+                ("h_used", C.c_double), ("h_next", C.c_double), ("t", C.c_double),
+                ("n_rhs", C.c_longlong), ("n_acc", C.c_longlong), ("n_rej", C.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class DnsError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+
+
+_lib = None
+
+_SIGS = {
+    "dns_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.POINTER(dns_forcing), C.c_int,
+                             C.POINTER(C.c_void_p)]),
+    "dns_create_ex": (C.c_int, [C.POINTER(dns_config), C.POINTER(C.c_void_p)]),
+    "dns_destroy": (None, [C.c_void_p]),
+    "dns_last_error": (C.c_char_p, [C.c_void_p]),
+    "dns_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "dns_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double]),
+    "dns_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "dns_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dns_step": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
+                           C.POINTER(dns_step_info)]),
+    "dns_integrate": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_double, C.c_double, C.c_double,
+                                C.c_int, C.POINTER(dns_step_info)]),
+    "dns_enqueue_attempts": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double,
+                                       C.c_double, C.c_double]),
+    "dns_get_info": (C.c_int, [C.c_void_p, C.POINTER(dns_step_info)]),
+    "dns_diagnostics": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double)]),
+    "dns_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
+    "dns_profile_count": (C.c_int, [C.c_void_p]),
+    "dns_profile_get": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_longlong),
+                                  C.POINTER(C.c_double)]),
+    "dns_query": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_size_t)]),
+}
+
+
+def load(path: Optional[str] = None):
+    """Load libdns.so (fails loudly if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"libdns.so not found at {p}; build it with "
+                          "`python -m paper_1810_10197_gb300.build`")
+    lib = C.CDLL(p)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def declared_symbols():
+    """Function names declared in include/dns.h."""
+    import re
+    txt = open(HEADER_PATH).read()
+    return sorted(set(re.findall(r"\b(dns_[a-z_]+)\s*\(", txt)))
+
+
+# ---- thin module-level wrappers with the C names ----------------------------------------
+
+def _ptr(x):
+    """Address of a torch tensor or numpy array (contiguous), or an int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _where(x):
+    """0 for device memory (a CUDA tensor), 1 for host memory."""
+    if hasattr(x, "is_cuda"):
+        return 0 if x.is_cuda else 1
+    return 1
+
+
+class Dns:
+    """One libdns context (an nx x ny x nz grid on the current CUDA device)."""
+
+    def __init__(self, nx, ny=None, nz=None, nu=0.0, precision="fp64", forcing=None,
+                 lengths=None, stream=None):
+        lib = load()
+        ny = nx if ny is None else ny
+        nz = nx if nz is None else nz
+        cfg = dns_config()
+        cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
+        if lengths is not None:
+            cfg.lx, cfg.ly, cfg.lz = (float(v) for v in lengths)
+        cfg.nu = float(nu)
+        cfg.precision = {"fp64": DNS_FP64, "fp32_mixed": DNS_FP32_MIXED}[precision] \
+            if isinstance(precision, str) else int(precision)
+        if forcing is not None:
+            cfg.forcing.kind = 1
+            cfg.forcing.kf, cfg.forcing.power = float(forcing[0]), float(forcing[1])
+        h = C.c_void_p()
+        st = lib.dns_create_ex(C.byref(cfg), C.byref(h))
+        if st != DNS_OK:
+            raise DnsError(st, "dns_create_ex")
+        self._lib = lib
+        self._h = h
+        self.shape = (nx, ny, nz)
+        self.nzh = nz // 2 + 1
+        if stream is not None:
+            self.set_stream(stream)
+
+    # lifetime
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.dns_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != DNS_OK:
+            msg = self._lib.dns_last_error(self._h)
+            raise DnsError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, an int handle, or None (legacy default stream)."""
+        h = getattr(stream, "cuda_stream", stream)
+        self._check(self._lib.dns_set_stream(self._h, C.c_void_p(h) if h else None), "dns_set_stream")
+
+    def set_state(self, uhat, t=0.0):
+        self._check(self._lib.dns_set_state(self._h, C.c_void_p(_ptr(uhat)), _where(uhat), float(t)),
+                    "dns_set_state")
+
+    def get_state(self, out=None):
+        """Current state; into `out` (device tensor or host array) or a new numpy array."""
+        if out is None:
+            out = np.empty((3,) + self.shape[:2] + (self.nzh,), dtype=np.complex128)
+        self._check(self._lib.dns_get_state(self._h, C.c_void_p(_ptr(out)), _where(out)), "dns_get_state")
+        return out
+
+    def rhs(self, uhat_dev, f_dev):
+        self._check(self._lib.dns_rhs(self._h, C.c_void_p(_ptr(uhat_dev)), C.c_void_p(_ptr(f_dev))),
+                    "dns_rhs")
+
+    def step(self, method, h, rtol=1e-6, atol=1e-6, t_end=float("inf")):
+        info = dns_step_info()
+        m = METHODS[method] if isinstance(method, str) else int(method)
+        self._check(self._lib.dns_step(self._h, m, float(h), float(rtol), float(atol), float(t_end),
+                                       C.byref(info)), "dns_step")
+        return info
+
+    def integrate(self, t_end, method, rtol=1e-6, atol=1e-6, h0=0.0, max_rejects=0, check=True):
+        info = dns_step_info()
+        m = METHODS[method] if isinstance(method, str) else int(method)
+        st = self._lib.dns_integrate(self._h, float(t_end), m, float(rtol), float(atol), float(h0),
+                                     int(max_rejects), C.byref(info))
+        if check:
+            self._check(st, "dns_integrate")
+        return info if check else (st, info)
+
+    def enqueue_attempts(self, n, method, rtol=1e-6, atol=1e-6, t_end=float("inf"), h0=0.0):
+        m = METHODS[method] if isinstance(method, str) else int(method)
+        self._check(self._lib.dns_enqueue_attempts(self._h, int(n), m, float(rtol), float(atol),
+                                                   float(t_end), float(h0)), "dns_enqueue_attempts")
+
+    def info(self):
+        info = dns_step_info()
+        self._check(self._lib.dns_get_info(self._h, C.byref(info)), "dns_get_info")
+        return info
+
+    def diagnostics(self):
+        E, O, eps = C.c_double(), C.c_double(), C.c_double()
+        self._check(self._lib.dns_diagnostics(self._h, C.byref(E), C.byref(O), C.byref(eps)),
+                    "dns_diagnostics")
+        return E.value, O.value, eps.value
+
+    def profile_enable(self, on=True):
+        self._check(self._lib.dns_profile_enable(self._h, 1 if on else 0), "dns_profile_enable")
+
+    def profile(self):
+        out = {}
+        for i in range(self._lib.dns_profile_count(self._h)):
+            name, n, ms = C.c_char_p(), C.c_longlong(), C.c_double()
+            self._check(self._lib.dns_profile_get(self._h, i, C.byref(name), C.byref(n), C.byref(ms)),
+                        "dns_profile_get")
+            if n.value:
+                out[name.value.decode()] = (n.value, ms.value)
+        return out
+
+    def query(self):
+        K = (C.c_int * 3)()
+        nb = C.c_size_t()
+        self._check(self._lib.dns_query(self._h, K, C.byref(nb)), "dns_query")
+        return tuple(K), nb.value
