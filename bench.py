@@ -1,0 +1,335 @@
+"""Benchmark: Taylor-Green vortex at 256^3, nu = 1/1600, FP64, Bogacki-Shampine 5(4) with
+embedded-error step control (rtol = atol = 1e-6), through the libdns C ABI.
+
+One "step" is one attempted BS5 step: stage sums, 7 right-hand-side evaluations (the 8th
+stage's derivative is carried over, first same as last), the error norm and the controller.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  `value` = right-hand-side evaluations per second over the timed steps
+(whole job: summed over ranks); `sim_time_per_gpu_s` = simulated time advanced per second.
+`--impl reference` times the FP64 CPU oracle on the same workload (each step one oracle
+right-hand-side evaluation of the same 256^3 field: a bounded sample).  Multi-GPU runs are
+independent replicas (the method has no exchange step on one field per GPU here).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sim-time/GPU-s at fixed L2 error vs FP64 oracle; RHS evals/s; % HBM roofline"
+UNIT = "RHS evals/s"
+N_GRID = 256
+NU = 1.0 / 1600.0
+TOL = 1e-6
+H0 = 0.01
+T_END = 2.0
+WORKLOAD = "taylor_green_3d_256^3_nu1/1600_bs5_adaptive_tol1e-6_to_t2"
+
+# Algorithmic (nominal) FP64 flop counts per launch of each pass, 5 n log2 n per complex
+# line of length n, 2.5 n log2 n per real line, plus the pointwise products.
+def pass_flops(n=N_GRID):
+    import math
+    K = (n - 1) // 3
+    Mx = My = 2 * K + 1
+    Mz = K + 1
+    lg = math.log2(n)
+    cl = 5 * n * lg          # complex line
+    rl = 2.5 * n * lg        # real line
+    return {
+        "p1_x_inverse_curl": 6 * My * Mz * cl,
+        "p2_y_inverse": 6 * n * Mz * cl,
+        "p3_z_c2r_cross_r2c": n * n * (9 * rl + 9 * n),
+        "p4_y_forward": 3 * n * Mz * cl,
+        "p5_x_forward_project": 3 * My * Mz * cl,
+    }
+
+
+def pass_bytes(n=N_GRID, esz=16):
+    """Algorithmic HBM bytes per launch (each pass reads its input and writes its output once)."""
+    K = (n - 1) // 3
+    M = (2 * K + 1) ** 2 * (K + 1)
+    L1 = n * (2 * K + 1) * (K + 1)
+    L2 = n * n * (K + 1)
+    return {
+        "p1_x_inverse_curl": 3 * M * 16 + 6 * L1 * esz,
+        "p2_y_inverse": 6 * L1 * esz + 6 * L2 * esz,
+        "p3_z_c2r_cross_r2c": 6 * L2 * esz + 3 * L2 * esz,
+        "p4_y_forward": 3 * L2 * esz + 3 * L1 * esz,
+        "p5_x_forward_project": 3 * L1 * esz + 3 * M * 16 * 2,
+    }
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}",
+                                          f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_sample(n_rhs=2):
+    """Oracle (FP64 numpy, one core) right-hand sides of the same 256^3 TG field."""
+    import synthetic as syn
+    from oracle import spectral as sp
+    g = sp.Grid(N_GRID, N_GRID, N_GRID)
+    uh = g.dealias(syn.taylor_green_3d_hat(N_GRID, N_GRID, N_GRID))
+    sp.rhs(g, uh, NU)
+    t0 = time.perf_counter()
+    for _ in range(n_rhs):
+        sp.rhs(g, uh, NU)
+    dt = time.perf_counter() - t0
+    return n_rhs / dt, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        cpu_sample(1)
+    v, dt = cpu_sample(args.steps)
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "grid": [N_GRID] * 3, "nu": NU, "method": "BS5_ADAPTIVE",
+                      "rtol": TOL, "atol": TOL},
+           "cpu_baseline": {"kind": "oracle", "value": v, "unit": UNIT, "cores": 1,
+                            "sample": f"{args.steps} oracle right-hand-side evaluations of the "
+                                      "256^3 TG field (numpy FP64, single thread); one BS5 "
+                                      "attempt costs 7 of them"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import synthetic as syn
+    from paper_1810_10197_gb300 import Dns, build
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    build.build()
+    stream = torch.cuda.Stream()
+    d = Dns(N_GRID, nu=NU, precision="fp64", stream=stream)
+    n = N_GRID
+    u0 = syn.taylor_green_3d_hat(n, n, n)
+    u0_dev = torch.from_numpy(u0).cuda()
+    d.set_state(u0_dev, 0.0)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up attempts (untimed)
+    d.enqueue_attempts(args.warmup, "BS5_ADAPTIVE", TOL, TOL, t_end=T_END, h0=H0)
+    i0 = d.info()
+    d.profile_enable(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    d.enqueue_attempts(args.steps, "BS5_ADAPTIVE", TOL, TOL, t_end=T_END, h0=0.0)
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    i1 = d.info()
+    prof = d.profile()
+    d.profile_enable(False)
+    n_rhs = i1.n_rhs - i0.n_rhs
+    sim = i1.t - i0.t
+    if ws > 1:
+        t = torch.tensor([ms, float(n_rhs), sim], dtype=torch.float64, device="cuda")
+        mx = t.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms_max, n_rhs_tot, sim_tot = mx[0].item(), sm[1].item(), sm[2].item()
+    else:
+        ms_max, n_rhs_tot, sim_tot = ms, float(n_rhs), sim
+    value = n_rhs_tot / (ms_max * 1e-3)
+
+    # ---- end to end through the public API with host buffers (pinned) -------------------
+    host_in = torch.from_numpy(u0).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    d.set_state(host_in, 0.0)
+    info = d.step("BS5_ADAPTIVE", H0, TOL, TOL, T_END)
+    h = info.h_next
+    t_sim = info.t
+    d.get_state(host_out)
+    e2e_steps = max(1, min(args.steps, 4))
+    barrier()
+    t0 = time.perf_counter()
+    e2e_rhs = 0
+    for _ in range(e2e_steps):
+        d.set_state(host_out, t_sim)             # H2D of this step's input
+        info = d.step("BS5_ADAPTIVE", h, TOL, TOL, T_END)
+        d.get_state(host_out)                    # D2H of this step's result
+        e2e_rhs += info.n_rhs
+        if info.accepted:
+            t_sim = info.t
+        h = info.h_next
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    state_bytes = host_in.numel() * host_in.element_size()
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel -------------------------------------------------
+    peaks, peak_src = load_peaks()
+    flops = pass_flops()
+    byts = pass_bytes()
+    names = list(flops)
+    dom = max(names, key=lambda k: prof.get(k, (0, 0.0))[1])
+    nl, tot_ms = prof[dom]
+    avg_s = tot_ms * 1e-3 / nl
+    fp64_peak_tflops = 1.25   # nominal FP64 rate of this part (152 SMs, FMA = 2 flops)
+    achieved = flops[dom] / avg_s / 1e12
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            traffic = json.load(fh).get(dom)
+    except Exception:
+        pass
+    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp64_peak_tflops,
+            "unit": "TFLOP/s", "frac": achieved / fp64_peak_tflops, "traffic": traffic,
+            "peak_source": "nominal FP64 (1.25 TFLOP/s); the FP64 pipe is the bound, see DESIGN",
+            "hbm_achieved_gbs": byts[dom] / avg_s / 1e9,
+            "hbm_frac_of_measured": byts[dom] / avg_s / 1e9 / peaks["hbm_gbs"],
+            "hbm_peak_source": peak_src}
+    launches = sum(v[0] for v in prof.values())
+    per_kernel = {k: {"launches": v[0], "total_ms": round(v[1], 3), "share": round(v[1] / ms, 4)}
+                  for k, v in prof.items()}
+
+    cpu = None
+    if ws == 1 and not args.no_cpu:
+        v, dt = cpu_sample(2)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "2 oracle right-hand-side evaluations of the same 256^3 TG field "
+                         f"(numpy FP64, one thread, {dt:.1f} s)"}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "grid": [n, n, n], "nu": NU, "method": "BS5_ADAPTIVE",
+                      "rtol": TOL, "atol": TOL, "h0": H0, "precision": "fp64",
+                      "l2": "inputs larger than L2 (3 GB per right-hand side)",
+                      "parallelism": f"replicas{ws}"},
+           "sim_time_per_gpu_s": sim_tot / (ms_max * 1e-3),
+           "sim_time_advanced": sim, "rhs_evals": n_rhs, "t_end_state": i1.t,
+           "accepted": i1.n_acc - i0.n_acc, "rejected": i1.n_rej - i0.n_rej,
+           "e2e": {"value": e2e_rhs / e2e_s * ws, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                   "d2h_bytes_per_step": state_bytes, "steps": e2e_steps,
+                   "note": "set_state from pinned host memory, one dns_step, get_state to host"},
+           "gpu_launches": launches,
+           "kernels": per_kernel,
+           "roofline": roof,
+           "clocks": clk,
+           "cpu_baseline": cpu}
+    print(json.dumps(out), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

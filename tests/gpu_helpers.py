@@ -30,12 +30,23 @@ def rel_max(a, b):
     return np.max(np.abs(a - b)) / (mb if mb > 0 else 1.0)
 
 
-def err_tolerance(h, ks, e, tab, eps_rhs=1e-13):
-    """Relative tolerance for the embedded error norm.
+def err_tolerance(h, ks, e, tab, u_old, u_new, atol, rtol, eps_rhs=1e-13):
+    """Relative tolerance for the embedded error norm err = max_c sqrt(mean (|e|/sc)^2).
 
-    e = h sum_j (b_j - bhat_j) k_j cancels heavily: a relative rounding error eps_rhs in each
-    k_j becomes eps_rhs * h sum_j |b_j - bhat_j| max|k_j| / max|e| in e (and in err).
+    The CUDA and oracle right-hand sides agree to eps_rhs relative to each field's largest
+    entry, so every mode of e = h sum_j (b_j - bhat_j) k_j carries an absolute error up to
+    de = eps_rhs h sum_j |b_j - bhat_j| max|k_j|, independent of the mode.  Linearising
+    err^2 = mean(|e|^2/sc^2) gives d(err)/err <= sum |e| de / sc^2 / sum |e|^2 / sc^2 for the
+    component that attains the maximum (the bound is taken over all components).
     """
-    num = h * sum(abs(float(b - bh)) * float(np.max(np.abs(k)))
-                  for b, bh, k in zip(tab.b, tab.bhat, ks))
-    return eps_rhs * num / float(np.max(np.abs(e)))
+    de = eps_rhs * h * sum(abs(float(b - bh)) * float(np.max(np.abs(k)))
+                           for b, bh, k in zip(tab.b, tab.bhat, ks))
+    sc = atol + rtol * np.maximum(np.abs(u_old), np.abs(u_new))
+    ae = np.abs(e)
+    rel = 0.0
+    for c in range(e.shape[0]):
+        num = float(np.sum(ae[c] * de / sc[c] ** 2))
+        den = float(np.sum(ae[c] ** 2 / sc[c] ** 2))
+        if den > 0:
+            rel = max(rel, num / den)
+    return rel + 1e-15

@@ -43,7 +43,7 @@ def test_single_bs5_attempt_matches_oracle():
     fac = rk.controller_factor(err, False)
     d = make(shape, uh, nu)
     info = d.step("BS5_ADAPTIVE", h, 1e-6, 1e-6)
-    tol = err_tolerance(h, ks, e, rk.BS5)
+    tol = err_tolerance(h, ks, e, rk.BS5, uh, u_new, 1e-6, 1e-6)
     assert abs(info.err - err) < tol * err
     assert bool(info.accepted) == (err <= 1)
     assert info.n_rhs == 8
@@ -64,7 +64,7 @@ def test_rejected_attempt_keeps_state_and_shrinks_step():
     d = make(shape, uh, nu)
     info = d.step("BS5_ADAPTIVE", h, 1e-9, 1e-9)
     assert not info.accepted and info.n_rej == 1 and info.t == 0.0
-    tol = err_tolerance(h, ks, e, rk.BS5)
+    tol = err_tolerance(h, ks, e, rk.BS5, uh, u_new, 1e-9, 1e-9)
     assert abs(info.err - err) < tol * err
     fac = rk.controller_factor(err, False)
     assert abs(info.h_next - h * fac) < (tol / 5 + 1e-15) * h * fac
