@@ -240,3 +240,37 @@ def test_taylor_green_2d_decays_as_exp_minus_2_nu_t(method, h0, tol):
     assert res.t == T
     rel = np.max(np.abs(res.u - math.exp(-2 * nu * T) * u0)) / np.max(np.abs(u0))
     assert rel < 1e-9
+
+
+def stability_poly(tab, weights, z):
+    """R(z) = 1 + sum_k w^T A^(k-1) 1 z^k, evaluated with exact fractions then rounded."""
+    s = tab.stages
+    A = [[(tab.A[i][j] if j < len(tab.A[i]) else Fr(0)) for j in range(s)] for i in range(s)]
+    v = [Fr(1)] * s
+    zf = Fr(z)
+    r, zk = Fr(1), Fr(1)
+    for _ in range(s):
+        zk *= zf
+        r += sum(w * x for w, x in zip(weights, v)) * zk
+        v = [sum(A[i][j] * v[j] for j in range(s)) for i in range(s)]
+    return r
+
+
+@pytest.mark.parametrize("nu,h,tol", [(0.5, 0.5, 1e-4), (0.2, 0.9, 1e-6), (1.0, 0.3, 1e-3)])
+def test_error_norm_closed_form_tg2d(nu, h, tol):
+    # For the z-independent TG flow f = -2 nu u exactly, so one BS5 attempt gives
+    # u_new = R_b(z) u and e = (R_b(z) - R_bhat(z)) u with z = -2 nu h.  Each velocity
+    # component has 4 stored modes of modulus a = N^3/4; the third component is zero, so
+    # err = |dR| a / (atol + rtol max(a, |R_b| a)) * sqrt(4 / (N^2 (N/2+1))).
+    n = 16
+    g = sp.Grid(n, n, n)
+    u0 = syn.taylor_green_2d_hat(n, n, n)
+    u_new, e, _ = rk.rk_attempt(lambda y: sp.rhs(g, y, nu), u0, h, rk.BS5)
+    err = rk.error_norm(u0, u_new, e, tol, tol, g.nmodes_half)
+    z = -2 * nu * h
+    Rb = float(stability_poly(rk.BS5, rk.BS5.b, z))
+    dR = float(stability_poly(rk.BS5, rk.BS5.b, z) - stability_poly(rk.BS5, rk.BS5.bhat, z))
+    a = n ** 3 / 4.0
+    expect = abs(dR) * a / (tol + tol * max(a, abs(Rb) * a)) * math.sqrt(4.0 / g.nmodes_half)
+    assert abs(err - expect) < 1e-9 * expect
+    assert np.max(np.abs(u_new - Rb * u0)) < 1e-13 * a
