@@ -157,6 +157,27 @@ dns_status dns_profile_get(dns_ctx* ctx, int i, const char** name, long long* la
 /* Grid facts: retained cut-offs K[3] and the number of device bytes the context holds. */
 dns_status dns_query(const dns_ctx* ctx, int* K3, size_t* device_bytes);
 
+/* The right-hand side of dns_rhs (same layout, same result) for small grids, without a
+ * context and without allocating any device memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc -- for instance a host program
+ * that hands out all device memory through its own pool or budget, or code on a
+ * latency-critical path where cudaMalloc/cudaFree would synchronise the device.
+ *
+ *   nx, ny, nz  each in {8, 12, 16, 24, 32} (domain [0, 2 pi)^3, no forcing, FP64);
+ *               larger sizes return DNS_ERR_UNSUPPORTED before any CUDA call.
+ *   nu          viscosity (>= 0);  uhat_dev, f_dev: device pointers as for dns_rhs (no alias).
+ *   stream      cudaStream_t as void* (NULL = legacy default stream); asynchronous.
+ *
+ * Work space: one static __device__ array of about 2.3 MB inside libdns, held by every GPU
+ * that loads the library until the process exits.  The first call on a device looks up its
+ * address (cudaGetSymbolAddress, with that device current); make that first call before any
+ * stream capture.  All calls on a device share the array and each call rewrites every part
+ * it reads, so no state carries over; calls that overlap on the GPU (different streams, or
+ * different host threads) race on it and must be serialised by the caller.
+ * Returns DNS_ERR_ARG for bad pointers or nu, DNS_ERR_CUDA if a launch fails. */
+dns_status dns_rhs_noalloc(int nx, int ny, int nz, double nu, const void* uhat_dev, void* f_dev,
+                           void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,6 +78,8 @@ _SIGS = {
     "dns_profile_get": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_longlong),
                                   C.POINTER(C.c_double)]),
     "dns_query": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_size_t)]),
+    "dns_rhs_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p,
+                                  C.c_void_p]),
 }
 
 
@@ -252,3 +254,11 @@ class Dns:
         nb = C.c_size_t()
         self._check(self._lib.dns_query(self._h, K, C.byref(nb)), "dns_query")
         return tuple(K), nb.value
+
+
+def dns_rhs_noalloc(nx, ny, nz, nu, uhat_dev, f_dev, stream=None):
+    """dns_rhs without a context or device allocation (grids up to 32^3); returns the status."""
+    lib = load()
+    h = getattr(stream, "cuda_stream", stream)
+    return lib.dns_rhs_noalloc(int(nx), int(ny), int(nz), float(nu), C.c_void_p(_ptr(uhat_dev)),
+                               C.c_void_p(_ptr(f_dev)), C.c_void_p(h) if h else None)
