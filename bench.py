@@ -36,10 +36,15 @@ TOL = 1e-6
 H0 = 0.01
 T_END = 2.0
 WORKLOAD = "taylor_green_3d_256^3_nu1/1600_bs5_adaptive_tol1e-6_to_t2"
+# other workloads of the same path (parity cases; --flow/--grid/--precision select them)
+FLOWS = {
+    "tg": dict(nu=1.0 / 1600.0, forcing=None),
+    "hit": dict(nu=1e-3, forcing=(2.5, None)),
+}
 
 # Algorithmic (nominal) FP64 flop counts per launch of each pass, 5 n log2 n per complex
 # line of length n, 2.5 n log2 n per real line, plus the pointwise products.
-def pass_flops(n=N_GRID):
+def pass_flops(n):
     import math
     K = (n - 1) // 3
     Mx = My = 2 * K + 1
@@ -56,7 +61,7 @@ def pass_flops(n=N_GRID):
     }
 
 
-def pass_bytes(n=N_GRID, esz=16):
+def pass_bytes(n, esz=16):
     """Algorithmic HBM bytes per launch (each pass reads its input and writes its output once)."""
     K = (n - 1) // 3
     M = (2 * K + 1) ** 2 * (K + 1)
@@ -142,13 +147,14 @@ def dist_env():
     return ws, rank, local
 
 
-def cpu_sample(n_rhs=2):
+def cpu_sample(n_rhs=2, n_warm=1):
     """Oracle (FP64 numpy, one core) right-hand sides of the same 256^3 TG field."""
     import synthetic as syn
     from oracle import spectral as sp
     g = sp.Grid(N_GRID, N_GRID, N_GRID)
     uh = g.dealias(syn.taylor_green_3d_hat(N_GRID, N_GRID, N_GRID))
-    sp.rhs(g, uh, NU)
+    for _ in range(n_warm):
+        sp.rhs(g, uh, NU)
     t0 = time.perf_counter()
     for _ in range(n_rhs):
         sp.rhs(g, uh, NU)
@@ -160,9 +166,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    for _ in range(args.warmup):
-        cpu_sample(1)
-    v, dt = cpu_sample(args.steps)
+    v, dt = cpu_sample(args.steps, args.warmup)
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -178,11 +182,28 @@ def run_reference(args):
     return 0
 
 
+def workload_name(args):
+    if args.flow == "tg" and args.grid == N_GRID and args.precision == "fp64":
+        base = WORKLOAD
+    else:
+        nu = FLOWS[args.flow]["nu"]
+        base = (f"{'taylor_green_3d' if args.flow == 'tg' else 'hit_forced_k0_4'}_{args.grid}^3_"
+                f"nu{nu:g}_bs5_adaptive_tol1e-6_{args.precision}")
+    return base if args.mode == "step" else base + "_rhs_only"
+
+
+def make_field(args):
+    import synthetic as syn
+    n = args.grid
+    if args.flow == "tg":
+        return syn.taylor_green_3d_hat(n, n, n)
+    return syn.random_solenoidal_hat(n, n, n, seed=1, k0=4.0)
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
 
-    import synthetic as syn
     from paper_1810_10197_gb300 import Dns, build
 
     ws, rank, local = dist_env()
@@ -191,10 +212,19 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     build.build()
     stream = torch.cuda.Stream()
-    d = Dns(N_GRID, nu=NU, precision="fp64", stream=stream)
-    n = N_GRID
-    u0 = syn.taylor_green_3d_hat(n, n, n)
+    n = args.grid
+    nu = FLOWS[args.flow]["nu"]
+    u0 = make_field(args)
     u0_dev = torch.from_numpy(u0).cuda()
+    forcing = None
+    if args.flow == "hit":
+        # constant power equal to the initial dissipation rate (input recipe)
+        d0 = Dns(n, nu=nu, precision="fp64", stream=stream)
+        d0.set_state(u0_dev, 0.0)
+        _, _, eps0 = d0.diagnostics()
+        d0.close()
+        forcing = (FLOWS["hit"]["forcing"][0], eps0)
+    d = Dns(n, nu=nu, precision=args.precision, forcing=forcing, stream=stream)
     d.set_state(u0_dev, 0.0)
 
     def barrier():
@@ -202,8 +232,13 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # warm-up attempts (untimed)
-    d.enqueue_attempts(args.warmup, "BS5_ADAPTIVE", TOL, TOL, t_end=T_END, h0=H0)
+    f_dev = torch.empty_like(u0_dev)
+    if args.mode == "rhs":
+        for _ in range(args.warmup):
+            d.rhs(u0_dev, f_dev)
+    else:
+        # warm-up attempts (untimed)
+        d.enqueue_attempts(args.warmup, "BS5_ADAPTIVE", TOL, TOL, t_end=T_END, h0=H0)
     i0 = d.info()
     d.profile_enable(True)
     clocks = ClockSampler(local)
@@ -212,7 +247,11 @@ def run_gpu(args):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    d.enqueue_attempts(args.steps, "BS5_ADAPTIVE", TOL, TOL, t_end=T_END, h0=0.0)
+    if args.mode == "rhs":
+        for _ in range(args.steps):
+            d.rhs(u0_dev, f_dev)
+    else:
+        d.enqueue_attempts(args.steps, "BS5_ADAPTIVE", TOL, TOL, t_end=T_END, h0=0.0)
     ev1.record(stream)
     barrier()
     ms = ev0.elapsed_time(ev1)
@@ -220,8 +259,8 @@ def run_gpu(args):
     i1 = d.info()
     prof = d.profile()
     d.profile_enable(False)
-    n_rhs = i1.n_rhs - i0.n_rhs
-    sim = i1.t - i0.t
+    n_rhs = (i1.n_rhs - i0.n_rhs) if args.mode == "step" else args.steps
+    sim = (i1.t - i0.t) if args.mode == "step" else 0.0
     if ws > 1:
         t = torch.tensor([ms, float(n_rhs), sim], dtype=torch.float64, device="cuda")
         mx = t.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
@@ -232,28 +271,46 @@ def run_gpu(args):
     value = n_rhs_tot / (ms_max * 1e-3)
 
     # ---- end to end through the public API with host buffers (pinned) -------------------
-    host_in = torch.from_numpy(u0).pin_memory()
-    host_out = torch.empty_like(host_in).pin_memory()
-    d.set_state(host_in, 0.0)
-    info = d.step("BS5_ADAPTIVE", H0, TOL, TOL, T_END)
-    h = info.h_next
-    t_sim = info.t
-    d.get_state(host_out)
-    e2e_steps = max(1, min(args.steps, 4))
-    barrier()
-    t0 = time.perf_counter()
-    e2e_rhs = 0
-    for _ in range(e2e_steps):
-        d.set_state(host_out, t_sim)             # H2D of this step's input
-        info = d.step("BS5_ADAPTIVE", h, TOL, TOL, T_END)
-        d.get_state(host_out)                    # D2H of this step's result
-        e2e_rhs += info.n_rhs
-        if info.accepted:
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.from_numpy(u0).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        state_bytes = host_in.numel() * host_in.element_size()
+        e2e_steps = max(1, min(args.steps, 4))
+        if args.mode == "rhs":
+            dev_in = torch.empty_like(u0_dev)
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                dev_in.copy_(host_in, non_blocking=True)      # H2D of this step's input
+                d.rhs(dev_in, f_dev)
+                host_out.copy_(f_dev, non_blocking=True)       # D2H of this step's result
+                torch.cuda.synchronize()
+            e2e_s = time.perf_counter() - t0
+            e2e_rhs = e2e_steps
+            note = "H2D copy from pinned host memory, one dns_rhs, D2H copy of f"
+        else:
+            d.set_state(host_in, 0.0)
+            info = d.step("BS5_ADAPTIVE", H0, TOL, TOL, T_END)
+            h = info.h_next
             t_sim = info.t
-        h = info.h_next
-    barrier()
-    e2e_s = time.perf_counter() - t0
-    state_bytes = host_in.numel() * host_in.element_size()
+            d.get_state(host_out)
+            barrier()
+            t0 = time.perf_counter()
+            e2e_rhs = 0
+            for _ in range(e2e_steps):
+                d.set_state(host_out, t_sim)             # H2D of this step's input
+                info = d.step("BS5_ADAPTIVE", h, TOL, TOL, T_END)
+                d.get_state(host_out)                    # D2H of this step's result
+                e2e_rhs += info.n_rhs
+                if info.accepted:
+                    t_sim = info.t
+                h = info.h_next
+            barrier()
+            e2e_s = time.perf_counter() - t0
+            note = "set_state from pinned host memory, one dns_step, get_state to host"
+        e2e = {"value": e2e_rhs / e2e_s * ws, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+               "d2h_bytes_per_step": state_bytes, "steps": e2e_steps, "note": note}
 
     if rank != 0:
         if ws > 1:
@@ -262,49 +319,60 @@ def run_gpu(args):
 
     # ---- roofline of the dominant kernel -------------------------------------------------
     peaks, peak_src = load_peaks()
-    flops = pass_flops()
-    byts = pass_bytes()
+    fp32 = args.precision == "fp32_mixed"
+    flops = pass_flops(n)
+    byts = pass_bytes(n, esz=8 if fp32 else 16)
     names = list(flops)
     dom = max(names, key=lambda k: prof.get(k, (0, 0.0))[1])
     nl, tot_ms = prof[dom]
     avg_s = tot_ms * 1e-3 / nl
-    fp64_peak_tflops = 1.25   # nominal FP64 rate of this part (152 SMs, FMA = 2 flops)
-    achieved = flops[dom] / avg_s / 1e12
     traffic = None
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
-            traffic = json.load(fh).get(dom)
+            traffic = json.load(fh).get(f"{args.precision}_{n}", {}).get(dom)
     except Exception:
         pass
-    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp64_peak_tflops,
-            "unit": "TFLOP/s", "frac": achieved / fp64_peak_tflops, "traffic": traffic,
-            "peak_source": "nominal FP64 (1.25 TFLOP/s); the FP64 pipe is the bound, see DESIGN",
-            "hbm_achieved_gbs": byts[dom] / avg_s / 1e9,
-            "hbm_frac_of_measured": byts[dom] / avg_s / 1e9 / peaks["hbm_gbs"],
-            "hbm_peak_source": peak_src}
+    hbm_gbs = byts[dom] / avg_s / 1e9
+    if fp32:
+        roof = {"bound": "hbm", "kernel": dom, "achieved": hbm_gbs, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": hbm_gbs / peaks["hbm_gbs"], "traffic": traffic,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                "flops_achieved_tflops": flops[dom] / avg_s / 1e12}
+    else:
+        fp64_peak_tflops = 1.25   # nominal FP64 rate of this part (FMA = 2 flops)
+        achieved = flops[dom] / avg_s / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp64_peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / fp64_peak_tflops, "traffic": traffic,
+                "peak_source": "nominal FP64 rate (1.25 TFLOP/s); the FP64 pipe bounds these passes",
+                "hbm_achieved_gbs": hbm_gbs, "hbm_frac_of_measured": hbm_gbs / peaks["hbm_gbs"],
+                "hbm_peak_source": peak_src}
     launches = sum(v[0] for v in prof.values())
-    per_kernel = {k: {"launches": v[0], "total_ms": round(v[1], 3), "share": round(v[1] / ms, 4)}
+    per_kernel = {k: {"launches": v[0], "total_ms": round(v[1], 3), "share": round(v[1] / ms, 4),
+                      "avg_ms": round(v[1] / max(v[0], 1), 4)}
                   for k, v in prof.items()}
-
+    rhs_bytes = sum(byts.values())
     cpu = None
     if ws == 1 and not args.no_cpu:
         v, dt = cpu_sample(2)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "2 oracle right-hand-side evaluations of the same 256^3 TG field "
+               "sample": "2 oracle right-hand-side evaluations of the 256^3 TG field "
                          f"(numpy FP64, one thread, {dt:.1f} s)"}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "grid": [n, n, n], "nu": NU, "method": "BS5_ADAPTIVE",
-                      "rtol": TOL, "atol": TOL, "h0": H0, "precision": "fp64",
-                      "l2": "inputs larger than L2 (3 GB per right-hand side)",
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if fp32 else "f64",
+           "data": "synthetic",
+           "config": {"workload": workload_name(args), "grid": [n, n, n], "nu": nu,
+                      "method": "BS5_ADAPTIVE" if args.mode == "step" else "rhs",
+                      "rtol": TOL, "atol": TOL, "h0": H0, "precision": args.precision,
+                      "forcing": forcing,
+                      "l2": "inputs larger than L2 (per right-hand side: "
+                            f"{rhs_bytes / 1e9:.2f} GB algorithmic traffic)",
                       "parallelism": f"replicas{ws}"},
            "sim_time_per_gpu_s": sim_tot / (ms_max * 1e-3),
            "sim_time_advanced": sim, "rhs_evals": n_rhs, "t_end_state": i1.t,
            "accepted": i1.n_acc - i0.n_acc, "rejected": i1.n_rej - i0.n_rej,
-           "e2e": {"value": e2e_rhs / e2e_s * ws, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
-                   "d2h_bytes_per_step": state_bytes, "steps": e2e_steps,
-                   "note": "set_state from pinned host memory, one dns_step, get_state to host"},
+           "rhs_hbm_frac_of_measured": rhs_bytes * value / ws / 1e9 / peaks["hbm_gbs"],
+           "e2e": e2e,
            "gpu_launches": launches,
            "kernels": per_kernel,
            "roofline": roof,
@@ -323,6 +391,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--grid", type=int, default=N_GRID)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_mixed"])
+    ap.add_argument("--flow", default="tg", choices=["tg", "hit"])
+    ap.add_argument("--mode", default="step", choices=["step", "rhs"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
