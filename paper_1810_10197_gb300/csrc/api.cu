@@ -151,21 +151,25 @@ dns_status alloc(dns_ctx* c, void** p, size_t bytes) {
   return DNS_OK;
 }
 
-// twiddle table exp(-2 pi i m / n), m < n, rounded once from long double
-dns_status make_twiddles(dns_ctx* c, int n, void** out) {
+// twiddle table of one axis (layout: axis_twiddle_turns), each entry rounded once from
+// long double
+dns_status make_twiddles(dns_ctx* c, int n, bool zaxis, void** out) {
   const bool f32 = c->precision == DNS_FP32_MIXED;
   const size_t esz = f32 ? sizeof(float2) : sizeof(double2);
-  std::vector<unsigned char> host(n * esz);
+  const int cnt = std::max(1, axis_twiddle_count(n, zaxis));
+  std::vector<unsigned char> host(cnt * esz, 0);
   const long double twopi = 6.283185307179586476925286766559005768L;
-  for (int m = 0; m < n; ++m) {
-    const long double ang = twopi * (long double)m / (long double)n;
+  for (int m = 0; m < axis_twiddle_count(n, zaxis); ++m) {
+    int num = 0, den = 1;
+    axis_twiddle_turns(n, zaxis, m, &num, &den);
+    const long double ang = twopi * (long double)num / (long double)den;
     const long double cr = cosl(ang), ci = -sinl(ang);
     if (f32) reinterpret_cast<float2*>(host.data())[m] = make_float2((float)cr, (float)ci);
     else reinterpret_cast<double2*>(host.data())[m] = make_double2((double)cr, (double)ci);
   }
-  dns_status s = alloc(c, out, n * esz);
+  dns_status s = alloc(c, out, cnt * esz);
   if (s != DNS_OK) return s;
-  CK(cudaMemcpy(*out, host.data(), n * esz, cudaMemcpyHostToDevice), "twiddle upload");
+  CK(cudaMemcpy(*out, host.data(), cnt * esz, cudaMemcpyHostToDevice), "twiddle upload");
   return DNS_OK;
 }
 
@@ -361,9 +365,9 @@ dns_status dns_create_ex(const dns_config* cfg, dns_ctx** out) {
   A(&c->bufA, nA * esz); A(&c->bufB, nB * esz);
   A((void**)&c->ctrl, sizeof(DnsCtrl)); A((void**)&c->ctrl_rhs, sizeof(DnsCtrl));
   A((void**)&c->partials, (size_t)kRedBlocks * 3 * sizeof(double));
-  if (s == DNS_OK) s = make_twiddles(c, g.nx, &c->tw[0]);
-  if (s == DNS_OK) s = make_twiddles(c, g.ny, &c->tw[1]);
-  if (s == DNS_OK) s = make_twiddles(c, g.nz, &c->tw[2]);
+  if (s == DNS_OK) s = make_twiddles(c, g.nx, false, &c->tw[0]);
+  if (s == DNS_OK) s = make_twiddles(c, g.ny, false, &c->tw[1]);
+  if (s == DNS_OK) s = make_twiddles(c, g.nz, true, &c->tw[2]);
   if (s == DNS_OK && cudaMallocHost((void**)&c->host_ctrl, sizeof(DnsCtrl)) != cudaSuccess) s = DNS_ERR_OOM;
   if (s == DNS_OK && cudaMallocHost((void**)&c->host_partials, (size_t)kRedBlocks * 3 * sizeof(double)) != cudaSuccess)
     s = DNS_ERR_OOM;

@@ -31,6 +31,37 @@ template <int S, typename V> __device__ __forceinline__ V mul_si(V a) {
 template <typename V> __device__ __forceinline__ V cscale(V a, decltype(V::x) s) { return mk<V>(a.x * s, a.y * s); }
 template <typename V> __device__ __forceinline__ V cconj(V a) { return mk<V>(a.x, -a.y); }
 
+// Conversions between FP64 and FP32 with integer bit arithmetic.  On this part FP64<->FP32
+// conversion instructions issue on the FP64 pipe (1/64 of the FP32 rate); the mixed-precision
+// passes convert every mode, so they use these instead.
+//   d2f_bits: round to nearest (ties away from zero), |x| < 2^-126 flushes to signed zero,
+//             overflow gives inf, NaN stays NaN.
+//   f2d_bits: exact; FP32 subnormals flush to signed zero; inf/NaN preserved.
+__device__ __forceinline__ float d2f_bits(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned s = hi & 0x80000000u, a = hi & 0x7fffffffu;
+  if (a < (897u << 20)) return __uint_as_float(s);
+  if (a >= (1151u << 20)) {
+    const bool nan = a > 0x7ff00000u || (a == 0x7ff00000u && lo != 0u);
+    return __uint_as_float(s | 0x7f800000u | (nan ? 0x400000u : 0u));
+  }
+  unsigned b = ((a - (896u << 20)) << 3) | (lo >> 29);
+  b += (lo >> 28) & 1u;
+  return __uint_as_float(s | b);
+}
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned s = b & 0x80000000u, e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+  if (e == 0u) return __hiloint2double((int)s, 0);
+  const unsigned eh = (e == 0xffu) ? 0x7ffu : e + 896u;
+  return __hiloint2double((int)(s | (eh << 20) | (m >> 3)), (int)(m << 29));
+}
+template <typename T> __device__ __forceinline__ T from_f64(double x);
+template <> __device__ __forceinline__ double from_f64<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_f64<float>(double x) { return d2f_bits(x); }
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f2d_bits(x); }
+
 // Grid geometry shared by every kernel.  Retained ("compact") spectral arrays are
 // [3][Mx][My][Mz] with Mx = 2Kx+1 (kx = i for i <= Kx, i - Mx above), Mz = Kz+1.
 struct Geom {
@@ -42,6 +73,8 @@ struct Geom {
   double sx, sy, sz;    // 2 pi / L per axis
   double inv_n3;        // 1 / (nx ny nz)
   double nmodes_half;   // nx ny (nz/2+1), divisor of the error norm
+  int nc;               // state components: 3 (velocity) or 4 (velocity, density)
+  int bouss;            // Boussinesq form (Section 3.2)
 };
 
 __host__ __device__ __forceinline__ int signed_mode(int i, int K, int Mc) { return i <= K ? i : i - Mc; }
@@ -62,7 +95,7 @@ struct DnsCtrl {
   double2* kk[2];
   double2* kfix[9];     // fixed stage buffers k_2..k_7 (index = stage number)
   double t, t_end, h, h_try, err, rtol, atol;
-  double errc[3];
+  double errc[4];
   double forcing_coef;  // power / (2 E_f) of the current stage input
   int method;
   int parity;

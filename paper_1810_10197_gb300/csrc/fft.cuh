@@ -3,7 +3,7 @@
 //
 // A CTA holds several lines of length N in shared memory; G threads cooperate on one line.
 // Stage s (radix R, NS = product of the earlier radices) reads R elements of butterfly j at
-// stride N/R, applies twiddles W_N^{(j mod NS) r N/(NS R)}, does an R-point DFT in registers
+// stride N/R, applies twiddles W_{NS R}^{(j mod NS) r}, does an R-point DFT in registers
 // and writes them to (j - j mod NS) R + j mod NS + r NS.  All reads of a stage finish
 // (barrier) before any write, so one buffer suffices.  SIGN = -1 forward, +1 inverse
 // (unnormalised both ways).
@@ -13,26 +13,73 @@
 
 namespace dns {
 
-template <int N> struct FftPlan;
-// S stages of radices R0, R1, R2; G threads per line.
-template <> struct FftPlan<4>   { static constexpr int S = 1, R0 = 4,  R1 = 1,  R2 = 1, G = 1;  };
-template <> struct FftPlan<6>   { static constexpr int S = 2, R0 = 2,  R1 = 3,  R2 = 1, G = 3;  };
-template <> struct FftPlan<8>   { static constexpr int S = 1, R0 = 8,  R1 = 1,  R2 = 1, G = 1;  };
-template <> struct FftPlan<12>  { static constexpr int S = 2, R0 = 4,  R1 = 3,  R2 = 1, G = 4;  };
-template <> struct FftPlan<16>  { static constexpr int S = 2, R0 = 4,  R1 = 4,  R2 = 1, G = 4;  };
-template <> struct FftPlan<24>  { static constexpr int S = 2, R0 = 8,  R1 = 3,  R2 = 1, G = 8;  };
-template <> struct FftPlan<32>  { static constexpr int S = 2, R0 = 8,  R1 = 4,  R2 = 1, G = 8;  };
-template <> struct FftPlan<48>  { static constexpr int S = 3, R0 = 4,  R1 = 4,  R2 = 3, G = 16; };
-template <> struct FftPlan<64>  { static constexpr int S = 2, R0 = 8,  R1 = 8,  R2 = 1, G = 8;  };
-template <> struct FftPlan<96>  { static constexpr int S = 3, R0 = 8,  R1 = 4,  R2 = 3, G = 16; };
-template <> struct FftPlan<128> { static constexpr int S = 2, R0 = 16, R1 = 8,  R2 = 1, G = 8;  };
-template <> struct FftPlan<256> { static constexpr int S = 2, R0 = 16, R1 = 16, R2 = 1, G = 16; };
-template <> struct FftPlan<512> { static constexpr int S = 3, R0 = 8,  R1 = 8,  R2 = 8, G = 32; };
+// Radix plans: stage radices (1 = unused) and G, the threads that share one line.  One
+// constexpr source for device templates and host-side twiddle-table construction.
+__host__ __device__ constexpr int plan_radix(int n, int s) {
+  switch (n) {
+    case 4: return s == 0 ? 4 : 1;
+    case 6: return s == 0 ? 2 : (s == 1 ? 3 : 1);
+    case 8: return s == 0 ? 8 : 1;
+    case 12: return s == 0 ? 4 : (s == 1 ? 3 : 1);
+    case 16: return s < 2 ? 4 : 1;
+    case 24: return s == 0 ? 8 : (s == 1 ? 3 : 1);
+    case 32: return s == 0 ? 8 : (s == 1 ? 4 : 1);
+    case 48: return s < 2 ? 4 : 3;
+    case 64: return s < 2 ? 8 : 1;
+    case 96: return s == 0 ? 8 : (s == 1 ? 4 : 3);
+    case 128: return s == 0 ? 16 : (s == 1 ? 8 : 1);
+    case 256: return s < 2 ? 16 : 1;
+    case 512: return 8;
+  }
+  return 0;
+}
+__host__ __device__ constexpr int plan_threads(int n) {
+  switch (n) {
+    case 4: case 8: return 1;
+    case 6: return 3;
+    case 12: case 16: return 4;
+    case 24: case 32: case 64: case 128: return 8;
+    case 48: case 96: case 256: return 16;
+    case 512: return 32;
+  }
+  return 0;
+}
+__host__ __device__ constexpr int plan_stages(int n) {
+  return plan_radix(n, 2) > 1 ? 3 : (plan_radix(n, 1) > 1 ? 2 : 1);
+}
+// product of the radices before stage s
+__host__ __device__ constexpr int plan_ns(int n, int s) {
+  return s == 0 ? 1 : (s == 1 ? plan_radix(n, 0) : plan_radix(n, 0) * plan_radix(n, 1));
+}
+// offset of stage s's twiddle table (stages >= 1 only; NS (R-1) entries each)
+__host__ __device__ constexpr int plan_tw_offset(int n, int s) {
+  return s <= 1 ? 0 : plan_ns(n, 1) * (plan_radix(n, 1) - 1);
+}
+__host__ __device__ constexpr int plan_tw_size(int n) {
+  int t = 0;
+  for (int s = 1; s < plan_stages(n); ++s) t += plan_ns(n, s) * (plan_radix(n, s) - 1);
+  return t;
+}
+
+template <int N> struct FftPlan {
+  static constexpr int S = plan_stages(N), R0 = plan_radix(N, 0), R1 = plan_radix(N, 1),
+                       R2 = plan_radix(N, 2), G = plan_threads(N);
+  static_assert(R0 * R1 * R2 == N, "unsupported line length");
+};
 
 template <int N, int s> struct StageInfo {
-  static constexpr int R = s == 0 ? FftPlan<N>::R0 : (s == 1 ? FftPlan<N>::R1 : FftPlan<N>::R2);
-  static constexpr int NS = s == 0 ? 1 : (s == 1 ? FftPlan<N>::R0 : FftPlan<N>::R0 * FftPlan<N>::R1);
+  static constexpr int R = plan_radix(N, s);
+  static constexpr int NS = plan_ns(N, s);
+  static constexpr int TWOFF = plan_tw_offset(N, s);
 };
+
+// Shared-memory layout of a line: element p sits at p + p / (128 B / element size), so
+// stride-R butterfly writes spread over all banks; LD is the (odd) line stride.
+template <typename V> __host__ __device__ constexpr int pad_shift() { return sizeof(V) == 8 ? 4 : 3; }
+template <typename V> __device__ __forceinline__ int pidx(int p) { return p + (p >> pad_shift<V>()); }
+template <typename V, int N> __host__ __device__ constexpr int line_ld() {
+  return (N + (N >> pad_shift<V>())) | 1;
+}
 
 // ---- R-point DFTs in registers: X_k = sum_r v_r exp(SIGN 2 pi i r k / R) -------------------
 
@@ -136,9 +183,11 @@ template <int SIGN, typename V> struct Dft<16, SIGN, V> {
 
 // ---- one Stockham stage and the whole line transform ------------------------------------
 
-// tw: table of N*TWS entries, tw[m] = exp(-2 pi i m / (N TWS)); the stage uses tw[m TWS].
-template <typename V, int N, int SIGN, int TWS, int s>
-__device__ __forceinline__ void fft_stage(V* x, int g, const V* tw, bool active) {
+// tws: the stage twiddle tables of this line length; stage s >= 1 holds, at
+// TWOFF + jm (R-1) + (r-1), exp(SIGN' 2 pi i jm r / (NS R)) with SIGN' = -1 (conjugated for
+// inverse transforms).
+template <typename V, int N, int SIGN, int s>
+__device__ __forceinline__ void fft_stage(V* x, int g, const V* tws, bool active) {
   constexpr int R = StageInfo<N, s>::R;
   constexpr int NS = StageInfo<N, s>::NS;
   constexpr int B = N / R;
@@ -150,12 +199,13 @@ __device__ __forceinline__ void fft_stage(V* x, int g, const V* tw, bool active)
     const int j = g + p * G;
     if (active && ((B % G == 0) || j < B)) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[p][r] = x[j + r * B];
+      for (int r = 0; r < R; ++r) v[p][r] = x[pidx<V>(j + r * B)];
       if (NS > 1) {
         const int jm = j % NS;
+        const V* t = tws + StageInfo<N, s>::TWOFF + jm * (R - 1) - 1;
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          const V w = tw[(jm * r * (N / (NS * R))) * TWS];
+          const V w = t[r];
           v[p][r] = SIGN < 0 ? cmul(v[p][r], w) : cmulc(v[p][r], w);
         }
       }
@@ -170,20 +220,20 @@ __device__ __forceinline__ void fft_stage(V* x, int g, const V* tw, bool active)
       const int jm = j % NS;
       const int base = (j - jm) * R + jm;
 #pragma unroll
-      for (int r = 0; r < R; ++r) x[base + r * NS] = v[p][r];
+      for (int r = 0; r < R; ++r) x[pidx<V>(base + r * NS)] = v[p][r];
     }
   }
   __syncthreads();
 }
 
-// Transform the line at x (contiguous, length N) with G = FftPlan<N>::G threads (g = 0..G-1).
-// Every thread of the CTA must call this (it contains barriers); the caller syncs before.
-// Threads with active = false only take part in the barriers.
-template <typename V, int N, int SIGN, int TWS>
-__device__ __forceinline__ void line_fft(V* x, int g, const V* tw, bool active = true) {
-  fft_stage<V, N, SIGN, TWS, 0>(x, g, tw, active);
-  if constexpr (FftPlan<N>::S > 1) fft_stage<V, N, SIGN, TWS, 1>(x, g, tw, active);
-  if constexpr (FftPlan<N>::S > 2) fft_stage<V, N, SIGN, TWS, 2>(x, g, tw, active);
+// Transform the line at x (length N, padded layout) with G = FftPlan<N>::G threads
+// (g = 0..G-1).  Every thread of the CTA must call this (it contains barriers); the caller
+// syncs before.  Threads with active = false only take part in the barriers.
+template <typename V, int N, int SIGN>
+__device__ __forceinline__ void line_fft(V* x, int g, const V* tws, bool active = true) {
+  fft_stage<V, N, SIGN, 0>(x, g, tws, active);
+  if constexpr (FftPlan<N>::S > 1) fft_stage<V, N, SIGN, 1>(x, g, tws, active);
+  if constexpr (FftPlan<N>::S > 2) fft_stage<V, N, SIGN, 2>(x, g, tws, active);
 }
 
 }  // namespace dns

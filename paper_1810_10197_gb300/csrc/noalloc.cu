@@ -20,7 +20,7 @@ constexpr int kNaMz = kNaK + 1;
 constexpr long long kNaCompact = 3LL * kNaMxy * kNaMxy * kNaMz;                  // double2
 constexpr long long kNaBufA = 6LL * kNaMaxN * kNaMxy * kNaMz;                     // >= 3 nx ny Mz
 constexpr long long kNaBufB = 6LL * kNaMaxN * kNaMaxN * kNaMz;                    // >= 3 nx My Mz
-constexpr long long kNaTw = 3LL * kNaMaxN;
+constexpr long long kNaTw = 3LL * kNaMaxN;   // >= twiddle_count_z(32) = 17 + 15 and xy counts
 constexpr long long kNaCtrl = (sizeof(DnsCtrl) + sizeof(double2) - 1) / sizeof(double2);
 // layout in double2 units: in | out | bufA | bufB | tw[3][32] | ctrl
 constexpr long long kOffIn = 0, kOffOut = kOffIn + kNaCompact, kOffA = kOffOut + kNaCompact;
@@ -55,9 +55,12 @@ __global__ void k_na_setup(double2* base, int nx, int ny, int nz) {
   }
   const int n3[3] = {nx, ny, nz};
   for (int a = 0; a < 3; ++a) {
-    for (int m = threadIdx.x; m < n3[a]; m += blockDim.x) {
+    const int cnt = axis_twiddle_count(n3[a], a == 2);
+    for (int m = threadIdx.x; m < cnt; m += blockDim.x) {
+      int num = 0, den = 1;
+      axis_twiddle_turns(n3[a], a == 2, m, &num, &den);
       double s, co;
-      sincospi(2.0 * (double)m / (double)n3[a], &s, &co);
+      sincospi(2.0 * (double)num / (double)den, &s, &co);
       base[kOffTw + a * kNaMaxN + m] = make_double2(co, -s);
     }
   }

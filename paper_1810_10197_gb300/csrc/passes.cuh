@@ -30,138 +30,202 @@ struct PassArgs {
   double2* kout;         // output, compact
   const void* in;        // pass input (T complex)
   void* out;             // pass output (T complex)
-  const void* tw;        // twiddle table (T complex) for this pass's axis
+  const void* tw;        // twiddle tables (T complex) of this pass's axis, see twiddle_count
   double nu;
   double kf2;            // forcing band |kappa|^2 <= kf2 (0: no forcing)
 };
 
-template <int N> __host__ __device__ constexpr int p1_cols() { return N >= 512 ? 4 : 8; }
-template <int N> __host__ __device__ constexpr int p3_lines() { return N >= 256 ? 4 : 8; }
-constexpr int kTZ = 8;   // kz columns per CTA in the y passes
+// Column tiles: kz-contiguous columns handled per CTA in the x and y passes (128-byte rows),
+// and z lines per CTA in the z pass.
+template <typename T, int N> __host__ __device__ constexpr int p1_cols() {
+  return sizeof(T) == 4 ? (N >= 512 ? 8 : 16) : (N >= 512 ? 4 : 8);
+}
+template <typename T> __host__ __device__ constexpr int py_cols() { return sizeof(T) == 4 ? 16 : 8; }
+template <typename T, int MZ> __host__ __device__ constexpr int p3_lines() { return MZ >= 256 ? 4 : 8; }
+// z-pass line stride: lines whose threads share a half-warp (FP32) or quarter-warp (FP64)
+// start at bank offsets that the first Stockham stage's writes do not overlap.
+template <typename V, int MZ> __host__ __device__ constexpr int p3_ld() {
+  constexpr int unit = sizeof(V) == 8 ? 16 : 8;               // elements per 128 bytes
+  constexpr int base = (MZ + 1) + ((MZ + 1) >> pad_shift<V>());
+  constexpr int G = plan_threads(MZ), R0 = plan_radix(MZ, 0);
+  constexpr int res = G >= unit ? 0 : (R0 == 8 && 2 * G == unit ? unit / 4 : G);
+  return base + ((res - base % unit) % unit + unit) % unit;
+}
+// twiddle entries of a pass: x and y passes hold the stage tables of their line length n; the
+// z pass holds exp(-2 pi i k / nz) for k <= nz/2, then the stage tables of nz/2.
+__host__ __device__ constexpr int twiddle_count_xy(int n) { return plan_tw_size(n); }
+__host__ __device__ constexpr int twiddle_count_z(int nz) { return nz / 2 + 1 + plan_tw_size(nz / 2); }
+
+// Entry i of a pass's twiddle table as a fraction num/den of a full turn: the value is
+// exp(-2 pi i num/den).  Stage tables of line length L: stage s >= 1 stores (jm, r) at
+// offset + jm (R-1) + (r-1) with angle jm r / (NS R).
+__host__ __device__ inline void stage_twiddle_turns(int L, int idx, int* num, int* den) {
+  int off = 0;
+  for (int s = 1; s < plan_stages(L); ++s) {
+    const int R = plan_radix(L, s), NS = plan_ns(L, s), sz = NS * (R - 1);
+    if (idx < off + sz) {
+      const int q = idx - off;
+      *num = (q / (R - 1)) * (q % (R - 1) + 1);
+      *den = NS * R;
+      return;
+    }
+    off += sz;
+  }
+  *num = 0;
+  *den = 1;
+}
+__host__ __device__ inline int axis_twiddle_count(int n, bool zaxis) {
+  return zaxis ? twiddle_count_z(n) : twiddle_count_xy(n);
+}
+__host__ __device__ inline void axis_twiddle_turns(int n, bool zaxis, int i, int* num, int* den) {
+  if (!zaxis) { stage_twiddle_turns(n, i, num, den); return; }
+  if (i <= n / 2) { *num = i; *den = n; return; }
+  stage_twiddle_turns(n / 2, i - (n / 2 + 1), num, den);
+}
 
 template <typename V> __device__ __forceinline__ V zero2() { return mk<V>(0, 0); }
+
+// Visit (row, q) for row < rows, q < len: one warp per row, lanes along q (coalesced, no
+// division) when the CTA is whole warps; otherwise a flat loop.
+template <int NTH, typename F>
+__device__ __forceinline__ void for_rows(int rows, int len, F&& fn) {
+  const int tid = threadIdx.x;
+  if constexpr (NTH % 32 == 0) {
+    const int lane = tid & 31, wid = tid >> 5;
+    for (int row = wid; row < rows; row += NTH / 32)
+      for (int q = lane; q < len; q += 32) fn(row, q);
+  } else {
+    for (int i = tid; i < rows * len; i += NTH) fn(i / len, i % len);
+  }
+}
+
+template <typename V>
+__device__ __forceinline__ void copy_tw(V* dst, const V* __restrict__ src, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
 
 // ------------------------------------------------------------------------------------------
 // P1: x-inverse with the curl fused in.  grid (ceil(MyMz/TC), 2): y = 0 -> u, 1 -> omega.
 // ------------------------------------------------------------------------------------------
 template <typename T, int NX>
-__global__ void __launch_bounds__(FftPlan<NX>::G * 3 * p1_cols<NX>())
+__global__ void __launch_bounds__(FftPlan<NX>::G * 3 * p1_cols<T, NX>())
 k_p1(const PassArgs a) {
   using V = v2_t<T>;
-  constexpr int TC = p1_cols<NX>();
+  constexpr int TC = p1_cols<T, NX>();
   constexpr int G = FftPlan<NX>::G;
-  constexpr int LD = NX + 1;
+  constexpr int LD = line_ld<V, NX>();
+  constexpr int NTW = twiddle_count_xy(NX);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw = reinterpret_cast<V*>(smem_raw);
-  V* lines = tw + NX;
+  V* lines = tw + NTW;
   if (gated_off(a.ctrl, a.gate_k1)) return;
   const Geom& g = a.g;
   const double2* __restrict__ Y = resolve_in(a.y, a.ctrl, a.yslot);
   V* __restrict__ out = reinterpret_cast<V*>(a.out);
-  const V* __restrict__ twg = reinterpret_cast<const V*>(a.tw);
   const int half = blockIdx.y;
   const int col0 = blockIdx.x * TC;
   const int tid = threadIdx.x, nth = blockDim.x;
-  for (int i = tid; i < NX; i += nth) tw[i] = twg[i];
-  const int nzero = NX - g.Mx;
-  for (int i = tid; i < 3 * TC * nzero; i += nth) {
-    const int l = i / nzero, q = i - l * nzero;
-    lines[l * LD + g.Kx + 1 + q] = zero2<V>();
-  }
-  for (int i = tid; i < g.Mx * TC; i += nth) {
-    const int ix = i / TC, c = i - ix * TC, col = col0 + c;
-    double2 f0 = make_double2(0, 0), f1 = f0, f2 = f0;
-    if (col < g.MyMz) {
-      const size_t off = (size_t)ix * g.MyMz + col;
-      const double2 y0 = Y[off], y1 = Y[off + g.M], y2 = Y[off + 2 * g.M];
-      const double s = g.inv_n3;
-      if (half == 0) {
-        f0 = make_double2(y0.x * s, y0.y * s);
-        f1 = make_double2(y1.x * s, y1.y * s);
-        f2 = make_double2(y2.x * s, y2.y * s);
-      } else {
-        const int jy = col / g.Mz, kz = col - jy * g.Mz;
-        const double kx = g.sx * signed_mode(ix, g.Kx, g.Mx);
-        const double ky = g.sy * signed_mode(jy, g.Ky, g.My);
-        const double kzz = g.sz * kz;
-        // omega = i kappa x Y
-        const double cx_r = ky * y2.x - kzz * y1.x, cx_i = ky * y2.y - kzz * y1.y;
-        const double cy_r = kzz * y0.x - kx * y2.x, cy_i = kzz * y0.y - kx * y2.y;
-        const double cz_r = kx * y1.x - ky * y0.x, cz_i = kx * y1.y - ky * y0.y;
-        f0 = make_double2(-cx_i * s, cx_r * s);
-        f1 = make_double2(-cy_i * s, cy_r * s);
-        f2 = make_double2(-cz_i * s, cz_r * s);
-      }
-    }
-    const int pos = ix <= g.Kx ? ix : NX - g.Mx + ix;
-    lines[(0 * TC + c) * LD + pos] = mk<V>((T)f0.x, (T)f0.y);
-    lines[(1 * TC + c) * LD + pos] = mk<V>((T)f1.x, (T)f1.y);
-    lines[(2 * TC + c) * LD + pos] = mk<V>((T)f2.x, (T)f2.y);
+  constexpr int NTH = G * 3 * TC;
+  T* colk = reinterpret_cast<T*>(lines + 3 * TC * LD);   // ky, kz of each column
+  copy_tw(tw, reinterpret_cast<const V*>(a.tw), NTW);
+  for_rows<NTH>(3 * TC, NX - g.Mx, [&](int l, int q) { lines[l * LD + pidx<V>(g.Kx + 1 + q)] = zero2<V>(); });
+  const T s = (T)g.inv_n3;
+  const T sx = (T)g.sx, sy = (T)g.sy, sz = (T)g.sz;
+  if (tid < TC) {
+    const int col = min(col0 + tid, g.MyMz - 1);
+    const int jy = col / g.Mz, kz = col - jy * g.Mz;
+    colk[2 * tid] = sy * (T)signed_mode(jy, g.Ky, g.My);
+    colk[2 * tid + 1] = sz * (T)kz;
   }
   __syncthreads();
-  line_fft<V, NX, +1, 1>(lines + (tid / G) * LD, tid % G, tw);
+  for (int i = tid; i < g.Mx * TC; i += nth) {
+    const int ix = i / TC, c = i - ix * TC, col = col0 + c;
+    V f0 = zero2<V>(), f1 = f0, f2 = f0;
+    if (col < g.MyMz) {
+      const size_t off = (size_t)ix * g.MyMz + col;
+      const double2 d0 = Y[off], d1 = Y[off + g.M], d2 = Y[off + 2 * g.M];
+      const V y0 = mk<V>(from_f64<T>(d0.x), from_f64<T>(d0.y));
+      const V y1 = mk<V>(from_f64<T>(d1.x), from_f64<T>(d1.y));
+      const V y2 = mk<V>(from_f64<T>(d2.x), from_f64<T>(d2.y));
+      if (half == 0) {
+        f0 = cscale(y0, s); f1 = cscale(y1, s); f2 = cscale(y2, s);
+      } else {
+        const T kx = sx * (T)signed_mode(ix, g.Kx, g.Mx);
+        const T ky = colk[2 * c], kzz = colk[2 * c + 1];
+        // omega = i kappa x Y, scaled by 1/(nx ny nz)
+        const V cx = mk<V>(ky * y2.x - kzz * y1.x, ky * y2.y - kzz * y1.y);
+        const V cy = mk<V>(kzz * y0.x - kx * y2.x, kzz * y0.y - kx * y2.y);
+        const V cz = mk<V>(kx * y1.x - ky * y0.x, kx * y1.y - ky * y0.y);
+        f0 = mk<V>(-cx.y * s, cx.x * s);
+        f1 = mk<V>(-cy.y * s, cy.x * s);
+        f2 = mk<V>(-cz.y * s, cz.x * s);
+      }
+    }
+    const int pos = pidx<V>(ix <= g.Kx ? ix : NX - g.Mx + ix);
+    lines[(0 * TC + c) * LD + pos] = f0;
+    lines[(1 * TC + c) * LD + pos] = f1;
+    lines[(2 * TC + c) * LD + pos] = f2;
+  }
+  __syncthreads();
+  line_fft<V, NX, +1>(lines + (tid / G) * LD, tid % G, tw);
   for (int i = tid; i < 3 * NX * TC; i += nth) {
     const int f = i / (NX * TC), r = i - f * (NX * TC), x = r / TC, c = r - x * TC, col = col0 + c;
-    if (col < g.MyMz) out[((size_t)(half * 3 + f) * NX + x) * g.MyMz + col] = lines[(f * TC + c) * LD + x];
+    if (col < g.MyMz)
+      out[((size_t)(half * 3 + f) * NX + x) * g.MyMz + col] = lines[(f * TC + c) * LD + pidx<V>(x)];
   }
 }
 
 // ------------------------------------------------------------------------------------------
-// P2 / P4: DFT along y for one (field, x) and kTZ kz columns.  grid (ceil(Mz/kTZ), nx, nf).
+// P2 / P4: DFT along y for one (field, x) and TZ kz columns.  grid (ceil(Mz/TZ), nx, nf).
 // INVERSE: retained ky -> all y.  Forward: all y -> retained ky.
 // ------------------------------------------------------------------------------------------
 template <typename T, int NY, bool INVERSE>
-__global__ void __launch_bounds__(FftPlan<NY>::G * kTZ)
+__global__ void __launch_bounds__(FftPlan<NY>::G * py_cols<T>())
 k_py(const PassArgs a) {
   using V = v2_t<T>;
+  constexpr int TZ = py_cols<T>();
   constexpr int G = FftPlan<NY>::G;
-  constexpr int LD = NY + 1;
+  constexpr int LD = line_ld<V, NY>();
+  constexpr int NTW = twiddle_count_xy(NY);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw = reinterpret_cast<V*>(smem_raw);
-  V* lines = tw + NY;
+  V* lines = tw + NTW;
   if (gated_off(a.ctrl, a.gate_k1)) return;
   const Geom& g = a.g;
   const V* __restrict__ in = reinterpret_cast<const V*>(a.in);
   V* __restrict__ out = reinterpret_cast<V*>(a.out);
-  const V* __restrict__ twg = reinterpret_cast<const V*>(a.tw);
-  const int f = blockIdx.z, x = blockIdx.y, kz0 = blockIdx.x * kTZ;
+  const int f = blockIdx.z, x = blockIdx.y, kz0 = blockIdx.x * TZ;
   const int tid = threadIdx.x, nth = blockDim.x;
   const int Mz = g.Mz;
-  for (int i = tid; i < NY; i += nth) tw[i] = twg[i];
+  copy_tw(tw, reinterpret_cast<const V*>(a.tw), NTW);
   if (INVERSE) {
-    const int nzero = NY - g.My;
-    for (int i = tid; i < kTZ * nzero; i += nth) {
-      const int l = i / nzero, q = i - l * nzero;
-      lines[l * LD + g.Ky + 1 + q] = zero2<V>();
-    }
+    for_rows<G * TZ>(TZ, NY - g.My, [&](int l, int q) { lines[l * LD + pidx<V>(g.Ky + 1 + q)] = zero2<V>(); });
     const V* src = in + ((size_t)f * g.nx + x) * g.My * Mz;
-    for (int i = tid; i < g.My * kTZ; i += nth) {
-      const int jy = i / kTZ, c = i - jy * kTZ, kz = kz0 + c;
+    for (int i = tid; i < g.My * TZ; i += nth) {
+      const int jy = i / TZ, c = i - jy * TZ, kz = kz0 + c;
       const V v = kz < Mz ? src[(size_t)jy * Mz + kz] : zero2<V>();
-      const int pos = jy <= g.Ky ? jy : NY - g.My + jy;
-      lines[c * LD + pos] = v;
+      lines[c * LD + pidx<V>(jy <= g.Ky ? jy : NY - g.My + jy)] = v;
     }
   } else {
     const V* src = in + ((size_t)f * g.nx + x) * NY * Mz;
-    for (int i = tid; i < NY * kTZ; i += nth) {
-      const int y = i / kTZ, c = i - y * kTZ, kz = kz0 + c;
-      lines[c * LD + y] = kz < Mz ? src[(size_t)y * Mz + kz] : zero2<V>();
+    for (int i = tid; i < NY * TZ; i += nth) {
+      const int y = i / TZ, c = i - y * TZ, kz = kz0 + c;
+      lines[c * LD + pidx<V>(y)] = kz < Mz ? src[(size_t)y * Mz + kz] : zero2<V>();
     }
   }
   __syncthreads();
-  line_fft<V, NY, INVERSE ? +1 : -1, 1>(lines + (tid / G) * LD, tid % G, tw);
+  line_fft<V, NY, INVERSE ? +1 : -1>(lines + (tid / G) * LD, tid % G, tw);
   if (INVERSE) {
     V* dst = out + ((size_t)f * g.nx + x) * NY * Mz;
-    for (int i = tid; i < NY * kTZ; i += nth) {
-      const int y = i / kTZ, c = i - y * kTZ, kz = kz0 + c;
-      if (kz < Mz) dst[(size_t)y * Mz + kz] = lines[c * LD + y];
+    for (int i = tid; i < NY * TZ; i += nth) {
+      const int y = i / TZ, c = i - y * TZ, kz = kz0 + c;
+      if (kz < Mz) dst[(size_t)y * Mz + kz] = lines[c * LD + pidx<V>(y)];
     }
   } else {
     V* dst = out + ((size_t)f * g.nx + x) * g.My * Mz;
-    for (int i = tid; i < g.My * kTZ; i += nth) {
-      const int jy = i / kTZ, c = i - jy * kTZ, kz = kz0 + c;
-      const int pos = jy <= g.Ky ? jy : NY - g.My + jy;
-      if (kz < Mz) dst[(size_t)jy * Mz + kz] = lines[c * LD + pos];
+    for (int i = tid; i < g.My * TZ; i += nth) {
+      const int jy = i / TZ, c = i - jy * TZ, kz = kz0 + c;
+      if (kz < Mz) dst[(size_t)jy * Mz + kz] = lines[c * LD + pidx<V>(jy <= g.Ky ? jy : NY - g.My + jy)];
     }
   }
 }
@@ -174,39 +238,34 @@ k_py(const PassArgs a) {
 //   R2C post-step: X_k = (Z_k + conj Z_{M-k})/2 - (i/2) e^{-2 pi i k/nz} (Z_k - conj Z_{M-k})
 // ------------------------------------------------------------------------------------------
 template <typename T, int MZ>
-__global__ void __launch_bounds__(FftPlan<MZ>::G * 6 * p3_lines<MZ>())
+__global__ void __launch_bounds__(FftPlan<MZ>::G * 6 * p3_lines<T, MZ>())
 k_p3(const PassArgs a) {
   using V = v2_t<T>;
-  constexpr int TL = p3_lines<MZ>();
+  constexpr int TL = p3_lines<T, MZ>();
   constexpr int G = FftPlan<MZ>::G;
-  constexpr int LD = MZ + 1;
-  constexpr int NZ = 2 * MZ;
+  constexpr int LD = p3_ld<V, MZ>();
+  constexpr int NTW = twiddle_count_z(2 * MZ);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* tw = reinterpret_cast<V*>(smem_raw);      // NZ entries: exp(-2 pi i m / NZ)
-  V* lines = tw + NZ;                          // 6*TL lines of LD
+  V* tw = reinterpret_cast<V*>(smem_raw);      // [0, MZ]: exp(-2 pi i k / nz); then stages
+  V* tws = tw + MZ + 1;
+  V* lines = tw + NTW;                         // 6*TL lines of LD
   if (gated_off(a.ctrl, a.gate_k1)) return;
   const Geom& g = a.g;
   const V* __restrict__ in = reinterpret_cast<const V*>(a.in);
   V* __restrict__ out = reinterpret_cast<V*>(a.out);
-  const V* __restrict__ twg = reinterpret_cast<const V*>(a.tw);
   const long long nxy = (long long)g.nx * g.ny;
   const long long xy0 = (long long)blockIdx.x * TL;
   const int Mz = g.Mz;
   const int tid = threadIdx.x, nth = blockDim.x;
-  for (int i = tid; i < NZ; i += nth) tw[i] = twg[i];
-  {
-    const int nzero = MZ + 1 - Mz;   // positions Mz..MZ
-    for (int i = tid; i < 6 * TL * nzero; i += nth) {
-      const int l = i / nzero, q = i - l * nzero;
-      lines[l * LD + Mz + q] = zero2<V>();
-    }
-  }
-  for (int i = tid; i < 6 * TL * Mz; i += nth) {
-    const int f = i / (TL * Mz), r = i - f * (TL * Mz);
-    const int l = r / Mz, kz = r - l * Mz;
+  constexpr int NTH = G * 6 * TL;
+  copy_tw(tw, reinterpret_cast<const V*>(a.tw), NTW);
+  // rows (field, line): kz < Mz from memory, Mz..MZ zero
+  for_rows<NTH>(6 * TL, MZ + 1, [&](int row, int kz) {
+    const int f = row / TL, l = row - f * TL;
     const long long xy = xy0 + l;
-    lines[(f * TL + l) * LD + kz] = xy < nxy ? in[((size_t)f * nxy + xy) * Mz + kz] : zero2<V>();
-  }
+    lines[row * LD + pidx<V>(kz)] =
+        (kz < Mz && xy < nxy) ? in[((size_t)f * nxy + xy) * Mz + kz] : zero2<V>();
+  });
   __syncthreads();
   // C2R pre-step on pairs (k, MZ-k), k = 0..MZ/2
   {
@@ -215,26 +274,21 @@ k_p3(const PassArgs a) {
       const int l = i / NP, k = i - l * NP;
       V* L = lines + l * LD;
       const int m = MZ - k;
-      const V xk = L[k], xm = L[m];
-      // Z_k
-      {
-        const V s = cadd(xk, cconj(xm)), d = csub(xk, cconj(xm));
-        const V w = cconj(tw[k]);                         // e^{+2 pi i k / NZ}
-        const V zk = cadd(s, mul_si<+1>(cmul(w, d)));
-        if (k != 0 && k != m) {
-          const V s2 = cadd(xm, cconj(xk)), d2 = csub(xm, cconj(xk));
-          const V w2 = cconj(tw[m]);
-          L[m] = cadd(s2, mul_si<+1>(cmul(w2, d2)));
-        }
-        L[k] = zk;
+      const V xk = L[pidx<V>(k)], xm = L[pidx<V>(m)];
+      const V s = cadd(xk, cconj(xm)), d = csub(xk, cconj(xm));
+      const V zk = cadd(s, mul_si<+1>(cmul(cconj(tw[k]), d)));      // e^{+2 pi i k / nz}
+      if (k != 0 && k != m) {
+        const V s2 = cadd(xm, cconj(xk)), d2 = csub(xm, cconj(xk));
+        L[pidx<V>(m)] = cadd(s2, mul_si<+1>(cmul(cconj(tw[m]), d2)));
       }
+      L[pidx<V>(k)] = zk;
     }
   }
   __syncthreads();
-  line_fft<V, MZ, +1, 2>(lines + (tid / G) * LD, tid % G, tw);
+  line_fft<V, MZ, +1>(lines + (tid / G) * LD, tid % G, tws);
   // u x omega on both packed halves (real part: even z, imaginary part: odd z)
   for (int i = tid; i < TL * MZ; i += nth) {
-    const int l = i / MZ, n = i - l * MZ;
+    const int l = i / MZ, n = pidx<V>(i - l * MZ);
     const V u0 = lines[(0 * TL + l) * LD + n], u1 = lines[(1 * TL + l) * LD + n], u2 = lines[(2 * TL + l) * LD + n];
     const V w0 = lines[(3 * TL + l) * LD + n], w1 = lines[(4 * TL + l) * LD + n], w2 = lines[(5 * TL + l) * LD + n];
     lines[(0 * TL + l) * LD + n] = mk<V>(u1.x * w2.x - u2.x * w1.x, u1.y * w2.y - u2.y * w1.y);
@@ -246,79 +300,95 @@ k_p3(const PassArgs a) {
   // still take part in the barriers
   {
     const int line = tid / G;
-    line_fft<V, MZ, -1, 2>(lines + (line < 3 * TL ? line : 0) * LD, tid % G, tw, line < 3 * TL);
+    line_fft<V, MZ, -1>(lines + (line < 3 * TL ? line : 0) * LD, tid % G, tws, line < 3 * TL);
   }
   // R2C post-step, keep kz <= Kz
-  for (int i = tid; i < 3 * TL * Mz; i += nth) {
-    const int c = i / (TL * Mz), r = i - c * (TL * Mz);
-    const int l = r / Mz, k = r - l * Mz;
+  for_rows<NTH>(3 * TL, Mz, [&](int row, int k) {
+    const int c = row / TL, l = row - c * TL;
     const long long xy = xy0 + l;
-    if (xy >= nxy) continue;
-    const V* L = lines + (c * TL + l) * LD;
-    const V zk = L[k], zm = L[(MZ - k) % MZ];
+    if (xy >= nxy) return;
+    const V* L = lines + row * LD;
+    const V zk = L[pidx<V>(k)], zm = L[pidx<V>((MZ - k) % MZ)];
     const V s = cadd(zk, cconj(zm)), d = csub(zk, cconj(zm));
-    const V od = cmul(tw[k], d);                   // e^{-2 pi i k / NZ} (Z_k - conj Z_{M-k})
+    const V od = cmul(tw[k], d);                   // e^{-2 pi i k / nz} (Z_k - conj Z_{M-k})
     const T hf = (T)0.5;
     // X = s/2 - (i/2) od
     out[((size_t)c * nxy + xy) * Mz + k] = mk<V>(hf * (s.x + od.y), hf * (s.y - od.x));
-  }
+  });
 }
 
 // ------------------------------------------------------------------------------------------
-// P5: x-forward + FP64 epilogue.  grid ceil(MyMz/TC).
+// P5: x-forward + epilogue.  grid ceil(MyMz/TC).  The Leray projection runs in the
+// transform precision T; the viscous term, forcing and the output k are FP64.
 // ------------------------------------------------------------------------------------------
 template <typename T, int NX>
-__global__ void __launch_bounds__(FftPlan<NX>::G * 3 * p1_cols<NX>())
+__global__ void __launch_bounds__(FftPlan<NX>::G * 3 * p1_cols<T, NX>())
 k_p5(const PassArgs a) {
   using V = v2_t<T>;
-  constexpr int TC = p1_cols<NX>();
+  constexpr int TC = p1_cols<T, NX>();
   constexpr int G = FftPlan<NX>::G;
-  constexpr int LD = NX + 1;
+  constexpr int LD = line_ld<V, NX>();
+  constexpr int NTW = twiddle_count_xy(NX);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw = reinterpret_cast<V*>(smem_raw);
-  V* lines = tw + NX;
+  V* lines = tw + NTW;
   if (gated_off(a.ctrl, a.gate_k1)) return;
   const Geom& g = a.g;
   const double2* __restrict__ Y = resolve_in(a.y, a.ctrl, a.yslot);
   double2* __restrict__ K = resolve_out(a.kout, a.ctrl, a.kslot);
   const V* __restrict__ in = reinterpret_cast<const V*>(a.in);
-  const V* __restrict__ twg = reinterpret_cast<const V*>(a.tw);
   const int col0 = blockIdx.x * TC;
   const int tid = threadIdx.x, nth = blockDim.x;
-  for (int i = tid; i < NX; i += nth) tw[i] = twg[i];
+  copy_tw(tw, reinterpret_cast<const V*>(a.tw), NTW);
   for (int i = tid; i < 3 * NX * TC; i += nth) {
     const int f = i / (NX * TC), r = i - f * (NX * TC), x = r / TC, c = r - x * TC, col = col0 + c;
-    lines[(f * TC + c) * LD + x] = col < g.MyMz ? in[((size_t)f * NX + x) * g.MyMz + col] : zero2<V>();
+    lines[(f * TC + c) * LD + pidx<V>(x)] = col < g.MyMz ? in[((size_t)f * NX + x) * g.MyMz + col] : zero2<V>();
   }
   __syncthreads();
-  line_fft<V, NX, -1, 1>(lines + (tid / G) * LD, tid % G, tw);
+  line_fft<V, NX, -1>(lines + (tid / G) * LD, tid % G, tw);
   const double fc = (a.ctrl && a.kf2 > 0) ? a.ctrl->forcing_coef : 0.0;
+  // -nu |kappa|^2 split per axis: x part per retained kx, y+z part per column (FP64)
+  double* visx = reinterpret_cast<double*>(lines + 3 * TC * LD);
+  double* visyz = visx + g.Mx;
+  for (int i = tid; i < g.Mx; i += nth) {
+    const double kx = g.sx * signed_mode(i, g.Kx, g.Mx);
+    visx[i] = -a.nu * kx * kx;
+  }
+  const T sx = (T)g.sx, sy = (T)g.sy, sz = (T)g.sz;
+  T* colk = reinterpret_cast<T*>(visyz + TC);
+  for (int c = tid; c < TC; c += nth) {
+    const int col = min(col0 + c, g.MyMz - 1);
+    const int jy = col / g.Mz, kz = col - jy * g.Mz;
+    const double ky = g.sy * signed_mode(jy, g.Ky, g.My), kzz = g.sz * kz;
+    visyz[c] = -a.nu * (ky * ky + kzz * kzz);
+    colk[2 * c] = sy * (T)signed_mode(jy, g.Ky, g.My);
+    colk[2 * c + 1] = sz * (T)kz;
+  }
+  __syncthreads();
+  const T kf2 = (T)a.kf2;
   for (int i = tid; i < g.Mx * TC; i += nth) {
     const int ix = i / TC, c = i - ix * TC, col = col0 + c;
     if (col >= g.MyMz) continue;
-    const int pos = ix <= g.Kx ? ix : NX - g.Mx + ix;
-    const V n0 = lines[(0 * TC + c) * LD + pos], n1 = lines[(1 * TC + c) * LD + pos], n2 = lines[(2 * TC + c) * LD + pos];
-    const int jy = col / g.Mz, kz = col - jy * g.Mz;
-    const double kx = g.sx * signed_mode(ix, g.Kx, g.Mx);
-    const double ky = g.sy * signed_mode(jy, g.Ky, g.My);
-    const double kzz = g.sz * kz;
-    const double k2 = kx * kx + ky * ky + kzz * kzz;
-    double nr0 = n0.x, ni0 = n0.y, nr1 = n1.x, ni1 = n1.y, nr2 = n2.x, ni2 = n2.y;
-    if (k2 > 0) {
-      const double ik2 = 1.0 / k2;
-      const double dr = (kx * nr0 + ky * nr1 + kzz * nr2) * ik2;
-      const double di = (kx * ni0 + ky * ni1 + kzz * ni2) * ik2;
-      nr0 -= kx * dr; ni0 -= kx * di;
-      nr1 -= ky * dr; ni1 -= ky * di;
-      nr2 -= kzz * dr; ni2 -= kzz * di;
+    const int pos = pidx<V>(ix <= g.Kx ? ix : NX - g.Mx + ix);
+    V n0 = lines[(0 * TC + c) * LD + pos], n1 = lines[(1 * TC + c) * LD + pos], n2 = lines[(2 * TC + c) * LD + pos];
+    const T kx = sx * (T)signed_mode(ix, g.Kx, g.Mx);
+    const T ky = colk[2 * c], kzz = colk[2 * c + 1];
+    const T k2 = kx * kx + ky * ky + kzz * kzz;
+    if (k2 > (T)0) {
+      const T ik2 = (T)1 / k2;
+      const T dr = (kx * n0.x + ky * n1.x + kzz * n2.x) * ik2;
+      const T di = (kx * n0.y + ky * n1.y + kzz * n2.y) * ik2;
+      n0 = mk<V>(n0.x - kx * dr, n0.y - kx * di);
+      n1 = mk<V>(n1.x - ky * dr, n1.y - ky * di);
+      n2 = mk<V>(n2.x - kzz * dr, n2.y - kzz * di);
     }
     const size_t off = (size_t)ix * g.MyMz + col;
     const double2 y0 = Y[off], y1 = Y[off + g.M], y2 = Y[off + 2 * g.M];
-    double vis = -a.nu * k2;
-    if (fc != 0.0 && k2 > 0 && k2 <= a.kf2) vis += fc;
-    K[off] = make_double2(nr0 + vis * y0.x, ni0 + vis * y0.y);
-    K[off + g.M] = make_double2(nr1 + vis * y1.x, ni1 + vis * y1.y);
-    K[off + 2 * g.M] = make_double2(nr2 + vis * y2.x, ni2 + vis * y2.y);
+    double vis = visx[ix] + visyz[c];
+    if (fc != 0.0 && k2 > (T)0 && k2 <= kf2) vis += fc;
+    K[off] = make_double2(fma(vis, y0.x, to_f64(n0.x)), fma(vis, y0.y, to_f64(n0.y)));
+    K[off + g.M] = make_double2(fma(vis, y1.x, to_f64(n1.x)), fma(vis, y1.y, to_f64(n1.y)));
+    K[off + 2 * g.M] = make_double2(fma(vis, y2.x, to_f64(n2.x)), fma(vis, y2.y, to_f64(n2.y)));
   }
 }
 

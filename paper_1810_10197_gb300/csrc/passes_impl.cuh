@@ -13,8 +13,10 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
 
 template <typename T, int N>
 static cudaError_t launch_p1(const PassArgs& a, cudaStream_t s) {
-  constexpr int TC = p1_cols<N>();
-  const size_t smem = (size_t)(N + 3 * TC * (N + 1)) * sizeof(v2_t<T>);
+  using V = v2_t<T>;
+  constexpr int TC = p1_cols<T, N>();
+  const size_t smem = (size_t)(twiddle_count_xy(N) + 3 * TC * line_ld<V, N>()) * sizeof(V) +
+                      (size_t)2 * TC * sizeof(T);
   cudaError_t e = set_smem(k_p1<T, N>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid((a.g.MyMz + TC - 1) / TC, 2);
@@ -24,8 +26,10 @@ static cudaError_t launch_p1(const PassArgs& a, cudaStream_t s) {
 
 template <typename T, int N>
 static cudaError_t launch_p5(const PassArgs& a, cudaStream_t s) {
-  constexpr int TC = p1_cols<N>();
-  const size_t smem = (size_t)(N + 3 * TC * (N + 1)) * sizeof(v2_t<T>);
+  using V = v2_t<T>;
+  constexpr int TC = p1_cols<T, N>();
+  const size_t smem = (size_t)(twiddle_count_xy(N) + 3 * TC * line_ld<V, N>()) * sizeof(V) +
+                      (size_t)(a.g.Mx + TC) * sizeof(double) + (size_t)2 * TC * sizeof(T);
   cudaError_t e = set_smem(k_p5<T, N>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid((a.g.MyMz + TC - 1) / TC);
@@ -35,18 +39,21 @@ static cudaError_t launch_p5(const PassArgs& a, cudaStream_t s) {
 
 template <typename T, int N, bool INV>
 static cudaError_t launch_py(const PassArgs& a, cudaStream_t s) {
-  const size_t smem = (size_t)(N + kTZ * (N + 1)) * sizeof(v2_t<T>);
+  using V = v2_t<T>;
+  constexpr int TZ = py_cols<T>();
+  const size_t smem = (size_t)(twiddle_count_xy(N) + TZ * line_ld<V, N>()) * sizeof(V);
   cudaError_t e = set_smem(k_py<T, N, INV>, smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((a.g.Mz + kTZ - 1) / kTZ, a.g.nx, INV ? 6 : 3);
-  k_py<T, N, INV><<<grid, FftPlan<N>::G * kTZ, smem, s>>>(a);
+  dim3 grid((a.g.Mz + TZ - 1) / TZ, a.g.nx, INV ? 6 : 3);
+  k_py<T, N, INV><<<grid, FftPlan<N>::G * TZ, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T, int MZ>
 static cudaError_t launch_p3(const PassArgs& a, cudaStream_t s) {
-  constexpr int TL = p3_lines<MZ>();
-  const size_t smem = (size_t)(2 * MZ + 6 * TL * (MZ + 1)) * sizeof(v2_t<T>);
+  using V = v2_t<T>;
+  constexpr int TL = p3_lines<T, MZ>();
+  const size_t smem = (size_t)(twiddle_count_z(2 * MZ) + 6 * TL * p3_ld<V, MZ>()) * sizeof(V);
   cudaError_t e = set_smem(k_p3<T, MZ>, smem);
   if (e != cudaSuccess) return e;
   const long long nxy = (long long)a.g.nx * a.g.ny;

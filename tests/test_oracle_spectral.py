@@ -207,3 +207,49 @@ def test_boussinesq_hydrostatic_rest_state():
     fu, fr = sp.rhs_boussinesq(g, np.zeros((3,) + rh.shape, complex), rh, 1e-3, 2e-3, 1.0)
     assert np.max(np.abs(fu)) < 1e-13 * np.max(np.abs(rh))
     assert np.max(np.abs(fr + 2e-3 * g.k2 * rh)) < 1e-13 * np.max(np.abs(rh))
+
+
+def brute_force_boussinesq(g, uh, rh, nu, kappa, ri):
+    """Eqs. (ufdefboussinesq), (rhofdefboussinesq) by exact convolution over retained modes.
+
+    f_u = P(k)[(u x omega)^ - Ri rho_k e_z (k != 0)] - nu |k|^2 u_k,
+    f_rho = -i k . (rho u)^ - kappa |k|^2 rho_k, with (rho u)^_k = (1/N^3) sum_{p+q=k} rho_p u_q.
+    """
+    scale = np.array([2 * np.pi / l for l in g.lengths])
+    U = full_spectrum(g, uh)
+    Rf = {m: v[0] for m, v in full_spectrum(g, rh[None]).items()}
+    W = {m: 1j * np.cross(np.array(m) * scale, v) for m, v in U.items()}
+    fu = np.zeros_like(uh)
+    fr = np.zeros_like(rh)
+    for (mx, my, mz) in U:
+        if mz < 0:
+            continue
+        nl = np.zeros(3, dtype=complex)
+        flux = np.zeros(3, dtype=complex)
+        for p, up in U.items():
+            q = (mx - p[0], my - p[1], mz - p[2])
+            if q in W:
+                nl += np.cross(up, W[q])
+                flux += Rf[q] * up
+        nl /= g.n3
+        flux /= g.n3
+        kv = np.array((mx, my, mz)) * scale
+        k2 = kv @ kv
+        if k2 > 0:
+            nl[2] -= ri * Rf[(mx, my, mz)]
+            nl = nl - kv * (kv @ nl) / k2
+        ix, iy = mx % g.nx, my % g.ny
+        fu[:, ix, iy, mz] = nl - nu * k2 * U[(mx, my, mz)]
+        fr[ix, iy, mz] = -1j * (kv @ flux) - kappa * k2 * Rf[(mx, my, mz)]
+    return fu, fr
+
+
+def test_boussinesq_rhs_equals_brute_force_convolution():
+    shape, L = (8, 8, 10), (2 * np.pi, 2 * np.pi, 2.5 * np.pi)
+    g = sp.Grid(*shape, lengths=L)
+    uh = g.dealias(syn.random_complex_hat(*shape, seed=31))
+    rh = g.dealias(syn.random_complex_hat(*shape, seed=32, ncomp=1)[0])
+    fu, fr = sp.rhs_boussinesq(g, uh, rh, 0.01, 0.02, 0.7)
+    ru, rr = brute_force_boussinesq(g, uh, rh, 0.01, 0.02, 0.7)
+    assert np.max(np.abs(fu - ru)) <= 1e-12 * np.max(np.abs(ru))
+    assert np.max(np.abs(fr - rr)) <= 1e-12 * np.max(np.abs(rr))
