@@ -101,6 +101,15 @@ dns_status dns_create(int nx, int ny, int nz, double nu, const dns_forcing* forc
                       int precision, dns_ctx** out);
 /* As dns_create, with domain lengths from cfg. */
 dns_status dns_create_ex(const dns_config* cfg, dns_ctx** out);
+/* Boussinesq form, Eqs. (ufdefboussinesq) and (rhofdefboussinesq) of Section 3.2:
+ *   d(uhat)/dt   = P(kappa)[(u x omega)^ - Ri rhohat e_z] - nu |kappa|^2 uhat
+ *   d(rhohat)/dt = -i kappa . (rho u)^ - kappa |kappa|^2 rhohat
+ * (the buoyancy's kappa = 0 mode is dropped: a mean body force is balanced by the mean
+ * pressure gradient).  The state has 4 components [4][nx][ny][nz/2+1]: velocity then the
+ * density deviation rho; every state/RHS call of this context uses that layout, and the
+ * error norm takes the maximum over the 4 components.  cfg->forcing must be kind 0;
+ * kappa is the density diffusivity 1/(Re Pr), ri the Richardson number. */
+dns_status dns_create_boussinesq(const dns_config* cfg, double kappa, double ri, dns_ctx** out);
 void dns_destroy(dns_ctx* ctx);
 /* Message for the last non-OK status of this context ("" if none).  Valid until next call. */
 const char* dns_last_error(const dns_ctx* ctx);

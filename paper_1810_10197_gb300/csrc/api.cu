@@ -73,6 +73,8 @@ struct dns_ctx {
   Geom g{};
   int precision = 0;
   double nu = 0;
+  double kappa_d = 0;   // Boussinesq density diffusivity
+  double ri = 0;        // Boussinesq Richardson number
   dns_forcing forcing{};
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -193,6 +195,8 @@ dns_status enqueue_rhs(dns_ctx* c, DnsCtrl* ctrl, int yslot, int kslot, int gate
   a.kslot = kslot;
   a.nu = c->nu;
   a.kf2 = c->forcing.kind == 1 ? c->forcing.kf * c->forcing.kf : 0.0;
+  a.kappa_d = c->kappa_d;
+  a.ri = c->ri;
   a.out = c->bufA; a.tw = c->tw[0];
   CK(timed(c, PR_P1, [&] { return pass(c, 1, a); }), "pass P1");
   a.in = c->bufA; a.out = c->bufB; a.tw = c->tw[1];
@@ -214,7 +218,7 @@ dns_status enqueue_stage(dns_ctx* c, int nterms, const int* kslots, const double
   for (int j = 0; j < nterms; ++j) { s.kslot[j] = kslots[j]; s.coef[j] = coef[j]; }
   s.uslot = SLOT_U;
   s.yslot = yslot;
-  s.n2 = 3 * c->g.M;
+  s.n2 = (long long)c->g.nc * c->g.M;
   CK(timed(c, PR_STAGE, [&] { return launch_stage_sum(s, c->stream); }), "stage sum");
   return DNS_OK;
 }
@@ -236,7 +240,7 @@ dns_status enqueue_attempt(dns_ctx* c, int method) {
     for (int j = 0; j < 4; ++j) { ks[j] = SLOT_K1 + j; cf[j] = frac_val(kRK4B[j]); }
     if ((st = enqueue_stage(c, 4, ks, cf, SLOT_UNEW)) != DNS_OK) return st;
     CK(timed(c, PR_CTRL, [&] {
-         return launch_controller(c->ctrl, c->partials, 0, 4, c->g.nmodes_half, c->stream);
+         return launch_controller(c->ctrl, c->partials, 0, 4, c->g.nmodes_half, c->g.nc, c->stream);
        }), "controller");
     return DNS_OK;
   }
@@ -253,6 +257,7 @@ dns_status enqueue_attempt(dns_ctx* c, int method) {
   ErrArgs e{};
   e.ctrl = c->ctrl;
   e.M = c->g.M;
+  e.nc = c->g.nc;
   e.partials = c->partials;
   int n = 0;
   for (int j = 0; j < 8; ++j) {
@@ -264,7 +269,7 @@ dns_status enqueue_attempt(dns_ctx* c, int method) {
   e.nterms = n;
   CK(timed(c, PR_ERR, [&] { return launch_err_partials(e, c->stream); }), "error norm");
   CK(timed(c, PR_CTRL, [&] {
-       return launch_controller(c->ctrl, c->partials, method, 8, c->g.nmodes_half, c->stream);
+       return launch_controller(c->ctrl, c->partials, method, 8, c->g.nmodes_half, c->g.nc, c->stream);
      }), "controller");
   return DNS_OK;
 }
@@ -308,7 +313,7 @@ dns_status status_from_ctrl(dns_ctx* c) {
 
 dns_status ensure_stage(dns_ctx* c) {
   if (c->full_stage) return DNS_OK;
-  const size_t bytes = (size_t)3 * c->g.nx * c->g.ny * c->g.nzh * sizeof(double2);
+  const size_t bytes = (size_t)c->g.nc * c->g.nx * c->g.ny * c->g.nzh * sizeof(double2);
   return alloc(c, (void**)&c->full_stage, bytes);
 }
 
@@ -324,7 +329,17 @@ dns_status dns_create(int nx, int ny, int nz, double nu, const dns_forcing* forc
   return dns_create_ex(&cfg, out);
 }
 
-dns_status dns_create_ex(const dns_config* cfg, dns_ctx** out) {
+static dns_status create_impl(const dns_config* cfg, int bouss, double kappa, double ri, dns_ctx** out);
+
+dns_status dns_create_ex(const dns_config* cfg, dns_ctx** out) { return create_impl(cfg, 0, 0.0, 0.0, out); }
+
+dns_status dns_create_boussinesq(const dns_config* cfg, double kappa, double ri, dns_ctx** out) {
+  if (!cfg || !out) return DNS_ERR_ARG;
+  if (!(kappa >= 0.0) || !std::isfinite(kappa) || !std::isfinite(ri) || cfg->forcing.kind != 0) return DNS_ERR_ARG;
+  return create_impl(cfg, 1, kappa, ri, out);
+}
+
+static dns_status create_impl(const dns_config* cfg, int bouss, double kappa, double ri, dns_ctx** out) {
   if (!cfg || !out) return DNS_ERR_ARG;
   *out = nullptr;
   if (!supported(cfg->nx) || !supported(cfg->ny) || !supported(cfg->nz)) return DNS_ERR_UNSUPPORTED;
@@ -334,6 +349,8 @@ dns_status dns_create_ex(const dns_config* cfg, dns_ctx** out) {
   dns_ctx* c = new dns_ctx();
   c->precision = cfg->precision;
   c->nu = cfg->nu;
+  c->kappa_d = kappa;
+  c->ri = ri;
   c->forcing = cfg->forcing;
   cudaGetDevice(&c->device);
   Geom& g = c->g;
@@ -350,11 +367,15 @@ dns_status dns_create_ex(const dns_config* cfg, dns_ctx** out) {
   g.sz = cfg->lz > 0 ? twopi / lz : 1.0;
   g.inv_n3 = 1.0 / ((double)g.nx * g.ny * g.nz);
   g.nmodes_half = (double)g.nx * g.ny * g.nzh;
+  g.nc = bouss ? 4 : 3;
+  g.bouss = bouss;
 
-  const size_t vbytes = (size_t)3 * g.M * sizeof(double2);
+  const size_t vbytes = (size_t)g.nc * g.M * sizeof(double2);
   const size_t esz = c->precision == DNS_FP32_MIXED ? sizeof(float2) : sizeof(double2);
-  const size_t nA = std::max((size_t)6 * g.nx * g.My * g.Mz, (size_t)3 * g.nx * g.ny * g.Mz);
-  const size_t nB = std::max((size_t)6 * g.nx * g.ny * g.Mz, (size_t)3 * g.nx * g.My * g.Mz);
+  // physical-side field counts: inverse (u, omega [, rho]), forward (u x omega [, rho u])
+  const size_t fin = g.bouss ? 7 : 6, fout = g.bouss ? 6 : 3;
+  const size_t nA = std::max(fin * g.nx * g.My * g.Mz, fout * g.nx * g.ny * g.Mz);
+  const size_t nB = std::max(fin * g.nx * g.ny * g.Mz, fout * g.nx * g.My * g.Mz);
   dns_status s = DNS_OK;
   auto A = [&](void** p, size_t b) { if (s == DNS_OK) s = alloc(c, p, b); };
   A((void**)&c->uu[0], vbytes); A((void**)&c->uu[1], vbytes);
@@ -364,12 +385,12 @@ dns_status dns_create_ex(const dns_config* cfg, dns_ctx** out) {
   A((void**)&c->rhs_in, vbytes); A((void**)&c->rhs_out, vbytes);
   A(&c->bufA, nA * esz); A(&c->bufB, nB * esz);
   A((void**)&c->ctrl, sizeof(DnsCtrl)); A((void**)&c->ctrl_rhs, sizeof(DnsCtrl));
-  A((void**)&c->partials, (size_t)kRedBlocks * 3 * sizeof(double));
+  A((void**)&c->partials, (size_t)kRedBlocks * kRedStride * sizeof(double));
   if (s == DNS_OK) s = make_twiddles(c, g.nx, false, &c->tw[0]);
   if (s == DNS_OK) s = make_twiddles(c, g.ny, false, &c->tw[1]);
   if (s == DNS_OK) s = make_twiddles(c, g.nz, true, &c->tw[2]);
   if (s == DNS_OK && cudaMallocHost((void**)&c->host_ctrl, sizeof(DnsCtrl)) != cudaSuccess) s = DNS_ERR_OOM;
-  if (s == DNS_OK && cudaMallocHost((void**)&c->host_partials, (size_t)kRedBlocks * 3 * sizeof(double)) != cudaSuccess)
+  if (s == DNS_OK && cudaMallocHost((void**)&c->host_partials, (size_t)kRedBlocks * kRedStride * sizeof(double)) != cudaSuccess)
     s = DNS_ERR_OOM;
   if (s == DNS_OK) {
     DnsCtrl h{};
@@ -430,7 +451,7 @@ dns_status dns_set_state(dns_ctx* c, const void* uhat, int where, double t) {
   const double2* src = reinterpret_cast<const double2*>(uhat);
   if (where == 1) {
     if ((s = ensure_stage(c)) != DNS_OK) return s;
-    const size_t bytes = (size_t)3 * c->g.nx * c->g.ny * c->g.nzh * sizeof(double2);
+    const size_t bytes = (size_t)c->g.nc * c->g.nx * c->g.ny * c->g.nzh * sizeof(double2);
     CK(cudaMemcpyAsync(c->full_stage, uhat, bytes, cudaMemcpyHostToDevice, c->stream), "state upload");
     src = c->full_stage;
   }
@@ -446,7 +467,7 @@ dns_status dns_get_state(dns_ctx* c, void* uhat, int where) {
   if (s != DNS_OK) return s;
   if (!uhat || (where != 0 && where != 1)) return fail(c, DNS_ERR_ARG, "dns_get_state: bad argument");
   if (!c->has_state) return fail(c, DNS_ERR_STATE, "no state set");
-  const size_t bytes = (size_t)3 * c->g.nx * c->g.ny * c->g.nzh * sizeof(double2);
+  const size_t bytes = (size_t)c->g.nc * c->g.nx * c->g.ny * c->g.nzh * sizeof(double2);
   double2* dst = reinterpret_cast<double2*>(uhat);
   if (where == 1) {
     if ((s = ensure_stage(c)) != DNS_OK) return s;
@@ -466,7 +487,7 @@ dns_status dns_rhs(dns_ctx* c, const void* uhat_dev, void* f_dev) {
   dns_status s = check_ctx(c);
   if (s != DNS_OK) return s;
   if (!uhat_dev || !f_dev || uhat_dev == f_dev) return fail(c, DNS_ERR_ARG, "dns_rhs: bad pointers");
-  const size_t bytes = (size_t)3 * c->g.nx * c->g.ny * c->g.nzh * sizeof(double2);
+  const size_t bytes = (size_t)c->g.nc * c->g.nx * c->g.ny * c->g.nzh * sizeof(double2);
   CK(launch_gather(c->g, reinterpret_cast<const double2*>(uhat_dev), c->rhs_in, c->stream), "gather");
   if ((s = enqueue_rhs(c, c->ctrl_rhs, SLOT_Y, SLOT_K1, 0)) != DNS_OK) return s;
   CK(cudaMemsetAsync(f_dev, 0, bytes, c->stream), "memset");
@@ -549,16 +570,16 @@ dns_status dns_diagnostics(dns_ctx* c, double* E, double* Omega, double* eps) {
   if (!c->has_state) return fail(c, DNS_ERR_STATE, "no state set");
   if ((s = read_ctrl(c)) != DNS_OK) return s;
   const double2* cur = c->uu[c->host_ctrl->parity];
-  CK(cudaMemcpyAsync(c->rhs_in, cur, (size_t)3 * c->g.M * sizeof(double2), cudaMemcpyDeviceToDevice,
+  CK(cudaMemcpyAsync(c->rhs_in, cur, (size_t)c->g.nc * c->g.M * sizeof(double2), cudaMemcpyDeviceToDevice,
                      c->stream), "copy");
   if ((s = enqueue_rhs(c, c->ctrl_rhs, SLOT_Y, SLOT_K1, 0)) != DNS_OK) return s;
   CK(launch_diag_partials(c->g, c->rhs_in, c->rhs_out, c->partials, c->stream), "diagnostics");
-  CK(cudaMemcpyAsync(c->host_partials, c->partials, (size_t)kRedBlocks * 3 * sizeof(double),
+  CK(cudaMemcpyAsync(c->host_partials, c->partials, (size_t)kRedBlocks * kRedStride * sizeof(double),
                      cudaMemcpyDeviceToHost, c->stream), "read partials");
   CK(cudaStreamSynchronize(c->stream), "synchronize");
   double v[3] = {0, 0, 0};
   for (int b = 0; b < kRedBlocks; ++b)
-    for (int q = 0; q < 3; ++q) v[q] += c->host_partials[b * 3 + q];
+    for (int q = 0; q < 3; ++q) v[q] += c->host_partials[b * kRedStride + q];
   const double n6 = c->g.inv_n3 * c->g.inv_n3;
   if (E) *E = 0.5 * v[0] * n6;
   if (Omega) *Omega = 0.5 * v[1] * n6;

@@ -97,6 +97,8 @@ extern "C" dns_status dns_rhs_noalloc(int nx, int ny, int nz, double nu, const v
   g.sx = g.sy = g.sz = 1.0;
   g.inv_n3 = 1.0 / ((double)nx * ny * nz);
   g.nmodes_half = (double)nx * ny * g.nzh;
+  g.nc = 3;
+  g.bouss = 0;
   DnsCtrl* ctrl = reinterpret_cast<DnsCtrl*>(base + kOffCtrl);
 
   k_na_setup<<<1, 64, 0, s>>>(base, nx, ny, nz);

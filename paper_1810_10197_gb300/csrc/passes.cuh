@@ -33,6 +33,8 @@ struct PassArgs {
   const void* tw;        // twiddle tables (T complex) of this pass's axis, see twiddle_count
   double nu;
   double kf2;            // forcing band |kappa|^2 <= kf2 (0: no forcing)
+  double kappa_d;        // density diffusivity (Boussinesq)
+  double ri;             // Richardson number (Boussinesq)
 };
 
 // Column tiles: kz-contiguous columns handled per CTA in the x and y passes (128-byte rows),
@@ -41,7 +43,9 @@ template <typename T, int N> __host__ __device__ constexpr int p1_cols() {
   return sizeof(T) == 4 ? (N >= 512 ? 8 : 16) : (N >= 512 ? 4 : 8);
 }
 template <typename T> __host__ __device__ constexpr int py_cols() { return sizeof(T) == 4 ? 16 : 8; }
-template <typename T, int MZ> __host__ __device__ constexpr int p3_lines() { return MZ >= 256 ? 4 : 8; }
+template <typename T, int MZ, bool BOUSS = false> __host__ __device__ constexpr int p3_lines() {
+  return BOUSS ? (MZ >= 256 ? 2 : 4) : (MZ >= 256 ? 4 : 8);
+}
 // z-pass line stride: lines whose threads share a half-warp (FP32) or quarter-warp (FP64)
 // start at bank offsets that the first Stockham stage's writes do not overlap.
 template <typename V, int MZ> __host__ __device__ constexpr int p3_ld() {
@@ -105,9 +109,10 @@ __device__ __forceinline__ void copy_tw(V* dst, const V* __restrict__ src, int n
 }
 
 // ------------------------------------------------------------------------------------------
-// P1: x-inverse with the curl fused in.  grid (ceil(MyMz/TC), 2): y = 0 -> u, 1 -> omega.
+// P1: x-inverse with the curl fused in.  grid (ceil(MyMz/TC), 2 or 3): y = 0 -> u,
+// 1 -> omega, 2 -> density (Boussinesq: one field over 3 TC columns, output field 6).
 // ------------------------------------------------------------------------------------------
-template <typename T, int NX>
+template <typename T, int NX, bool BOUSS>
 __global__ void __launch_bounds__(FftPlan<NX>::G * 3 * p1_cols<T, NX>())
 k_p1(const PassArgs a) {
   using V = v2_t<T>;
@@ -131,6 +136,30 @@ k_p1(const PassArgs a) {
   for_rows<NTH>(3 * TC, NX - g.Mx, [&](int l, int q) { lines[l * LD + pidx<V>(g.Kx + 1 + q)] = zero2<V>(); });
   const T s = (T)g.inv_n3;
   const T sx = (T)g.sx, sy = (T)g.sy, sz = (T)g.sz;
+  if constexpr (BOUSS) {
+    if (half == 2) {   // density: lines are 3 TC columns of one field
+      constexpr int TC3 = 3 * TC;
+      const int c0 = blockIdx.x * TC3;
+      if (c0 >= g.MyMz) return;   // uniform over the CTA, before any barrier
+      __syncthreads();
+      for (int i = tid; i < g.Mx * TC3; i += nth) {
+        const int ix = i / TC3, c = i - ix * TC3, col = c0 + c;
+        V f = zero2<V>();
+        if (col < g.MyMz) {
+          const double2 d = Y[3 * g.M + (size_t)ix * g.MyMz + col];
+          f = cscale(mk<V>(from_f64<T>(d.x), from_f64<T>(d.y)), s);
+        }
+        lines[c * LD + pidx<V>(ix <= g.Kx ? ix : NX - g.Mx + ix)] = f;
+      }
+      __syncthreads();
+      line_fft<V, NX, +1>(lines + (tid / G) * LD, tid % G, tw);
+      for (int i = tid; i < NX * TC3; i += nth) {
+        const int x = i / TC3, c = i - x * TC3, col = c0 + c;
+        if (col < g.MyMz) out[((size_t)6 * NX + x) * g.MyMz + col] = lines[c * LD + pidx<V>(x)];
+      }
+      return;
+    }
+  }
   if (tid < TC) {
     const int col = min(col0 + tid, g.MyMz - 1);
     const int jy = col / g.Mz, kz = col - jy * g.Mz;
@@ -237,18 +266,20 @@ k_py(const PassArgs a) {
 //   C2R pre-step : Z_k = (X_k + conj X_{M-k}) + i e^{+2 pi i k/nz} (X_k - conj X_{M-k})
 //   R2C post-step: X_k = (Z_k + conj Z_{M-k})/2 - (i/2) e^{-2 pi i k/nz} (Z_k - conj Z_{M-k})
 // ------------------------------------------------------------------------------------------
-template <typename T, int MZ>
-__global__ void __launch_bounds__(FftPlan<MZ>::G * 6 * p3_lines<T, MZ>())
+template <typename T, int MZ, bool BOUSS>
+__global__ void __launch_bounds__(FftPlan<MZ>::G * (BOUSS ? 7 : 6) * p3_lines<T, MZ, BOUSS>())
 k_p3(const PassArgs a) {
   using V = v2_t<T>;
-  constexpr int TL = p3_lines<T, MZ>();
+  constexpr int TL = p3_lines<T, MZ, BOUSS>();
+  constexpr int NIN = BOUSS ? 7 : 6;    // u, omega (, rho)
+  constexpr int NOUT = BOUSS ? 6 : 3;   // u x omega (, rho u)
   constexpr int G = FftPlan<MZ>::G;
   constexpr int LD = p3_ld<V, MZ>();
   constexpr int NTW = twiddle_count_z(2 * MZ);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw = reinterpret_cast<V*>(smem_raw);      // [0, MZ]: exp(-2 pi i k / nz); then stages
   V* tws = tw + MZ + 1;
-  V* lines = tw + NTW;                         // 6*TL lines of LD
+  V* lines = tw + NTW;                         // NIN*TL lines of LD
   if (gated_off(a.ctrl, a.gate_k1)) return;
   const Geom& g = a.g;
   const V* __restrict__ in = reinterpret_cast<const V*>(a.in);
@@ -257,10 +288,10 @@ k_p3(const PassArgs a) {
   const long long xy0 = (long long)blockIdx.x * TL;
   const int Mz = g.Mz;
   const int tid = threadIdx.x, nth = blockDim.x;
-  constexpr int NTH = G * 6 * TL;
+  constexpr int NTH = G * NIN * TL;
   copy_tw(tw, reinterpret_cast<const V*>(a.tw), NTW);
   // rows (field, line): kz < Mz from memory, Mz..MZ zero
-  for_rows<NTH>(6 * TL, MZ + 1, [&](int row, int kz) {
+  for_rows<NTH>(NIN * TL, MZ + 1, [&](int row, int kz) {
     const int f = row / TL, l = row - f * TL;
     const long long xy = xy0 + l;
     lines[row * LD + pidx<V>(kz)] =
@@ -270,7 +301,7 @@ k_p3(const PassArgs a) {
   // C2R pre-step on pairs (k, MZ-k), k = 0..MZ/2
   {
     constexpr int NP = MZ / 2 + 1;
-    for (int i = tid; i < 6 * TL * NP; i += nth) {
+    for (int i = tid; i < NIN * TL * NP; i += nth) {
       const int l = i / NP, k = i - l * NP;
       V* L = lines + l * LD;
       const int m = MZ - k;
@@ -286,7 +317,7 @@ k_p3(const PassArgs a) {
   }
   __syncthreads();
   line_fft<V, MZ, +1>(lines + (tid / G) * LD, tid % G, tws);
-  // u x omega on both packed halves (real part: even z, imaginary part: odd z)
+  // u x omega (and rho u) on both packed halves (real part: even z, imaginary part: odd z)
   for (int i = tid; i < TL * MZ; i += nth) {
     const int l = i / MZ, n = pidx<V>(i - l * MZ);
     const V u0 = lines[(0 * TL + l) * LD + n], u1 = lines[(1 * TL + l) * LD + n], u2 = lines[(2 * TL + l) * LD + n];
@@ -294,16 +325,22 @@ k_p3(const PassArgs a) {
     lines[(0 * TL + l) * LD + n] = mk<V>(u1.x * w2.x - u2.x * w1.x, u1.y * w2.y - u2.y * w1.y);
     lines[(1 * TL + l) * LD + n] = mk<V>(u2.x * w0.x - u0.x * w2.x, u2.y * w0.y - u0.y * w2.y);
     lines[(2 * TL + l) * LD + n] = mk<V>(u0.x * w1.x - u1.x * w0.x, u0.y * w1.y - u1.y * w0.y);
+    if constexpr (BOUSS) {
+      const V r = lines[(6 * TL + l) * LD + n];
+      lines[(3 * TL + l) * LD + n] = mk<V>(r.x * u0.x, r.y * u0.y);
+      lines[(4 * TL + l) * LD + n] = mk<V>(r.x * u1.x, r.y * u1.y);
+      lines[(5 * TL + l) * LD + n] = mk<V>(r.x * u2.x, r.y * u2.y);
+    }
   }
   __syncthreads();
-  // forward complex DFT of the 3 packed product lines; threads on lines >= 3 TL idle but
+  // forward complex DFT of the packed product lines; threads on lines >= NOUT TL idle but
   // still take part in the barriers
   {
     const int line = tid / G;
-    line_fft<V, MZ, -1>(lines + (line < 3 * TL ? line : 0) * LD, tid % G, tws, line < 3 * TL);
+    line_fft<V, MZ, -1>(lines + (line < NOUT * TL ? line : 0) * LD, tid % G, tws, line < NOUT * TL);
   }
   // R2C post-step, keep kz <= Kz
-  for_rows<NTH>(3 * TL, Mz, [&](int row, int k) {
+  for_rows<NTH>(NOUT * TL, Mz, [&](int row, int k) {
     const int c = row / TL, l = row - c * TL;
     const long long xy = xy0 + l;
     if (xy >= nxy) return;
@@ -320,12 +357,19 @@ k_p3(const PassArgs a) {
 // ------------------------------------------------------------------------------------------
 // P5: x-forward + epilogue.  grid ceil(MyMz/TC).  The Leray projection runs in the
 // transform precision T; the viscous term, forcing and the output k are FP64.
+// Boussinesq (Section 3.2): fields 0..2 hold (u x omega)^, 3..5 (rho u)^; the buoyancy
+// -Ri rho e_z (kappa != 0) enters before the projection, and the density equation is
+// -i kappa . (rho u)^ - kappa_d |kappa|^2 rho.
 // ------------------------------------------------------------------------------------------
-template <typename T, int NX>
+template <typename T, int NX> __host__ __device__ constexpr int p5_cols(bool bouss) {
+  return bouss ? p1_cols<T, NX>() / 2 : p1_cols<T, NX>();
+}
+template <typename T, int NX, bool BOUSS>
 __global__ void __launch_bounds__(FftPlan<NX>::G * 3 * p1_cols<T, NX>())
 k_p5(const PassArgs a) {
   using V = v2_t<T>;
-  constexpr int TC = p1_cols<T, NX>();
+  constexpr int TC = p5_cols<T, NX>(BOUSS);
+  constexpr int NF = BOUSS ? 6 : 3;
   constexpr int G = FftPlan<NX>::G;
   constexpr int LD = line_ld<V, NX>();
   constexpr int NTW = twiddle_count_xy(NX);
@@ -340,27 +384,27 @@ k_p5(const PassArgs a) {
   const int col0 = blockIdx.x * TC;
   const int tid = threadIdx.x, nth = blockDim.x;
   copy_tw(tw, reinterpret_cast<const V*>(a.tw), NTW);
-  for (int i = tid; i < 3 * NX * TC; i += nth) {
+  for (int i = tid; i < NF * NX * TC; i += nth) {
     const int f = i / (NX * TC), r = i - f * (NX * TC), x = r / TC, c = r - x * TC, col = col0 + c;
     lines[(f * TC + c) * LD + pidx<V>(x)] = col < g.MyMz ? in[((size_t)f * NX + x) * g.MyMz + col] : zero2<V>();
   }
   __syncthreads();
   line_fft<V, NX, -1>(lines + (tid / G) * LD, tid % G, tw);
   const double fc = (a.ctrl && a.kf2 > 0) ? a.ctrl->forcing_coef : 0.0;
-  // -nu |kappa|^2 split per axis: x part per retained kx, y+z part per column (FP64)
-  double* visx = reinterpret_cast<double*>(lines + 3 * TC * LD);
-  double* visyz = visx + g.Mx;
+  // |kappa|^2 split per axis (FP64): x part per retained kx, y+z part per column
+  double* k2x = reinterpret_cast<double*>(lines + NF * TC * LD);
+  double* k2yz = k2x + g.Mx;
   for (int i = tid; i < g.Mx; i += nth) {
     const double kx = g.sx * signed_mode(i, g.Kx, g.Mx);
-    visx[i] = -a.nu * kx * kx;
+    k2x[i] = kx * kx;
   }
   const T sx = (T)g.sx, sy = (T)g.sy, sz = (T)g.sz;
-  T* colk = reinterpret_cast<T*>(visyz + TC);
+  T* colk = reinterpret_cast<T*>(k2yz + TC);
   for (int c = tid; c < TC; c += nth) {
     const int col = min(col0 + c, g.MyMz - 1);
     const int jy = col / g.Mz, kz = col - jy * g.Mz;
     const double ky = g.sy * signed_mode(jy, g.Ky, g.My), kzz = g.sz * kz;
-    visyz[c] = -a.nu * (ky * ky + kzz * kzz);
+    k2yz[c] = ky * ky + kzz * kzz;
     colk[2 * c] = sy * (T)signed_mode(jy, g.Ky, g.My);
     colk[2 * c + 1] = sz * (T)kz;
   }
@@ -374,6 +418,15 @@ k_p5(const PassArgs a) {
     const T kx = sx * (T)signed_mode(ix, g.Kx, g.Mx);
     const T ky = colk[2 * c], kzz = colk[2 * c + 1];
     const T k2 = kx * kx + ky * ky + kzz * kzz;
+    const size_t off = (size_t)ix * g.MyMz + col;
+    double2 rho = make_double2(0.0, 0.0);
+    if constexpr (BOUSS) {
+      rho = Y[off + 3 * g.M];
+      if (k2 > (T)0) {
+        const T ri = (T)a.ri;
+        n2 = mk<V>(n2.x - ri * from_f64<T>(rho.x), n2.y - ri * from_f64<T>(rho.y));
+      }
+    }
     if (k2 > (T)0) {
       const T ik2 = (T)1 / k2;
       const T dr = (kx * n0.x + ky * n1.x + kzz * n2.x) * ik2;
@@ -382,13 +435,20 @@ k_p5(const PassArgs a) {
       n1 = mk<V>(n1.x - ky * dr, n1.y - ky * di);
       n2 = mk<V>(n2.x - kzz * dr, n2.y - kzz * di);
     }
-    const size_t off = (size_t)ix * g.MyMz + col;
     const double2 y0 = Y[off], y1 = Y[off + g.M], y2 = Y[off + 2 * g.M];
-    double vis = visx[ix] + visyz[c];
+    const double k2d = k2x[ix] + k2yz[c];
+    double vis = -a.nu * k2d;
     if (fc != 0.0 && k2 > (T)0 && k2 <= kf2) vis += fc;
     K[off] = make_double2(fma(vis, y0.x, to_f64(n0.x)), fma(vis, y0.y, to_f64(n0.y)));
     K[off + g.M] = make_double2(fma(vis, y1.x, to_f64(n1.x)), fma(vis, y1.y, to_f64(n1.y)));
     K[off + 2 * g.M] = make_double2(fma(vis, y2.x, to_f64(n2.x)), fma(vis, y2.y, to_f64(n2.y)));
+    if constexpr (BOUSS) {
+      const V f0 = lines[(3 * TC + c) * LD + pos], f1 = lines[(4 * TC + c) * LD + pos], f2 = lines[(5 * TC + c) * LD + pos];
+      const V kd = mk<V>(kx * f0.x + ky * f1.x + kzz * f2.x, kx * f0.y + ky * f1.y + kzz * f2.y);
+      const double visr = -a.kappa_d * k2d;
+      // -i (kappa . F) = (Im, -Re)
+      K[off + 3 * g.M] = make_double2(fma(visr, rho.x, to_f64(kd.y)), fma(visr, rho.y, -to_f64(kd.x)));
+    }
   }
 }
 

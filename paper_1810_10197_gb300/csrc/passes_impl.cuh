@@ -11,29 +11,30 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <typename T, int N>
+template <typename T, int N, bool B>
 static cudaError_t launch_p1(const PassArgs& a, cudaStream_t s) {
   using V = v2_t<T>;
   constexpr int TC = p1_cols<T, N>();
   const size_t smem = (size_t)(twiddle_count_xy(N) + 3 * TC * line_ld<V, N>()) * sizeof(V) +
                       (size_t)2 * TC * sizeof(T);
-  cudaError_t e = set_smem(k_p1<T, N>, smem);
+  cudaError_t e = set_smem(k_p1<T, N, B>, smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((a.g.MyMz + TC - 1) / TC, 2);
-  k_p1<T, N><<<grid, FftPlan<N>::G * 3 * TC, smem, s>>>(a);
+  dim3 grid((a.g.MyMz + TC - 1) / TC, B ? 3 : 2);
+  k_p1<T, N, B><<<grid, FftPlan<N>::G * 3 * TC, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename T, int N>
+template <typename T, int N, bool B>
 static cudaError_t launch_p5(const PassArgs& a, cudaStream_t s) {
   using V = v2_t<T>;
-  constexpr int TC = p1_cols<T, N>();
-  const size_t smem = (size_t)(twiddle_count_xy(N) + 3 * TC * line_ld<V, N>()) * sizeof(V) +
+  constexpr int TC = p5_cols<T, N>(B);
+  constexpr int NF = B ? 6 : 3;
+  const size_t smem = (size_t)(twiddle_count_xy(N) + NF * TC * line_ld<V, N>()) * sizeof(V) +
                       (size_t)(a.g.Mx + TC) * sizeof(double) + (size_t)2 * TC * sizeof(T);
-  cudaError_t e = set_smem(k_p5<T, N>, smem);
+  cudaError_t e = set_smem(k_p5<T, N, B>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid((a.g.MyMz + TC - 1) / TC);
-  k_p5<T, N><<<grid, FftPlan<N>::G * 3 * TC, smem, s>>>(a);
+  k_p5<T, N, B><<<grid, FftPlan<N>::G * NF * TC, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -44,21 +45,23 @@ static cudaError_t launch_py(const PassArgs& a, cudaStream_t s) {
   const size_t smem = (size_t)(twiddle_count_xy(N) + TZ * line_ld<V, N>()) * sizeof(V);
   cudaError_t e = set_smem(k_py<T, N, INV>, smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((a.g.Mz + TZ - 1) / TZ, a.g.nx, INV ? 6 : 3);
+  const int nf = INV ? (a.g.bouss ? 7 : 6) : (a.g.bouss ? 6 : 3);
+  dim3 grid((a.g.Mz + TZ - 1) / TZ, a.g.nx, nf);
   k_py<T, N, INV><<<grid, FftPlan<N>::G * TZ, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename T, int MZ>
+template <typename T, int MZ, bool B>
 static cudaError_t launch_p3(const PassArgs& a, cudaStream_t s) {
   using V = v2_t<T>;
-  constexpr int TL = p3_lines<T, MZ>();
-  const size_t smem = (size_t)(twiddle_count_z(2 * MZ) + 6 * TL * p3_ld<V, MZ>()) * sizeof(V);
-  cudaError_t e = set_smem(k_p3<T, MZ>, smem);
+  constexpr int TL = p3_lines<T, MZ, B>();
+  constexpr int NIN = B ? 7 : 6;
+  const size_t smem = (size_t)(twiddle_count_z(2 * MZ) + NIN * TL * p3_ld<V, MZ>()) * sizeof(V);
+  cudaError_t e = set_smem(k_p3<T, MZ, B>, smem);
   if (e != cudaSuccess) return e;
   const long long nxy = (long long)a.g.nx * a.g.ny;
   dim3 grid((unsigned)((nxy + TL - 1) / TL));
-  k_p3<T, MZ><<<grid, FftPlan<MZ>::G * 6 * TL, smem, s>>>(a);
+  k_p3<T, MZ, B><<<grid, FftPlan<MZ>::G * NIN * TL, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -70,7 +73,7 @@ cudaError_t launch_pass(int which, const PassArgs& a, cudaStream_t s) {
   switch (which) {
     case 1:
       switch (a.g.nx) {
-#define C1(N) case N: return launch_p1<T, N>(a, s);
+#define C1(N) case N: return a.g.bouss ? launch_p1<T, N, true>(a, s) : launch_p1<T, N, false>(a, s);
         DNS_XY_SIZES(C1)
 #undef C1
       }
@@ -84,7 +87,7 @@ cudaError_t launch_pass(int which, const PassArgs& a, cudaStream_t s) {
       break;
     case 3:
       switch (a.g.nz / 2) {
-#define C3(N) case N: return launch_p3<T, N>(a, s);
+#define C3(N) case N: return a.g.bouss ? launch_p3<T, N, true>(a, s) : launch_p3<T, N, false>(a, s);
         DNS_ZH_SIZES(C3)
 #undef C3
       }
@@ -98,7 +101,7 @@ cudaError_t launch_pass(int which, const PassArgs& a, cudaStream_t s) {
       break;
     case 5:
       switch (a.g.nx) {
-#define C5(N) case N: return launch_p5<T, N>(a, s);
+#define C5(N) case N: return a.g.bouss ? launch_p5<T, N, true>(a, s) : launch_p5<T, N, false>(a, s);
         DNS_XY_SIZES(C5)
 #undef C5
       }

@@ -45,31 +45,33 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Deterministic block sum of three values (fixed tree), result valid in thread 0.
-__device__ __forceinline__ void block_sum3(double v[3], double* sh /* 3*32 */) {
+// Deterministic block sum of NV values (fixed tree), result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double v[NV], double* sh /* NV*32 */) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-  for (int q = 0; q < 3; ++q) v[q] = warp_sum(v[q]);
+  for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
   if (lane == 0) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) sh[q * 32 + w] = v[q];
+    for (int q = 0; q < NV; ++q) sh[q * 32 + w] = v[q];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < NV; ++q) {
       double s = 0.0;
       for (int i = 0; i < nw; ++i) s += sh[q * 32 + i];
       v[q] = s;
     }
   }
 }
+__device__ __forceinline__ void block_sum3(double v[3], double* sh) { block_sum<3>(v, sh); }
 
 // Per-block partial sums of (|e| / sc)^2 per component, e = h sum_j (b_j - bhat_j) k_j,
 // sc = atol + rtol max(|u_n|, |u_{n+1}|)  (Section 2.2.1).
 template <int NT>
 __global__ void __launch_bounds__(kRedThreads) k_err_partials(const ErrArgs a) {
-  __shared__ double sh[3 * 32];
+  __shared__ double sh[4 * 32];
   const DnsCtrl* c = a.ctrl;
   if (c->skip) return;
   const double h = c->h_try, rtol = c->rtol, atol = c->atol;
@@ -78,10 +80,11 @@ __global__ void __launch_bounds__(kRedThreads) k_err_partials(const ErrArgs a) {
   const double2* k[NT];
 #pragma unroll
   for (int j = 0; j < NT; ++j) k[j] = c->slot[a.kslot[j]];
-  double acc[3] = {0.0, 0.0, 0.0};
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
   const long long stride = (long long)gridDim.x * blockDim.x;
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {
+  for (int q = 0; q < 4; ++q) {
+    if (q >= a.nc) break;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.M; i += stride) {
       const long long idx = q * a.M + i;
       double2 kv = k[0][idx];
@@ -100,10 +103,10 @@ __global__ void __launch_bounds__(kRedThreads) k_err_partials(const ErrArgs a) {
       acc[q] += fma(er, er, ei * ei) / (sc * sc);
     }
   }
-  block_sum3(acc, sh);
+  block_sum<4>(acc, sh);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) a.partials[blockIdx.x * 3 + q] = acc[q];
+    for (int q = 0; q < 4; ++q) a.partials[blockIdx.x * kRedStride + q] = acc[q];
   }
 }
 
@@ -132,24 +135,24 @@ __global__ void k_begin_attempt(DnsCtrl* c, int method) {
 // h_new = h min(dmax, max(dmin, 0.8 err^(-1/5))), dmax = 1 right after a rejection.
 __global__ void __launch_bounds__(kRedThreads) k_controller(DnsCtrl* c, const double* partials,
                                                             int method, int nstages, int nblk,
-                                                            double nmodes) {
-  __shared__ double sh[3][kRedThreads];
+                                                            double nmodes, int nc) {
+  __shared__ double sh[4][kRedThreads];
   if (c->skip) return;
   const int tid = threadIdx.x;
-  double s[3] = {0.0, 0.0, 0.0};
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
   if (method != 0) {
     for (int b = tid; b < nblk; b += blockDim.x) {
 #pragma unroll
-      for (int q = 0; q < 3; ++q) s[q] += partials[b * 3 + q];
+      for (int q = 0; q < 4; ++q) s[q] += partials[b * kRedStride + q];
     }
   }
 #pragma unroll
-  for (int q = 0; q < 3; ++q) sh[q][tid] = s[q];
+  for (int q = 0; q < 4; ++q) sh[q][tid] = s[q];
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if (tid < w) {
 #pragma unroll
-      for (int q = 0; q < 3; ++q) sh[q][tid] += sh[q][tid + w];
+      for (int q = 0; q < 4; ++q) sh[q][tid] += sh[q][tid + w];
     }
     __syncthreads();
   }
@@ -159,7 +162,7 @@ __global__ void __launch_bounds__(kRedThreads) k_controller(DnsCtrl* c, const do
   double err = 0.0;
   bool nan = false;
   if (method != 0) {
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < nc; ++q) {
       const double e = sqrt(sh[q][0] / nmodes);
       c->errc[q] = e;
       if (e != e) nan = true;
@@ -204,7 +207,7 @@ __global__ void __launch_bounds__(kRedThreads) k_controller(DnsCtrl* c, const do
 
 __global__ void k_ctrl_reset(DnsCtrl* c, double t) {
   c->t = t; c->t_end = t; c->h = 0.0; c->h_try = 0.0; c->err = 0.0;
-  c->errc[0] = c->errc[1] = c->errc[2] = 0.0;
+  c->errc[0] = c->errc[1] = c->errc[2] = c->errc[3] = 0.0;
   c->parity = 0; c->skip = 0; c->need_k1 = 1; c->k1_valid = 0; c->done = 1; c->status = 0;
   c->clipped = 0; c->after_reject = 0; c->accepted = 0;
   c->n_rhs = c->n_acc = c->n_rej = c->n_attempts = c->rejects_in_row = 0;
@@ -221,7 +224,7 @@ __global__ void k_ctrl_config(DnsCtrl* c, double t_end, int method, double rtol,
 }
 
 __global__ void k_gather(const Geom g, const double2* __restrict__ full, double2* __restrict__ cmp) {
-  const long long n = 3 * g.M;
+  const long long n = (long long)g.nc * g.M;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const long long q = i / g.M, r = i - q * g.M;
@@ -234,7 +237,7 @@ __global__ void k_gather(const Geom g, const double2* __restrict__ full, double2
 }
 
 __global__ void k_scatter(const Geom g, const double2* __restrict__ cmp, double2* __restrict__ full) {
-  const long long n = 3 * g.M;
+  const long long n = (long long)g.nc * g.M;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const long long q = i / g.M, r = i - q * g.M;
@@ -310,7 +313,7 @@ __global__ void __launch_bounds__(kRedThreads) k_diag_partials(const Geom g, con
   block_sum3(v, sh);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) partials[blockIdx.x * 3 + q] = v[q];
+    for (int q = 0; q < 3; ++q) partials[blockIdx.x * kRedStride + q] = v[q];
   }
 }
 
@@ -347,8 +350,8 @@ cudaError_t launch_begin_attempt(DnsCtrl* c, int method, cudaStream_t s) {
 }
 
 cudaError_t launch_controller(DnsCtrl* c, const double* partials, int method, int nstages,
-                              double nmodes, cudaStream_t s) {
-  k_controller<<<1, kRedThreads, 0, s>>>(c, partials, method, nstages, kRedBlocks, nmodes);
+                              double nmodes, int nc, cudaStream_t s) {
+  k_controller<<<1, kRedThreads, 0, s>>>(c, partials, method, nstages, kRedBlocks, nmodes, nc);
   return cudaGetLastError();
 }
 
@@ -364,12 +367,12 @@ cudaError_t launch_ctrl_config(DnsCtrl* c, double t_end, int method, double rtol
 }
 
 cudaError_t launch_gather(const Geom& g, const double2* full, double2* compact, cudaStream_t s) {
-  k_gather<<<grid_for(3 * g.M, 256, 152 * 16), 256, 0, s>>>(g, full, compact);
+  k_gather<<<grid_for((long long)g.nc * g.M, 256, 152 * 16), 256, 0, s>>>(g, full, compact);
   return cudaGetLastError();
 }
 
 cudaError_t launch_scatter(const Geom& g, const double2* compact, double2* full, cudaStream_t s) {
-  k_scatter<<<grid_for(3 * g.M, 256, 152 * 16), 256, 0, s>>>(g, compact, full);
+  k_scatter<<<grid_for((long long)g.nc * g.M, 256, 152 * 16), 256, 0, s>>>(g, compact, full);
   return cudaGetLastError();
 }
 

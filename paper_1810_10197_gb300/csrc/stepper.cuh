@@ -26,7 +26,8 @@ struct ErrArgs {
   int kslot[kMaxTerms];
   double coef[kMaxTerms];   // b_j - bhat_j
   long long M;              // modes per component
-  double* partials;         // [kRedBlocks][3]
+  int nc;                   // state components (3 or 4)
+  double* partials;         // [kRedBlocks][4]
 };
 
 // Host launchers (stepper.cu).  All enqueue on stream s and return the launch status.
@@ -34,7 +35,7 @@ cudaError_t launch_stage_sum(const StageArgs& a, cudaStream_t s);
 cudaError_t launch_err_partials(const ErrArgs& a, cudaStream_t s);
 cudaError_t launch_begin_attempt(DnsCtrl* c, int method, cudaStream_t s);
 cudaError_t launch_controller(DnsCtrl* c, const double* partials, int method, int nstages,
-                              double nmodes, cudaStream_t s);
+                              double nmodes, int nc, cudaStream_t s);
 cudaError_t launch_ctrl_reset(DnsCtrl* c, double t, cudaStream_t s);
 cudaError_t launch_ctrl_config(DnsCtrl* c, double t_end, int method, double rtol, double atol,
                                double h0, int max_rejects, cudaStream_t s);
@@ -43,6 +44,7 @@ cudaError_t launch_scatter(const Geom& g, const double2* compact, double2* full,
 cudaError_t launch_copy_slot(DnsCtrl* c, int slot, double2* dst, long long n2, cudaStream_t s);
 cudaError_t launch_forcing_coef(const Geom& g, DnsCtrl* c, int yslot, double kf, double power,
                                 int gate_k1, cudaStream_t s);
+constexpr int kRedStride = 4;      // partial sums per block (components)
 cudaError_t launch_diag_partials(const Geom& g, const double2* u, const double2* f,
                                  double* partials, cudaStream_t s);
 

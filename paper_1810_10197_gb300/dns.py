@@ -58,6 +58,8 @@ _SIGS = {
     "dns_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.POINTER(dns_forcing), C.c_int,
                              C.POINTER(C.c_void_p)]),
     "dns_create_ex": (C.c_int, [C.POINTER(dns_config), C.POINTER(C.c_void_p)]),
+    "dns_create_boussinesq": (C.c_int, [C.POINTER(dns_config), C.c_double, C.c_double,
+                                        C.POINTER(C.c_void_p)]),
     "dns_destroy": (None, [C.c_void_p]),
     "dns_last_error": (C.c_char_p, [C.c_void_p]),
     "dns_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -138,7 +140,8 @@ class Dns:
     """One libdns context (an nx x ny x nz grid on the current CUDA device)."""
 
     def __init__(self, nx, ny=None, nz=None, nu=0.0, precision="fp64", forcing=None,
-                 lengths=None, stream=None):
+                 lengths=None, stream=None, boussinesq=None):
+        """boussinesq=(kappa, ri) selects the Boussinesq form (state of 4 components)."""
         lib = load()
         ny = nx if ny is None else ny
         nz = nx if nz is None else nz
@@ -153,9 +156,14 @@ class Dns:
             cfg.forcing.kind = 1
             cfg.forcing.kf, cfg.forcing.power = float(forcing[0]), float(forcing[1])
         h = C.c_void_p()
-        st = lib.dns_create_ex(C.byref(cfg), C.byref(h))
+        if boussinesq is not None:
+            st = lib.dns_create_boussinesq(C.byref(cfg), float(boussinesq[0]), float(boussinesq[1]),
+                                           C.byref(h))
+        else:
+            st = lib.dns_create_ex(C.byref(cfg), C.byref(h))
         if st != DNS_OK:
-            raise DnsError(st, "dns_create_ex")
+            raise DnsError(st, "dns_create")
+        self.ncomp = 4 if boussinesq is not None else 3
         self._lib = lib
         self._h = h
         self.shape = (nx, ny, nz)
@@ -196,7 +204,7 @@ class Dns:
     def get_state(self, out=None):
         """Current state; into `out` (device tensor or host array) or a new numpy array."""
         if out is None:
-            out = np.empty((3,) + self.shape[:2] + (self.nzh,), dtype=np.complex128)
+            out = np.empty((self.ncomp,) + self.shape[:2] + (self.nzh,), dtype=np.complex128)
         self._check(self._lib.dns_get_state(self._h, C.c_void_p(_ptr(out)), _where(out)), "dns_get_state")
         return out
 
