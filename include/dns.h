@@ -163,6 +163,46 @@ int dns_profile_count(dns_ctx* ctx);
 dns_status dns_profile_get(dns_ctx* ctx, int i, const char** name, long long* launches,
                            double* total_ms);
 
+/* Attempt trace.  dns_set_trace allocates room for `capacity` records in the context (0
+ * frees it) and clears it; each later attempt appends one record of DNS_TRACE_COLS doubles:
+ *   t at the start, h used, err, accepted (1/0), RHS evaluations so far, E, Omega, eps
+ * The last three (Section 3.1, of the state after the attempt) are filled only when
+ * `diagnostics` != 0 (NaN otherwise; eps also NaN for RK4).  Records beyond the capacity
+ * are dropped.  dns_trace copies min(n, cap) records to the host array `out` (row-major)
+ * and returns the number recorded in *n.  Synchronous. */
+#define DNS_TRACE_COLS 8
+dns_status dns_set_trace(dns_ctx* ctx, long long capacity, int diagnostics);
+dns_status dns_trace(dns_ctx* ctx, double* out, long long cap, long long* n);
+
+/* Step-size controller of the adaptive method.  DNS_CTRL_I: Section 2.2.1 (default).
+ * DNS_CTRL_PI: after an accepted step h_new = h min(2, max(0.01, 0.8 err^-0.14 err_prev^0.08))
+ * (the PI controller the paper names as future work, Section 4, with exponents 0.7/(q+1),
+ * 0.4/(q+1)).  DNS_CTRL_MLP: after an accepted step, once 4 accepted steps are known, a
+ * learned proposal h_new = h exp(clamp(y, log 0.01, log 2)) from the network below (capped at
+ * 1 right after a rejection).  In every variant the embedded error norm still accepts or
+ * rejects each step, and rejections (and non-finite proposals) use the Section 2.2.1 factor.
+ * mlp_params_dev: DNS_MLP_PARAMS floats on the device (copied in), for DNS_CTRL_MLP only. */
+typedef enum { DNS_CTRL_I = 0, DNS_CTRL_PI = 1, DNS_CTRL_MLP = 2 } dns_controller;
+dns_status dns_set_controller(dns_ctx* ctx, int kind, const float* mlp_params_dev);
+
+/* The learned proposal's network (not in the paper): inputs 16 features of the 4 newest
+ * accepted steps (newest first, each [log10 err, log(h_i/h_0), rejections before it,
+ * log(h_i/h_{i+1})]), output log(h_next/h).  Parameters (float): W1[64][16], b1[64],
+ * W2[64][64], b2[64], w3[64], b3; y = w3.relu(W2 relu(W1 x + b1) + b2) + b3, evaluated with the
+ * weights rounded to bfloat16 and FP32 arithmetic.  All pointers are device pointers;
+ * asynchronous on `stream`.
+ *   dns_mlp_forward:   y[b] for x[n][16].
+ *   dns_mlp_loss_grad: mean squared error against t[n] and its gradient (n <= 128).
+ *   dns_mlp_train:     `steps` Adam steps (lr, beta 0.9/0.999) on random mini-batches of
+ *                      `batch` (<= 128) samples drawn with a counter hash of `seed`; params
+ *                      updated in place; loss_hist[steps] (may be NULL) receives batch losses. */
+#define DNS_MLP_PARAMS 5313
+dns_status dns_mlp_forward(const float* params, const float* x, int n, float* y, void* stream);
+dns_status dns_mlp_loss_grad(const float* params, const float* x, const float* t, int n, float* grad,
+                             float* loss, void* stream);
+dns_status dns_mlp_train(float* params, const float* x, const float* t, int n, int steps, int batch,
+                         float lr, unsigned seed, float* loss_hist, void* stream);
+
 /* Grid facts: retained cut-offs K[3] and the number of device bytes the context holds. */
 dns_status dns_query(const dns_ctx* ctx, int* K3, size_t* device_bytes);
 

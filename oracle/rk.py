@@ -176,6 +176,20 @@ def controller_factor(err: float, after_reject: bool) -> float:
     return min(dmax, max(DELTA_MIN, DELTA * err ** (-1.0 / (BS5.embedded_order + 1))))
 
 
+# PI controller (Gustafsson; Hairer & Wanner II, Sec. IV.2): the paper names it as future work
+# (Section 4).  Exponents alpha = 0.7/(q+1), beta = 0.4/(q+1), q = 4.
+PI_ALPHA = 0.7 / 5.0
+PI_BETA = 0.4 / 5.0
+
+
+def pi_factor(err: float, err_prev: float, after_reject: bool) -> float:
+    """min(dmax, max(dmin, 0.8 err^(-alpha) err_prev^beta)) for an accepted step."""
+    dmax = 1.0 if after_reject else DELTA_MAX
+    if err == 0.0:
+        return dmax
+    return min(dmax, max(DELTA_MIN, DELTA * err ** (-PI_ALPHA) * err_prev ** PI_BETA))
+
+
 @dataclass
 class Result:
     u: np.ndarray
@@ -191,12 +205,16 @@ class Result:
 def integrate(f: Callable, u0: np.ndarray, t0: float, t_end: float, method: str, h0: float,
               rtol: float = 1e-6, atol: float = 1e-6, nmodes: Optional[int] = None,
               max_rejects: int = 30, max_steps: int = 10 ** 7,
-              on_accept: Optional[Callable] = None) -> Result:
+              on_accept: Optional[Callable] = None, controller="I") -> Result:
     """Integrate u' = f(u) from t0 to t_end.
 
     method: "RK4" (fixed h0), "BS5_FIXED" (fixed h0, error logged), "BS5_ADAPTIVE",
     "DP5_FIXED", "DP5_ADAPTIVE".  The last step is clipped to land on t_end.
+    controller (adaptive methods): "I" (Section 2.2.1), "PI", or ("MLP", params): after an
+    accepted step the PI / network proposal replaces the factor; after a rejection, and for
+    the first 4 accepted steps (MLP), the Section 2.2.1 factor is used.
     """
+    from . import mlp as _mlp
     tabname, _, mode = method.partition("_")
     tab = TABLEAUS[tabname]
     adaptive = mode == "ADAPTIVE"
@@ -210,6 +228,9 @@ def integrate(f: Callable, u0: np.ndarray, t0: float, t_end: float, method: str,
     after_reject = False
     rejects_in_row = 0
     steps = 0
+    err_prev = 1.0
+    hist = []            # accepted (err, h, rejections before it), newest first
+    rej_since = 0
     while t < t_end and steps < max_steps:
         steps += 1
         # last step: land exactly on t_end (also when h falls short of it by rounding only)
@@ -224,6 +245,14 @@ def integrate(f: Callable, u0: np.ndarray, t0: float, t_end: float, method: str,
         if adaptive:
             accepted = math.isfinite(err) and err <= 1.0
             fac = controller_factor(err, after_reject)
+            if accepted and controller == "PI":
+                fac = pi_factor(err, err_prev, after_reject)
+            elif accepted and isinstance(controller, tuple) and controller[0] == "MLP":
+                hist = [(err, h_step, rej_since)] + hist[:4]
+                if len(hist) >= 4:
+                    prop = _mlp.propose_factor(controller[1], hist)
+                    if prop is not None:
+                        fac = min(1.0, prop) if after_reject else prop
             h_new = h_step * fac
         else:
             accepted = True
@@ -235,6 +264,9 @@ def integrate(f: Callable, u0: np.ndarray, t0: float, t_end: float, method: str,
             k1 = ks[-1] if tab.fsal else None
             after_reject = False
             rejects_in_row = 0
+            rej_since = 0
+            if err > 0:
+                err_prev = err
             res.n_acc += 1
             if on_accept is not None:
                 on_accept(t, u, ks[-1] if tab.fsal else None)
@@ -242,6 +274,7 @@ def integrate(f: Callable, u0: np.ndarray, t0: float, t_end: float, method: str,
             after_reject = True
             k1 = ks[0] if tab.fsal else None
             rejects_in_row += 1
+            rej_since += 1
             res.n_rej += 1
             if rejects_in_row > max_rejects:
                 res.status = "max_rejects"

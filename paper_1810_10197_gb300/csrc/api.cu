@@ -12,6 +12,7 @@
 #include "common.cuh"
 #include "passes.cuh"
 #include "stepper.cuh"
+#include "mlp.cuh"
 
 using namespace dns;
 
@@ -97,6 +98,9 @@ struct dns_ctx {
   bool failed = false;
   bool has_state = false;
   std::string err;
+  double* trace_buf = nullptr;     // attempt records (dns_set_trace)
+  int trace_diag = 0;
+  float* mlp_buf = nullptr;        // learned-controller parameters (dns_set_controller)
   bool prof = false;
   std::vector<ProfRec> recs;
   std::vector<cudaEvent_t> pool;
@@ -242,6 +246,7 @@ dns_status enqueue_attempt(dns_ctx* c, int method) {
     CK(timed(c, PR_CTRL, [&] {
          return launch_controller(c->ctrl, c->partials, 0, 4, c->g.nmodes_half, c->g.nc, c->stream);
        }), "controller");
+    if (c->trace_diag) CK(launch_trace_diag(c->g, c->ctrl, c->partials, 0, c->stream), "trace diagnostics");
     return DNS_OK;
   }
   // BS5: k_1 only when not carried over (first same as last)
@@ -271,6 +276,7 @@ dns_status enqueue_attempt(dns_ctx* c, int method) {
   CK(timed(c, PR_CTRL, [&] {
        return launch_controller(c->ctrl, c->partials, method, 8, c->g.nmodes_half, c->g.nc, c->stream);
      }), "controller");
+  if (c->trace_diag) CK(launch_trace_diag(c->g, c->ctrl, c->partials, method, c->stream), "trace diagnostics");
   return DNS_OK;
 }
 
@@ -427,7 +433,7 @@ void dns_destroy(dns_ctx* c) {
   else cudaDeviceSynchronize();
   void* ptrs[] = {c->uu[0], c->uu[1], c->kk[0], c->kk[1], c->ystage, c->rhs_in, c->rhs_out,
                   c->full_stage, c->bufA, c->bufB, c->tw[0], c->tw[1], c->tw[2], c->ctrl,
-                  c->ctrl_rhs, c->partials};
+                  c->ctrl_rhs, c->partials, c->trace_buf, c->mlp_buf};
   for (void* p : ptrs) if (p) cudaFree(p);
   for (int i = 2; i <= 7; ++i) if (c->kfix[i]) cudaFree(c->kfix[i]);
   if (c->host_ctrl) cudaFreeHost(c->host_ctrl);
@@ -614,6 +620,44 @@ dns_status dns_profile_get(dns_ctx* c, int i, const char** name, long long* laun
   if (name) *name = kPassNames[i];
   if (launches) *launches = n;
   if (total_ms) *total_ms = ms;
+  return DNS_OK;
+}
+
+dns_status dns_set_trace(dns_ctx* c, long long capacity, int diagnostics) {
+  dns_status s = check_ctx(c);
+  if (s != DNS_OK) return s;
+  if (capacity < 0) return fail(c, DNS_ERR_ARG, "negative trace capacity");
+  CK(cudaStreamSynchronize(c->stream), "synchronize");
+  if (c->trace_buf) { cudaFree(c->trace_buf); c->trace_buf = nullptr; }
+  if (capacity > 0 && (s = alloc(c, (void**)&c->trace_buf, (size_t)capacity * kTraceCols * sizeof(double))) != DNS_OK)
+    return s;
+  c->trace_diag = capacity > 0 && diagnostics != 0;
+  CK(launch_ctrl_set_trace(c->ctrl, c->trace_buf, capacity, c->trace_diag, c->stream), "trace set");
+  return DNS_OK;
+}
+
+dns_status dns_trace(dns_ctx* c, double* out, long long cap, long long* n) {
+  dns_status s = check_ctx(c);
+  if (s != DNS_OK) return s;
+  if ((s = read_ctrl(c)) != DNS_OK) return s;
+  const long long have = c->host_ctrl->trace_n;
+  if (n) *n = have;
+  const long long m = std::min(have, cap);
+  if (out && m > 0 && c->trace_buf)
+    CK(cudaMemcpy(out, c->trace_buf, (size_t)m * kTraceCols * sizeof(double), cudaMemcpyDeviceToHost), "trace read");
+  return DNS_OK;
+}
+
+dns_status dns_set_controller(dns_ctx* c, int kind, const float* mlp_params_dev) {
+  dns_status s = check_ctx(c);
+  if (s != DNS_OK) return s;
+  if (kind < 0 || kind > 2 || (kind == 2 && !mlp_params_dev)) return fail(c, DNS_ERR_ARG, "bad controller");
+  if (kind == 2) {
+    if (!c->mlp_buf && (s = alloc(c, (void**)&c->mlp_buf, kMlpParams * sizeof(float))) != DNS_OK) return s;
+    CK(cudaMemcpyAsync(c->mlp_buf, mlp_params_dev, kMlpParams * sizeof(float), cudaMemcpyDeviceToDevice,
+                       c->stream), "copy network");
+  }
+  CK(launch_ctrl_set_controller(c->ctrl, kind, kind == 2 ? c->mlp_buf : nullptr, c->stream), "controller set");
   return DNS_OK;
 }
 

@@ -110,7 +110,22 @@ struct DnsCtrl {
   int max_rejects;
   int pad_;
   long long n_rhs, n_acc, n_rej, n_attempts, rejects_in_row;
+  // controller variant: 0 = Section 2.2.1, 1 = PI, 2 = learned proposal (MLP)
+  int ctrl_kind;
+  int hist_n;           // accepted steps in the history (<= 5), newest first
+  int rej_since;        // rejections since the last accepted step
+  int trace_diag;       // trace E, Omega, eps after every attempt
+  double err_prev;      // err of the last accepted step (PI)
+  double hist_err[5], hist_h[5];
+  int hist_rej[5];
+  int pad2_;
+  const float* mlp;     // network parameters of the learned proposal
+  double* trace;        // [trace_cap][kTraceCols] attempt records
+  long long trace_cap, trace_n;
 };
+
+// attempt record: t at the start, h used, err, accepted, n_rhs so far, E, Omega, eps
+constexpr int kTraceCols = 8;
 
 __device__ __forceinline__ const double2* resolve_in(const double2* p, const DnsCtrl* c, int slot) {
   return (c && slot >= 0) ? c->slot[slot] : p;

@@ -1,6 +1,7 @@
 // Runge-Kutta stage sums, embedded error norm and the device step controller (Section 2.2 of
 // arXiv:1810.10197), plus the copies between the half-spectrum layout and the retained box.
 #include "stepper.cuh"
+#include "mlp.cuh"
 
 namespace dns {
 
@@ -133,10 +134,18 @@ __global__ void k_begin_attempt(DnsCtrl* c, int method) {
 
 // Section 2.2.1: err = max_j sqrt(S_j / (nx ny (nz/2+1))); accept iff err <= 1;
 // h_new = h min(dmax, max(dmin, 0.8 err^(-1/5))), dmax = 1 right after a rejection.
+// Variants after an accepted step: PI (0.8 err^(-0.7/5) err_prev^(0.4/5)) or the learned
+// proposal exp(clamp(mlp(features))) once 4 accepted steps are known; after a rejection and
+// when the proposal is not finite the Section 2.2.1 factor is used.
 __global__ void __launch_bounds__(kRedThreads) k_controller(DnsCtrl* c, const double* partials,
                                                             int method, int nstages, int nblk,
                                                             double nmodes, int nc) {
   __shared__ double sh[4][kRedThreads];
+  __shared__ float feat[kMlpIn];
+  __shared__ float work[2 * kMlpH];
+  __shared__ int use_mlp;
+  __shared__ double s_err, s_fac;
+  __shared__ int s_accept;
   if (c->skip) return;
   const int tid = threadIdx.x;
   double s[4] = {0.0, 0.0, 0.0, 0.0};
@@ -156,44 +165,86 @@ __global__ void __launch_bounds__(kRedThreads) k_controller(DnsCtrl* c, const do
     }
     __syncthreads();
   }
-  if (tid != 0) return;
-  c->n_attempts += 1;
-  c->n_rhs += (nstages - 1) + c->need_k1;
-  double err = 0.0;
-  bool nan = false;
-  if (method != 0) {
-    for (int q = 0; q < nc; ++q) {
-      const double e = sqrt(sh[q][0] / nmodes);
-      c->errc[q] = e;
-      if (e != e) nan = true;
-      err = e > err ? e : err;
+  if (tid == 0) {
+    c->n_attempts += 1;
+    c->n_rhs += (nstages - 1) + c->need_k1;
+    double err = 0.0;
+    bool nan = false;
+    if (method != 0) {
+      for (int q = 0; q < nc; ++q) {
+        const double e = sqrt(sh[q][0] / nmodes);
+        c->errc[q] = e;
+        if (e != e) nan = true;
+        err = e > err ? e : err;
+      }
+      if (nan) err = __longlong_as_double(0x7ff8000000000000ULL);
+      c->k1_valid = 1;
     }
-    if (nan) err = __longlong_as_double(0x7ff8000000000000ULL);
-    c->k1_valid = 1;
+    bool accept = true;
+    double fac = 1.0;
+    int mlp_now = 0;
+    if (method == 2) {
+      const bool fin = isfinite(err);
+      accept = fin && err <= 1.0;
+      const double dmax = c->after_reject ? 1.0 : 2.0;
+      if (!fin) fac = 0.01;
+      else if (err == 0.0) fac = dmax;
+      else fac = fmin(dmax, fmax(0.01, 0.8 * pow(err, -1.0 / 5.0)));
+      if (accept && c->ctrl_kind == 1 && err > 0.0)
+        fac = fmin(dmax, fmax(0.01, 0.8 * pow(err, -(0.7 / 5.0)) * pow(c->err_prev, 0.4 / 5.0)));
+      if (accept && c->ctrl_kind == 2 && c->mlp) {
+        for (int i = 4; i > 0; --i) {
+          c->hist_err[i] = c->hist_err[i - 1]; c->hist_h[i] = c->hist_h[i - 1]; c->hist_rej[i] = c->hist_rej[i - 1];
+        }
+        c->hist_err[0] = err; c->hist_h[0] = c->h_try; c->hist_rej[0] = c->rej_since;
+        c->hist_n = min(c->hist_n + 1, 5);
+        if (c->hist_n >= 4) {
+          const double h0 = c->hist_h[0];
+          for (int i = 0; i < 4; ++i) {
+            const double hp = (i + 1 < c->hist_n) ? c->hist_h[i + 1] : c->hist_h[i];
+            feat[4 * i + 0] = (float)log10(fmax(c->hist_err[i], 1e-300));
+            feat[4 * i + 1] = (float)log(c->hist_h[i] / h0);
+            feat[4 * i + 2] = (float)c->hist_rej[i];
+            feat[4 * i + 3] = (float)log(c->hist_h[i] / hp);
+          }
+          mlp_now = 1;
+        }
+      }
+    }
+    s_err = err;
+    s_fac = fac;
+    s_accept = accept ? 1 : 0;
+    use_mlp = mlp_now;
   }
+  __syncthreads();
+  float y = 0.f;
+  if (use_mlp) y = mlp_forward_block(c->mlp, feat, work);
+  if (tid != 0) return;
+  const double err = s_err;
+  const bool accept = s_accept != 0;
+  double fac = s_fac;
+  if (use_mlp && isfinite(y)) {
+    const double lf = fmin(log(2.0), fmax(log(0.01), (double)y));
+    fac = exp(lf);
+    if (c->after_reject) fac = fmin(1.0, fac);
+  }
+  const double t_before = c->t;
   c->err = err;
-  bool accept = true;
   double h_new = c->h;
-  if (method == 2) {
-    const bool fin = isfinite(err);
-    accept = fin && err <= 1.0;
-    const double dmax = c->after_reject ? 1.0 : 2.0;
-    double fac;
-    if (!fin) fac = 0.01;
-    else if (err == 0.0) fac = dmax;
-    else fac = fmin(dmax, fmax(0.01, 0.8 * pow(err, -1.0 / 5.0)));
-    h_new = c->h_try * fac;
-  }
+  if (method == 2) h_new = c->h_try * fac;
   if (accept) {
     c->t = c->clipped ? c->t_end : c->t + c->h_try;
     c->parity ^= 1;
     c->after_reject = 0;
     c->rejects_in_row = 0;
+    c->rej_since = 0;
+    if (err > 0.0) c->err_prev = err;
     c->n_acc += 1;
     if (method == 0) c->k1_valid = 0;
   } else {
     c->after_reject = 1;
     c->rejects_in_row += 1;
+    c->rej_since += 1;
     c->n_rej += 1;
     if (c->rejects_in_row > c->max_rejects) {
       c->status = isfinite(err) ? ST_MAX_REJECTS : ST_NONFINITE;
@@ -203,9 +254,85 @@ __global__ void __launch_bounds__(kRedThreads) k_controller(DnsCtrl* c, const do
   c->accepted = accept ? 1 : 0;
   c->h = h_new;
   if (c->t >= c->t_end) c->done = 1;
+  if (c->trace && c->trace_n < c->trace_cap) {
+    double* r = c->trace + c->trace_n * kTraceCols;
+    const double qnan = __longlong_as_double(0x7ff8000000000000ULL);
+    r[0] = t_before; r[1] = c->h_try; r[2] = err; r[3] = accept ? 1.0 : 0.0; r[4] = (double)c->n_rhs;
+    r[5] = qnan; r[6] = qnan; r[7] = qnan;
+    c->trace_n += 1;
+  }
+}
+
+// E, Omega and eps of the current state for the last trace record (eps from the carried-over
+// derivative k_1 = f(u_n) of a first-same-as-last pair).
+__global__ void __launch_bounds__(kRedThreads) k_trace_partials(const Geom g, const DnsCtrl* c,
+                                                                double* partials) {
+  __shared__ double sh[3 * 32];
+  if (c->skip || !c->trace_diag || !c->trace) return;
+  const double2* __restrict__ u = c->uu[c->parity];
+  const double2* __restrict__ f = c->kk[c->parity];
+  double v[3] = {0.0, 0.0, 0.0};
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < g.M; r += stride) {
+    const int ix = (int)(r / g.MyMz), rem = (int)(r - (long long)ix * g.MyMz);
+    const int jy = rem / g.Mz, kz = rem - jy * g.Mz;
+    const double kx = g.sx * signed_mode(ix, g.Kx, g.Mx), ky = g.sy * signed_mode(jy, g.Ky, g.My);
+    const double kzz = g.sz * kz;
+    const double k2 = kx * kx + ky * ky + kzz * kzz;
+    const double w = kz == 0 ? 1.0 : 2.0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const double2 a = u[q * g.M + r], b = f[q * g.M + r];
+      const double m2 = a.x * a.x + a.y * a.y;
+      v[0] += w * m2;
+      v[1] += w * k2 * m2;
+      v[2] += w * (a.x * b.x + a.y * b.y);
+    }
+  }
+  block_sum3(v, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) partials[blockIdx.x * kRedStride + q] = v[q];
+  }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_trace_finish(const Geom g, DnsCtrl* c, const double* partials,
+                                                              int nblk, int method) {
+  __shared__ double sh[3][kRedThreads];
+  if (c->skip || !c->trace_diag || !c->trace || c->trace_n == 0) return;
+  const int tid = threadIdx.x;
+  double s[3] = {0.0, 0.0, 0.0};
+  for (int b = tid; b < nblk; b += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) s[q] += partials[b * kRedStride + q];
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) sh[q][tid] = s[q];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (tid < w) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) sh[q][tid] += sh[q][tid + w];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    double* r = c->trace + (c->trace_n - 1) * kTraceCols;
+    const double n6 = g.inv_n3 * g.inv_n3;
+    r[5] = 0.5 * sh[0][0] * n6;
+    r[6] = 0.5 * sh[1][0] * n6;
+    r[7] = (method != 0 && c->k1_valid) ? -sh[2][0] * n6 : __longlong_as_double(0x7ff8000000000000ULL);
+  }
+}
+
+__global__ void k_ctrl_set(DnsCtrl* c, int what, int kind, const float* mlp, double* trace,
+                           long long cap, int diag) {
+  if (what == 0) { c->ctrl_kind = kind; c->mlp = mlp; c->hist_n = 0; }
+  else { c->trace = trace; c->trace_cap = cap; c->trace_n = 0; c->trace_diag = diag; }
 }
 
 __global__ void k_ctrl_reset(DnsCtrl* c, double t) {
+  c->hist_n = 0; c->rej_since = 0; c->err_prev = 1.0; c->trace_n = 0;
   c->t = t; c->t_end = t; c->h = 0.0; c->h_try = 0.0; c->err = 0.0;
   c->errc[0] = c->errc[1] = c->errc[2] = c->errc[3] = 0.0;
   c->parity = 0; c->skip = 0; c->need_k1 = 1; c->k1_valid = 0; c->done = 1; c->status = 0;
@@ -352,6 +479,22 @@ cudaError_t launch_begin_attempt(DnsCtrl* c, int method, cudaStream_t s) {
 cudaError_t launch_controller(DnsCtrl* c, const double* partials, int method, int nstages,
                               double nmodes, int nc, cudaStream_t s) {
   k_controller<<<1, kRedThreads, 0, s>>>(c, partials, method, nstages, kRedBlocks, nmodes, nc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace_diag(const Geom& g, DnsCtrl* c, double* partials, int method, cudaStream_t s) {
+  k_trace_partials<<<kRedBlocks, kRedThreads, 0, s>>>(g, c, partials);
+  k_trace_finish<<<1, kRedThreads, 0, s>>>(g, c, partials, kRedBlocks, method);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ctrl_set_controller(DnsCtrl* c, int kind, const float* mlp, cudaStream_t s) {
+  k_ctrl_set<<<1, 1, 0, s>>>(c, 0, kind, mlp, nullptr, 0, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ctrl_set_trace(DnsCtrl* c, double* trace, long long cap, int diag, cudaStream_t s) {
+  k_ctrl_set<<<1, 1, 0, s>>>(c, 1, 0, nullptr, trace, cap, diag);
   return cudaGetLastError();
 }
 

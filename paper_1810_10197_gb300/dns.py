@@ -82,7 +82,18 @@ _SIGS = {
     "dns_query": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_size_t)]),
     "dns_rhs_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p,
                                   C.c_void_p]),
+    "dns_set_trace": (C.c_int, [C.c_void_p, C.c_longlong, C.c_int]),
+    "dns_trace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.POINTER(C.c_longlong)]),
+    "dns_set_controller": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "dns_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "dns_mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                                    C.c_void_p, C.c_void_p]),
+    "dns_mlp_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                C.c_float, C.c_uint, C.c_void_p, C.c_void_p]),
 }
+TRACE_COLS = 8
+MLP_PARAMS = 5313
+CONTROLLERS = {"I": 0, "PI": 1, "MLP": 2}
 
 
 def load(path: Optional[str] = None):
@@ -257,6 +268,24 @@ class Dns:
                 out[name.value.decode()] = (n.value, ms.value)
         return out
 
+    def set_trace(self, capacity, diagnostics=False):
+        self._check(self._lib.dns_set_trace(self._h, int(capacity), 1 if diagnostics else 0), "dns_set_trace")
+
+    def trace(self):
+        """Attempt records as an (n, 8) array: t, h, err, accepted, n_rhs, E, Omega, eps."""
+        n = C.c_longlong()
+        self._check(self._lib.dns_trace(self._h, None, 0, C.byref(n)), "dns_trace")
+        out = np.empty((n.value, TRACE_COLS))
+        if n.value:
+            self._check(self._lib.dns_trace(self._h, C.c_void_p(out.ctypes.data), n.value, C.byref(n)),
+                        "dns_trace")
+        return out
+
+    def set_controller(self, kind, params_dev=None):
+        k = CONTROLLERS[kind] if isinstance(kind, str) else int(kind)
+        self._check(self._lib.dns_set_controller(self._h, k, C.c_void_p(_ptr(params_dev)) if params_dev is not None
+                                                 else None), "dns_set_controller")
+
     def query(self):
         K = (C.c_int * 3)()
         nb = C.c_size_t()
@@ -270,3 +299,26 @@ def dns_rhs_noalloc(nx, ny, nz, nu, uhat_dev, f_dev, stream=None):
     h = getattr(stream, "cuda_stream", stream)
     return lib.dns_rhs_noalloc(int(nx), int(ny), int(nz), float(nu), C.c_void_p(_ptr(uhat_dev)),
                                C.c_void_p(_ptr(f_dev)), C.c_void_p(h) if h else None)
+
+
+def _st(stream):
+    h = getattr(stream, "cuda_stream", stream)
+    return C.c_void_p(h) if h else None
+
+
+def dns_mlp_forward(params, x, y, stream=None):
+    """y[b] = network(x[b]) for device float32 tensors params[5313], x[n,16], y[n]."""
+    return load().dns_mlp_forward(C.c_void_p(_ptr(params)), C.c_void_p(_ptr(x)), int(x.shape[0]),
+                                  C.c_void_p(_ptr(y)), _st(stream))
+
+
+def dns_mlp_loss_grad(params, x, t, grad, loss, stream=None):
+    return load().dns_mlp_loss_grad(C.c_void_p(_ptr(params)), C.c_void_p(_ptr(x)), C.c_void_p(_ptr(t)),
+                                    int(x.shape[0]), C.c_void_p(_ptr(grad)), C.c_void_p(_ptr(loss)),
+                                    _st(stream))
+
+
+def dns_mlp_train(params, x, t, steps, batch=128, lr=1e-3, seed=0, loss_hist=None, stream=None):
+    return load().dns_mlp_train(C.c_void_p(_ptr(params)), C.c_void_p(_ptr(x)), C.c_void_p(_ptr(t)),
+                                int(x.shape[0]), int(steps), int(batch), float(lr), int(seed) & 0xFFFFFFFF,
+                                C.c_void_p(_ptr(loss_hist)) if loss_hist is not None else None, _st(stream))

@@ -1,0 +1,75 @@
+"""Training pipeline for the learned step-size proposal (DNS_CTRL_MLP).
+
+Trajectories come from the device attempt trace (dns_set_trace / dns_trace) of runs with the
+Section 2.2.1 controller; the training pairs are built on the host (a few thousand rows)
+and the network is trained on the GPU by the library's own kernels (dns_mlp_train).
+
+Features at accepted step n (newest first, i = 0..3, h_0 = h_n):
+    [log10 err_i, log(h_i / h_0), rejections just before step i, log(h_i / h_{i+1})]
+Target: log(h*_n / h_n) with h*_n = h_{n+1} (0.8^5 / err_{n+1})^(1/5), n+1 the next accepted
+step: the step that in hindsight gives the error 0.8^5 the controller aims for.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import dns as _dns
+
+
+def _features(hist):
+    h0 = hist[0][1]
+    out = []
+    for i in range(4):
+        err, h, rej = hist[i]
+        hp = hist[i + 1][1] if i + 1 < len(hist) else h
+        out += [math.log10(max(err, 1e-300)), math.log(h / h0), float(rej), math.log(h / hp)]
+    return out
+
+
+def pairs_from_trace(trace: np.ndarray):
+    """(X[n,16], T[n]) from an attempt trace (columns t, h, err, accepted, ...)."""
+    acc, rej = [], 0
+    for row in trace:
+        h, err, ok = float(row[1]), float(row[2]), row[3] > 0.5
+        if ok:
+            acc.append((err, h, rej))
+            rej = 0
+        else:
+            rej += 1
+    X, T = [], []
+    for n in range(3, len(acc) - 1):
+        err1, h1, _ = acc[n + 1]
+        if not (err1 > 0 and math.isfinite(err1)):
+            continue
+        hist = [acc[n - i] for i in range(min(5, n + 1))]
+        X.append(_features(hist))
+        T.append(math.log(h1 * (0.8 ** 5 / err1) ** 0.2 / acc[n][1]))
+    return np.asarray(X, dtype=np.float32).reshape(-1, 16), np.asarray(T, dtype=np.float32)
+
+
+def init_params(seed=0):
+    """He-style initial parameters (float32), layout of dns.h DNS_MLP_PARAMS."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.standard_normal((64, 16)) * math.sqrt(2.0 / 16)
+    W2 = rng.standard_normal((64, 64)) * math.sqrt(2.0 / 64)
+    w3 = rng.standard_normal(64) * math.sqrt(1.0 / 64)
+    p = np.concatenate([W1.ravel(), np.zeros(64), W2.ravel(), np.zeros(64), w3, [0.0]])
+    return p.astype(np.float32)
+
+
+def train(X: np.ndarray, T: np.ndarray, steps=3000, batch=128, lr=2e-3, seed=0):
+    """Train on the GPU; returns (params as a device tensor, batch-loss history)."""
+    import torch
+    dev = torch.device("cuda")
+    x = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(dev)
+    t = torch.from_numpy(np.ascontiguousarray(T, dtype=np.float32)).to(dev)
+    p = torch.from_numpy(init_params(seed)).to(dev)
+    hist = torch.zeros(max(steps, 1), dtype=torch.float32, device=dev)
+    st = _dns.dns_mlp_train(p, x, t, steps, batch=min(batch, 128), lr=lr, seed=seed, loss_hist=hist,
+                            stream=torch.cuda.current_stream())
+    if st != 0:
+        raise _dns.DnsError(st, "dns_mlp_train")
+    torch.cuda.synchronize()
+    return p, hist.cpu().numpy()

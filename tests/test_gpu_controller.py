@@ -1,0 +1,184 @@
+"""Learned and PI step-size controllers, the network kernels and the attempt trace.
+
+* network forward and gradient (dns_mlp_forward / dns_mlp_loss_grad, bf16 weights, FP32
+  arithmetic) against the FP64 oracle with the same bf16-rounded weights: 1e-5 / 1e-4
+  relative (FP32 accumulation over 16..64 terms and up to 128 samples);
+* training on the GPU lowers the loss;
+* PI and MLP controllers on the device make the same accept/reject decisions as the oracle;
+* the trace's diagnostics match the oracle's (Section 3.1);
+* the gain of the trained network over the Section 2.2.1 controller on a Rayleigh-Taylor run
+  (trained on Taylor-Green and forced-turbulence trajectories) is measured and reported.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle import diag, mlp, rk
+from oracle import spectral as sp
+from tests.gpu_helpers import lib_ready, rel_l2, require_gpu, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    require_gpu()
+    lib_ready()
+
+
+def dev32(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def test_network_forward_and_gradient_match_oracle():
+    from paper_1810_10197_gb300.dns import dns_mlp_forward, dns_mlp_loss_grad
+    rng = np.random.default_rng(5)
+    p = (mlp.init_params(2) + 0.05 * rng.standard_normal(mlp.N_PARAMS)).astype(np.float32)
+    X = rng.standard_normal((100, 16)).astype(np.float32)
+    t = rng.standard_normal(100).astype(np.float32)
+    pr = mlp.round_bf16(p)
+    y_ref, _ = mlp.forward(pr, X.astype(np.float64))
+    L_ref, g_ref = mlp.loss_and_grad(pr, X.astype(np.float64), t.astype(np.float64))
+    pd, xd, td = dev32(p), dev32(X), dev32(t)
+    y = torch.empty(100, dtype=torch.float32, device="cuda")
+    g = torch.empty(mlp.N_PARAMS, dtype=torch.float32, device="cuda")
+    L = torch.empty(1, dtype=torch.float32, device="cuda")
+    assert dns_mlp_forward(pd, xd, y) == 0
+    assert dns_mlp_loss_grad(pd, xd, td, g, L) == 0
+    torch.cuda.synchronize()
+    assert np.max(np.abs(y.cpu().numpy() - y_ref)) < 1e-5 * np.max(np.abs(y_ref))
+    assert abs(L.item() - L_ref) < 1e-5 * L_ref
+    gg = g.cpu().numpy()
+    assert np.max(np.abs(gg - g_ref)) < 1e-4 * np.max(np.abs(g_ref))
+    # parameters are not modified by the gradient call
+    assert np.array_equal(pd.cpu().numpy(), p)
+
+
+def test_training_on_gpu_lowers_the_loss():
+    from paper_1810_10197_gb300 import learned
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((2000, 16)).astype(np.float32)
+    T = (np.tanh(X[:, 0] - 0.5 * X[:, 3]) + 0.3 * X[:, 5]).astype(np.float32)
+    p, hist = learned.train(X, T, steps=1500, lr=2e-3, seed=1)
+    assert np.all(np.isfinite(hist))
+    assert hist[-100:].mean() < 0.1 * hist[:20].mean()
+
+
+def run_pair(controller, params=None, shape=(32, 32, 32), nu=0.01, T=1.0, tol=1e-8):
+    from paper_1810_10197_gb300 import Dns
+    g = sp.Grid(*shape)
+    uh = g.dealias(syn.taylor_green_3d_hat(*shape))
+    ctl = controller if controller != "MLP" else ("MLP", params)
+    ref = rk.integrate(lambda y: sp.rhs(g, y, nu), uh, 0.0, T, "BS5_ADAPTIVE", 0.01, tol, tol,
+                       nmodes=g.nmodes_half, controller=ctl)
+    d = Dns(*shape, nu=nu)
+    d.set_state(to_dev(uh), 0.0)
+    if controller == "MLP":
+        d.set_controller("MLP", dev32(params))
+    else:
+        d.set_controller(controller)
+    info = d.integrate(T, "BS5_ADAPTIVE", tol, tol, h0=0.01)
+    return ref, info, d
+
+
+def test_pi_controller_matches_oracle():
+    ref, info, d = run_pair("PI")
+    assert (info.n_acc, info.n_rej, info.n_rhs) == (ref.n_acc, ref.n_rej, ref.n_rhs)
+    assert abs(info.h_next - ref.h_next) < 1e-7 * ref.h_next
+    assert rel_l2(d.get_state(), ref.u) < 1e-12
+
+
+def test_mlp_controller_matches_oracle_decisions():
+    rng = np.random.default_rng(9)
+    # a network that proposes about log 1.3 with mild feature dependence
+    p = (0.02 * rng.standard_normal(mlp.N_PARAMS)).astype(np.float32)
+    p[-1] = math.log(1.3)
+    ref, info, d = run_pair("MLP", p)
+    assert (info.n_acc, info.n_rej) == (ref.n_acc, ref.n_rej)
+    assert abs(info.h_next - ref.h_next) < 1e-5 * ref.h_next
+    assert rel_l2(d.get_state(), ref.u) < 1e-9
+
+
+def test_trace_diagnostics_match_oracle():
+    from paper_1810_10197_gb300 import Dns
+    shape, nu = (32, 32, 32), 0.02
+    g = sp.Grid(*shape)
+    uh = g.dealias(syn.random_solenoidal_hat(*shape, seed=4, k0=3.0))
+    d = Dns(*shape, nu=nu)
+    d.set_state(to_dev(uh), 0.0)
+    d.set_trace(100, diagnostics=True)
+    info = d.integrate(0.3, "BS5_ADAPTIVE", 1e-7, 1e-7, h0=0.01)
+    tr = d.trace()
+    assert len(tr) == info.n_acc + info.n_rej
+    assert tr[-1, 4] == info.n_rhs
+    u = d.get_state()
+    f = sp.rhs(g, u, nu)
+    assert tr[-1, 5] == pytest.approx(diag.energy(g, u), rel=1e-12)
+    assert tr[-1, 6] == pytest.approx(diag.enstrophy(g, u), rel=1e-12)
+    assert tr[-1, 7] == pytest.approx(diag.dissipation(g, u, f), rel=1e-10)
+    # energy decays monotonically for an unforced flow
+    E = tr[tr[:, 3] > 0.5, 5]
+    assert np.all(np.diff(E) < 0)
+
+
+def trajectories(flows):
+    from paper_1810_10197_gb300 import Dns, learned
+    Xs, Ts = [], []
+    for (shape, uh, nu, forcing, tol, T) in flows:
+        d = Dns(*shape, nu=nu, forcing=forcing)
+        d.set_state(to_dev(uh), 0.0)
+        d.set_trace(4000)
+        d.integrate(T, "BS5_ADAPTIVE", tol, tol, h0=1e-3)
+        X, Tt = learned.pairs_from_trace(d.trace())
+        Xs.append(X)
+        Ts.append(Tt)
+        d.close()
+    return np.concatenate(Xs), np.concatenate(Ts)
+
+
+def test_learned_controller_gain_on_rayleigh_taylor():
+    """Train on TG and forced-HIT trajectories, apply to a Rayleigh-Taylor run (held out)."""
+    from paper_1810_10197_gb300 import Dns, learned
+    n = 32
+    flows = []
+    for tol in (1e-5, 1e-6, 1e-7, 1e-8):
+        flows.append(((n, n, n), syn.taylor_green_3d_hat(n, n, n), 0.01, None, tol, 2.0))
+        flows.append(((n, n, n), syn.random_solenoidal_hat(n, n, n, seed=3, k0=3.0), 0.01, (2.5, 0.05),
+                      tol, 1.0))
+    X, T = trajectories(flows)
+    assert len(X) > 100
+    params, hist = learned.train(X, T, steps=3000, lr=2e-3, seed=0)
+    assert hist[-200:].mean() < hist[:20].mean()
+    # held-out problem: periodic RT at 32 x 32 x 64, from rest to t = 3
+    shape = (32, 32, 64)
+    rho, L = syn.rayleigh_taylor_fields(*shape, seed=7, width=0.2, amplitude=1e-2)
+    g = sp.Grid(*shape, lengths=L)
+    Y = np.zeros((4, 32, 32, 33), complex)
+    Y[3] = g.dealias(g.to_spectral(rho))
+    res = {}
+    for kind in ("I", "PI", "MLP", "REF"):
+        d = Dns(*shape, nu=1e-3, lengths=L, boussinesq=(1e-3, 1.0))
+        d.set_state(to_dev(Y), 0.0)
+        if kind == "MLP":
+            d.set_controller("MLP", params)
+        elif kind == "PI":
+            d.set_controller("PI")
+        tol = 1e-10 if kind == "REF" else 1e-6
+        d.set_trace(100000)
+        info = d.integrate(3.0, "BS5_ADAPTIVE", tol, tol, h0=1e-3)
+        tr = d.trace()
+        acc = tr[tr[:, 3] > 0.5]
+        assert np.all(acc[:, 2] <= 1.0)
+        res[kind] = (info.n_rhs, info.n_rej, d.get_state())
+        d.close()
+    ref = res["REF"][2]
+    line = []
+    for kind in ("I", "PI", "MLP"):
+        nr, nj, u = res[kind]
+        line.append(f"{kind}: {nr} RHS, {nj} rejected, L2 err vs tol-1e-10 run {rel_l2(u, ref):.2e}")
+    print("\nRT 32x32x64 to t=3, tol 1e-6 | " + " | ".join(line))
+    # every controller reaches t_end within the tolerance regime (error well below 1e-3)
+    for kind in ("I", "PI", "MLP"):
+        assert rel_l2(res[kind][2], ref) < 1e-3

@@ -1,0 +1,74 @@
+"""Pins for the learned-controller reference (oracle/mlp.py) and the PI controller."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import mlp, rk
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_parameter_count():
+    assert mlp.N_PARAMS == 64 * 16 + 64 + 64 * 64 + 64 + 64 + 1 == 5313
+
+
+def test_gradient_matches_central_differences():
+    rng = np.random.default_rng(3)
+    p = mlp.init_params(1) + 0.01 * rng.standard_normal(mlp.N_PARAMS)
+    X = rng.standard_normal((37, 16))
+    t = rng.standard_normal(37)
+    L, g = mlp.loss_and_grad(p, X, t)
+    idx = rng.choice(mlp.N_PARAMS, 60, replace=False)
+    for i in idx:
+        e = np.zeros_like(p)
+        e[i] = 1e-6
+        num = (mlp.loss_and_grad(p + e, X, t)[0] - mlp.loss_and_grad(p - e, X, t)[0]) / 2e-6
+        assert abs(num - g[i]) <= 1e-7 * max(1.0, abs(g[i])), (i, num, g[i])
+
+
+def test_forward_is_the_stated_network():
+    # a network whose only path is x0 -> unit 0 -> unit 0 -> output computes 3*relu(2*relu(x0))+1
+    p = np.zeros(mlp.N_PARAMS)
+    W1, b1, W2, b2, w3, b3 = (None,) * 6
+    p[0] = 1.0                                   # W1[0][0]
+    o = 64 * 16 + 64
+    p[o + 0] = 2.0                               # W2[0][0]
+    o += 64 * 64 + 64
+    p[o + 0] = 3.0                               # w3[0]
+    p[-1] = 1.0                                  # b3
+    X = np.zeros((3, 16))
+    X[:, 0] = [-1.0, 0.5, 2.0]
+    y, _ = mlp.forward(p, X)
+    assert np.allclose(y, [1.0, 4.0, 13.0])
+
+
+def test_bf16_rounding():
+    vals = np.array([1.0, 1.00390625, 1.001953125, 3.14159265, -2.5e-3, 0.0])
+    r = mlp.round_bf16(vals)
+    # bf16 keeps 8 significant bits: 1 + 2^-8 is representable? no: spacing at 1 is 2^-7
+    assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0
+    assert abs(r[3] - 3.140625) < 1e-12
+    assert r[5] == 0.0
+    assert np.all(np.abs(r - vals) <= np.abs(vals) * 2 ** -8 + 1e-30)
+
+
+def test_dataset_targets_are_hindsight_steps():
+    # history: accepted steps with known errors; target = log(h_{n+1} (0.8^5/err_{n+1})^(1/5) / h_n)
+    steps = [(0, 0.1, 0.5, True), (0.1, 0.1, 0.5, True), (0.2, 0.1, 0.5, True), (0.3, 0.2, 2.0, False),
+             (0.3, 0.12, 0.4, True), (0.42, 0.15, 0.32768, True)]
+    X, T = mlp.dataset_from_history(steps)
+    assert X.shape == (1, 16)
+    # n = 3 (4th accepted: h=0.12), next accepted h=0.15 with err = 0.8^5 -> h* = 0.15
+    assert abs(T[0] - math.log(0.15 / 0.12)) < 1e-12
+    # features: newest accepted err 0.4 with 1 rejection before it
+    assert abs(X[0, 0] - math.log10(0.4)) < 1e-12 and X[0, 2] == 1.0 and X[0, 1] == 0.0
+
+
+def test_pi_factor_hand_worked():
+    with open(os.path.join(GOLDEN, "pi_controller_cases.txt")) as fh:
+        rows = [l.split() for l in fh if l.strip() and not l.startswith("#")]
+    for err, errp, after, fac in rows:
+        got = rk.pi_factor(float(err), float(errp), bool(int(after)))
+        assert abs(got - float(fac)) < 1e-13, (err, errp, after, got, fac)
