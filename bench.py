@@ -200,6 +200,77 @@ def make_field(args):
     return syn.random_solenoidal_hat(n, n, n, seed=1, k0=4.0)
 
 
+def ensemble_specs(count=64):
+    """64 seeded instances: 24 x 64^3, 24 x 96^3, 16 x 128^3; k0 in [2, 6], nu log-uniform in
+    [1e-3, 1e-2] (drawn with the SplitMix64 generator of the synthetic inputs, seed = id)."""
+    import synthetic as syn
+    sizes = [64] * 24 + [96] * 24 + [128] * 16
+    out = []
+    for i, n in enumerate(sizes[:count]):
+        u = syn.uniform01(np.arange(2, dtype=np.uint64), 1000 + i)
+        k0 = 2.0 + 4.0 * float(u[0])
+        nu = 10.0 ** (-3.0 + float(u[1]))
+        out.append((n, k0, nu, i))
+    return out
+
+
+def run_ensemble(args):
+    """Config: 64 independent simulations, BS5 adaptive tol 1e-6 each to t_end; one graph
+    launch (dns_integrate_batch) against the same instances integrated one after another."""
+    import torch
+
+    import synthetic as syn
+    from paper_1810_10197_gb300 import Dns, build
+    from paper_1810_10197_gb300.dns import DnsBatch
+    torch.cuda.set_device(0)
+    build.build()
+    specs = ensemble_specs(args.count)
+    t_end = args.t_end
+    fields = [syn.random_solenoidal_hat(n, n, n, seed=i, k0=k0) for (n, k0, nu, i) in specs]
+    b = DnsBatch([dict(nx=n, nu=nu) for (n, k0, nu, i) in specs])
+    tiles = [inst.autotune() for inst in b.instances]
+    # warm-up: one short batched integration
+    for inst, f in zip(b.instances, fields):
+        inst.set_state(torch.from_numpy(f).cuda(), 0.0)
+    b.integrate("BS5_ADAPTIVE", [0.01] * len(specs), [TOL] * len(specs), [TOL] * len(specs), [H0] * len(specs))
+    for inst, f in zip(b.instances, fields):
+        inst.set_state(torch.from_numpy(f).cuda(), 0.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    infos = b.integrate("BS5_ADAPTIVE", [t_end] * len(specs), [TOL] * len(specs), [TOL] * len(specs),
+                        [H0] * len(specs))
+    torch.cuda.synchronize()
+    batched_s = time.perf_counter() - t0
+    n_rhs = sum(i.n_rhs for i in infos)
+    # the same instances, one after another through dns_integrate
+    seq_s, seq_rhs = 0.0, 0
+    for (n, k0, nu, i), f in zip(specs, fields):
+        d = Dns(n, nu=nu)
+        d.autotune()
+        d.set_state(torch.from_numpy(f).cuda(), 0.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = d.integrate(t_end, "BS5_ADAPTIVE", TOL, TOL, h0=H0)
+        torch.cuda.synchronize()
+        seq_s += time.perf_counter() - t0
+        seq_rhs += info.n_rhs
+        d.close()
+    sim = len(specs) * t_end
+    out = {"metric": METRIC, "value": n_rhs / batched_s, "unit": UNIT, "n_gpus": 1, "steps": 1,
+           "warmup": 1, "ms_per_step": batched_s * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"ensemble_{len(specs)}x(24x64^3,24x96^3,16x128^3)_bs5_tol1e-6_to_t{t_end:g}",
+                      "tiles": tiles},
+           "sim_time_per_gpu_s": sim / batched_s,
+           "sequential": {"rhs_evals_per_s": seq_rhs / seq_s, "sim_time_per_gpu_s": sim / seq_s,
+                          "seconds": seq_s},
+           "batched_seconds": batched_s, "speedup_vs_sequential": seq_s / batched_s,
+           "rhs_evals": n_rhs, "rejected": sum(i.n_rej for i in infos)}
+    print(json.dumps(out), flush=True)
+    b.close()
+    return 0
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -225,6 +296,7 @@ def run_gpu(args):
         d0.close()
         forcing = (FLOWS["hit"]["forcing"][0], eps0)
     d = Dns(n, nu=nu, precision=args.precision, forcing=forcing, stream=stream)
+    tiles = d.autotune()
     d.set_state(u0_dev, 0.0)
 
     def barrier():
@@ -364,7 +436,7 @@ def run_gpu(args):
            "config": {"workload": workload_name(args), "grid": [n, n, n], "nu": nu,
                       "method": "BS5_ADAPTIVE" if args.mode == "step" else "rhs",
                       "rtol": TOL, "atol": TOL, "h0": H0, "precision": args.precision,
-                      "forcing": forcing,
+                      "forcing": forcing, "tiles": tiles,
                       "l2": "inputs larger than L2 (per right-hand side: "
                             f"{rhs_bytes / 1e9:.2f} GB algorithmic traffic)",
                       "parallelism": f"replicas{ws}"},
@@ -396,11 +468,16 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_mixed"])
     ap.add_argument("--flow", default="tg", choices=["tg", "hit"])
     ap.add_argument("--mode", default="step", choices=["step", "rhs"])
+    ap.add_argument("--workload", default="single", choices=["single", "ensemble"])
+    ap.add_argument("--count", type=int, default=64)
+    ap.add_argument("--t-end", type=float, default=0.5)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "ensemble":
+        return run_ensemble(args)
     return run_gpu(args)
 
 

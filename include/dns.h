@@ -38,6 +38,13 @@
 
 #include <stddef.h>
 
+/* Exported entry points (the library hides every other symbol). */
+#if defined(__GNUC__)
+#define DNS_API __attribute__((visibility("default")))
+#else
+#define DNS_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -97,10 +104,10 @@ typedef struct {
 
 /* Create a context for an nx x ny x nz grid on the current CUDA device (Eq. ufdef with
  * viscosity nu, optional forcing, precision a dns_precision).  Domain [0, 2 pi)^3. */
-dns_status dns_create(int nx, int ny, int nz, double nu, const dns_forcing* forcing,
+DNS_API dns_status dns_create(int nx, int ny, int nz, double nu, const dns_forcing* forcing,
                       int precision, dns_ctx** out);
 /* As dns_create, with domain lengths from cfg. */
-dns_status dns_create_ex(const dns_config* cfg, dns_ctx** out);
+DNS_API dns_status dns_create_ex(const dns_config* cfg, dns_ctx** out);
 /* Boussinesq form, Eqs. (ufdefboussinesq) and (rhofdefboussinesq) of Section 3.2:
  *   d(uhat)/dt   = P(kappa)[(u x omega)^ - Ri rhohat e_z] - nu |kappa|^2 uhat
  *   d(rhohat)/dt = -i kappa . (rho u)^ - kappa |kappa|^2 rhohat
@@ -109,30 +116,30 @@ dns_status dns_create_ex(const dns_config* cfg, dns_ctx** out);
  * density deviation rho; every state/RHS call of this context uses that layout, and the
  * error norm takes the maximum over the 4 components.  cfg->forcing must be kind 0;
  * kappa is the density diffusivity 1/(Re Pr), ri the Richardson number. */
-dns_status dns_create_boussinesq(const dns_config* cfg, double kappa, double ri, dns_ctx** out);
-void dns_destroy(dns_ctx* ctx);
+DNS_API dns_status dns_create_boussinesq(const dns_config* cfg, double kappa, double ri, dns_ctx** out);
+DNS_API void dns_destroy(dns_ctx* ctx);
 /* Message for the last non-OK status of this context ("" if none).  Valid until next call. */
-const char* dns_last_error(const dns_ctx* ctx);
+DNS_API const char* dns_last_error(const dns_ctx* ctx);
 
 /* Stream for all later work (a cudaStream_t as void*; NULL = legacy default stream). */
-dns_status dns_set_stream(dns_ctx* ctx, void* stream);
+DNS_API dns_status dns_set_stream(dns_ctx* ctx, void* stream);
 
 /* Load the state uhat (layout above) at time t; where = 0: device pointer, 1: host pointer.
  * Truncates to the 2/3 box, resets the step counters and the controller (next h comes from
  * dns_integrate's h0).  Asynchronous for device input, synchronous for host input. */
-dns_status dns_set_state(dns_ctx* ctx, const void* uhat, int where, double t);
+DNS_API dns_status dns_set_state(dns_ctx* ctx, const void* uhat, int where, double t);
 /* Write the current state (zero outside the 2/3 box); where as above.  Synchronous. */
-dns_status dns_get_state(dns_ctx* ctx, void* uhat, int where);
+DNS_API dns_status dns_get_state(dns_ctx* ctx, void* uhat, int where);
 
 /* Eq. (ufdef), once: f = P(kappa) [u x omega]^ - nu |kappa|^2 uhat (+ forcing), evaluated
  * pseudo-spectrally with 2/3 dealiasing (Section 2.1).  uhat and f are device pointers in the
  * layout above (may not alias).  Asynchronous on the context's stream. */
-dns_status dns_rhs(dns_ctx* ctx, const void* uhat_dev, void* f_dev);
+DNS_API dns_status dns_rhs(dns_ctx* ctx, const void* uhat_dev, void* f_dev);
 
 /* One attempted step from the current state with step size h (clipped to t_end if t_end >
  * t), embedded error norm with (rtol, atol) and the controller of Section 2.2.1 (adaptive
  * methods accept iff err <= 1 and propose h_new).  Synchronous; fills info if non-NULL. */
-dns_status dns_step(dns_ctx* ctx, int method, double h, double rtol, double atol,
+DNS_API dns_status dns_step(dns_ctx* ctx, int method, double h, double rtol, double atol,
                     double t_end, dns_step_info* info);
 
 /* Integrate from the current time to t_end.  h0 > 0 sets the step (fixed methods) or the
@@ -140,27 +147,27 @@ dns_status dns_step(dns_ctx* ctx, int method, double h, double rtol, double atol
  * is clipped to land on t_end.  max_rejects consecutive rejections (default 30 when <= 0)
  * end the run with DNS_ERR_MAX_REJECTS (DNS_ERR_NONFINITE if err was not finite).
  * Synchronous; fills info if non-NULL. */
-dns_status dns_integrate(dns_ctx* ctx, double t_end, int method, double rtol, double atol,
+DNS_API dns_status dns_integrate(dns_ctx* ctx, double t_end, int method, double rtol, double atol,
                          double h0, int max_rejects, dns_step_info* info);
 
 /* Enqueue exactly n step attempts toward t_end without waiting (for timing loops); attempts
  * after t_end is reached do nothing on the device.  Read the outcome with dns_get_info. */
-dns_status dns_enqueue_attempts(dns_ctx* ctx, int n, int method, double rtol, double atol,
+DNS_API dns_status dns_enqueue_attempts(dns_ctx* ctx, int n, int method, double rtol, double atol,
                                 double t_end, double h0);
 /* Synchronous read of the controller state and counters. */
-dns_status dns_get_info(dns_ctx* ctx, dns_step_info* info);
+DNS_API dns_status dns_get_info(dns_ctx* ctx, dns_step_info* info);
 
 /* Kinetic energy E, enstrophy Omega and dissipation rate eps = -dE/dt of the current state
  * (Section 3.1, half-spectrum weights).  eps uses one right-hand-side evaluation.
  * Synchronous. */
-dns_status dns_diagnostics(dns_ctx* ctx, double* E, double* Omega, double* eps);
+DNS_API dns_status dns_diagnostics(dns_ctx* ctx, double* E, double* Omega, double* eps);
 
 /* Per-kernel timing with CUDA events on the context's stream.  enable != 0 starts recording
  * (and clears earlier records).  dns_profile_get returns, for kernel index i < count, its
  * name, number of launches and summed duration in ms (synchronous). */
-dns_status dns_profile_enable(dns_ctx* ctx, int enable);
-int dns_profile_count(dns_ctx* ctx);
-dns_status dns_profile_get(dns_ctx* ctx, int i, const char** name, long long* launches,
+DNS_API dns_status dns_profile_enable(dns_ctx* ctx, int enable);
+DNS_API int dns_profile_count(dns_ctx* ctx);
+DNS_API dns_status dns_profile_get(dns_ctx* ctx, int i, const char** name, long long* launches,
                            double* total_ms);
 
 /* Attempt trace.  dns_set_trace allocates room for `capacity` records in the context (0
@@ -171,8 +178,8 @@ dns_status dns_profile_get(dns_ctx* ctx, int i, const char** name, long long* la
  * are dropped.  dns_trace copies min(n, cap) records to the host array `out` (row-major)
  * and returns the number recorded in *n.  Synchronous. */
 #define DNS_TRACE_COLS 8
-dns_status dns_set_trace(dns_ctx* ctx, long long capacity, int diagnostics);
-dns_status dns_trace(dns_ctx* ctx, double* out, long long cap, long long* n);
+DNS_API dns_status dns_set_trace(dns_ctx* ctx, long long capacity, int diagnostics);
+DNS_API dns_status dns_trace(dns_ctx* ctx, double* out, long long cap, long long* n);
 
 /* Step-size controller of the adaptive method.  DNS_CTRL_I: Section 2.2.1 (default).
  * DNS_CTRL_PI: after an accepted step h_new = h min(2, max(0.01, 0.8 err^-0.14 err_prev^0.08))
@@ -183,7 +190,7 @@ dns_status dns_trace(dns_ctx* ctx, double* out, long long cap, long long* n);
  * rejects each step, and rejections (and non-finite proposals) use the Section 2.2.1 factor.
  * mlp_params_dev: DNS_MLP_PARAMS floats on the device (copied in), for DNS_CTRL_MLP only. */
 typedef enum { DNS_CTRL_I = 0, DNS_CTRL_PI = 1, DNS_CTRL_MLP = 2 } dns_controller;
-dns_status dns_set_controller(dns_ctx* ctx, int kind, const float* mlp_params_dev);
+DNS_API dns_status dns_set_controller(dns_ctx* ctx, int kind, const float* mlp_params_dev);
 
 /* The learned proposal's network (not in the paper): inputs 16 features of the 4 newest
  * accepted steps (newest first, each [log10 err, log(h_i/h_0), rejections before it,
@@ -197,14 +204,42 @@ dns_status dns_set_controller(dns_ctx* ctx, int kind, const float* mlp_params_de
  *                      `batch` (<= 128) samples drawn with a counter hash of `seed`; params
  *                      updated in place; loss_hist[steps] (may be NULL) receives batch losses. */
 #define DNS_MLP_PARAMS 5313
-dns_status dns_mlp_forward(const float* params, const float* x, int n, float* y, void* stream);
-dns_status dns_mlp_loss_grad(const float* params, const float* x, const float* t, int n, float* grad,
+DNS_API dns_status dns_mlp_forward(const float* params, const float* x, int n, float* y, void* stream);
+DNS_API dns_status dns_mlp_loss_grad(const float* params, const float* x, const float* t, int n, float* grad,
                              float* loss, void* stream);
-dns_status dns_mlp_train(float* params, const float* x, const float* t, int n, int steps, int batch,
+DNS_API dns_status dns_mlp_train(float* params, const float* x, const float* t, int n, int steps, int batch,
                          float lr, unsigned seed, float* loss_hist, void* stream);
 
+/* Ensembles of independent simulations (uneven sizes allowed), advanced together.
+ * dns_create_batch makes one context per config (each owns its buffers; all on the current
+ * device).  Load each instance's state through dns_batch_context + dns_set_state (or read it
+ * with dns_get_state); the contexts belong to the batch: do not destroy them yourself.
+ * dns_integrate_batch integrates every instance i from its current time to t_end[i] with its
+ * own tolerances and first step h0[i] (<= 0 keeps the current proposal), by ONE launch of a
+ * CUDA graph: a conditional loop whose body runs one attempt of every instance (instances in
+ * parallel branches) and continues while any instance is unfinished (at most 10^7 rounds).
+ * The graph is built on the first call for a method and reused.  Synchronous; info[i]
+ * receives each instance's outcome; returns the first non-OK instance status (or DNS_OK). */
+typedef struct dns_batch dns_batch;
+DNS_API dns_status dns_create_batch(int count, const dns_config* cfgs, dns_batch** out);
+DNS_API void dns_destroy_batch(dns_batch* batch);
+DNS_API const char* dns_batch_last_error(const dns_batch* batch);
+DNS_API dns_status dns_batch_context(dns_batch* batch, int i, dns_ctx** out);
+DNS_API dns_status dns_integrate_batch(dns_batch* batch, int method, const double* t_end, const double* rtol,
+                               const double* atol, const double* h0, dns_step_info* info);
+
+/* Autotuner of the FFT tile shapes.  The y passes (columns per CTA) and the z pass (lines
+ * per CTA) each have two compiled tile variants (0: full, 1: half); dns_autotune times
+ * `reps` launches of each variant on this context's buffers with CUDA events on its stream,
+ * keeps the faster one, and caches the choice per (grid, precision, form) for the process
+ * and, if the environment variable DNS_TUNE_CACHE names a file, in that file (read on first
+ * use, appended to).  variants (may be NULL) receives {y pass, z pass}.  dns_create_batch
+ * tunes every instance.  dns_set_tiles sets the variants by hand.  Synchronous. */
+DNS_API dns_status dns_autotune(dns_ctx* ctx, int reps, int* variants);
+DNS_API dns_status dns_set_tiles(dns_ctx* ctx, int var_py, int var_p3);
+
 /* Grid facts: retained cut-offs K[3] and the number of device bytes the context holds. */
-dns_status dns_query(const dns_ctx* ctx, int* K3, size_t* device_bytes);
+DNS_API dns_status dns_query(const dns_ctx* ctx, int* K3, size_t* device_bytes);
 
 /* The right-hand side of dns_rhs (same layout, same result) for small grids, without a
  * context and without allocating any device memory.  The paper has no counterpart: this
@@ -224,7 +259,7 @@ dns_status dns_query(const dns_ctx* ctx, int* K3, size_t* device_bytes);
  * it reads, so no state carries over; calls that overlap on the GPU (different streams, or
  * different host threads) race on it and must be serialised by the caller.
  * Returns DNS_ERR_ARG for bad pointers or nu, DNS_ERR_CUDA if a launch fails. */
-dns_status dns_rhs_noalloc(int nx, int ny, int nz, double nu, const void* uhat_dev, void* f_dev,
+DNS_API dns_status dns_rhs_noalloc(int nx, int ny, int nz, double nu, const void* uhat_dev, void* f_dev,
                            void* stream);
 
 #ifdef __cplusplus

@@ -4,8 +4,12 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/dns.h"
@@ -101,6 +105,8 @@ struct dns_ctx {
   double* trace_buf = nullptr;     // attempt records (dns_set_trace)
   int trace_diag = 0;
   float* mlp_buf = nullptr;        // learned-controller parameters (dns_set_controller)
+  int var_py = 0, var_p3 = 0;      // tile variants (dns_autotune)
+  size_t bytesA = 0, bytesB = 0;   // sizes of the scratch buffers A and B
   bool prof = false;
   std::vector<ProfRec> recs;
   std::vector<cudaEvent_t> pool;
@@ -201,6 +207,8 @@ dns_status enqueue_rhs(dns_ctx* c, DnsCtrl* ctrl, int yslot, int kslot, int gate
   a.kf2 = c->forcing.kind == 1 ? c->forcing.kf * c->forcing.kf : 0.0;
   a.kappa_d = c->kappa_d;
   a.ri = c->ri;
+  a.var_py = c->var_py;
+  a.var_p3 = c->var_p3;
   a.out = c->bufA; a.tw = c->tw[0];
   CK(timed(c, PR_P1, [&] { return pass(c, 1, a); }), "pass P1");
   a.in = c->bufA; a.out = c->bufB; a.tw = c->tw[1];
@@ -390,6 +398,8 @@ static dns_status create_impl(const dns_config* cfg, int bouss, double kappa, do
   A((void**)&c->ystage, vbytes);
   A((void**)&c->rhs_in, vbytes); A((void**)&c->rhs_out, vbytes);
   A(&c->bufA, nA * esz); A(&c->bufB, nB * esz);
+  c->bytesA = nA * esz;
+  c->bytesB = nB * esz;
   A((void**)&c->ctrl, sizeof(DnsCtrl)); A((void**)&c->ctrl_rhs, sizeof(DnsCtrl));
   A((void**)&c->partials, (size_t)kRedBlocks * kRedStride * sizeof(double));
   if (s == DNS_OK) s = make_twiddles(c, g.nx, false, &c->tw[0]);
@@ -661,11 +671,277 @@ dns_status dns_set_controller(dns_ctx* c, int kind, const float* mlp_params_dev)
   return DNS_OK;
 }
 
+}  // extern "C"
+
+namespace {
+using TuneKey = std::tuple<int, int, int, int, int>;   // nx, ny, nz, precision, boussinesq
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune;
+bool g_tune_loaded = false;
+
+void tune_load_file() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("DNS_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  int v[7];
+  while (std::fscanf(f, "%d %d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6]) == 7)
+    g_tune[TuneKey(v[0], v[1], v[2], v[3], v[4])] = {v[5], v[6]};
+  std::fclose(f);
+}
+
+void tune_save(const TuneKey& k, std::pair<int, int> v) {
+  const char* path = std::getenv("DNS_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k),
+               std::get<4>(k), v.first, v.second);
+  std::fclose(f);
+}
+}  // namespace
+
+extern "C" {
+
+dns_status dns_autotune(dns_ctx* c, int reps, int* variants) {
+  dns_status s = check_ctx(c);
+  if (s != DNS_OK) return s;
+  if (reps < 1) reps = 3;
+  const TuneKey key(c->g.nx, c->g.ny, c->g.nz, c->precision, c->g.bouss);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_file();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      c->var_py = it->second.first;
+      c->var_p3 = it->second.second;
+      if (variants) { variants[0] = c->var_py; variants[1] = c->var_p3; }
+      return DNS_OK;
+    }
+  }
+  CK(cudaMemsetAsync(c->bufA, 0, c->bytesA, c->stream), "zero");
+  CK(cudaMemsetAsync(c->bufB, 0, c->bytesB, c->stream), "zero");
+  PassArgs a{};
+  a.g = c->g;
+  a.ctrl = c->ctrl_rhs;
+  a.yslot = SLOT_Y;
+  a.kslot = SLOT_K1;
+  a.nu = c->nu;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0), "event");
+  CK(cudaEventCreate(&e1), "event");
+  float best[2][2] = {{0, 0}, {0, 0}};
+  for (int which = 0; which < 2; ++which) {        // 0: y pass (P2), 1: z pass (P3)
+    for (int v = 0; v < 2; ++v) {
+      a.var_py = which == 0 ? v : 0;
+      a.var_p3 = which == 1 ? v : 0;
+      if (which == 0) { a.in = c->bufA; a.out = c->bufB; a.tw = c->tw[1]; }
+      else { a.in = c->bufB; a.out = c->bufA; a.tw = c->tw[2]; }
+      const int pass_id = which == 0 ? 2 : 3;
+      CK(pass(c, pass_id, a), "tune launch");
+      CK(cudaEventRecord(e0, c->stream), "event");
+      for (int r = 0; r < reps; ++r) CK(pass(c, pass_id, a), "tune launch");
+      CK(cudaEventRecord(e1, c->stream), "event");
+      CK(cudaEventSynchronize(e1), "event sync");
+      CK(cudaEventElapsedTime(&best[which][v], e0, e1), "elapsed");
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->var_py = best[0][1] < best[0][0] ? 1 : 0;
+  c->var_p3 = best[1][1] < best[1][0] ? 1 : 0;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = {c->var_py, c->var_p3};
+    tune_save(key, {c->var_py, c->var_p3});
+  }
+  if (variants) { variants[0] = c->var_py; variants[1] = c->var_p3; }
+  return DNS_OK;
+}
+
+dns_status dns_set_tiles(dns_ctx* c, int var_py, int var_p3) {
+  if (!c || var_py < 0 || var_py > 1 || var_p3 < 0 || var_p3 > 1) return DNS_ERR_ARG;
+  c->var_py = var_py;
+  c->var_p3 = var_p3;
+  return DNS_OK;
+}
+
 dns_status dns_query(const dns_ctx* c, int* K3, size_t* device_bytes) {
   if (!c) return DNS_ERR_ARG;
   if (K3) { K3[0] = c->g.Kx; K3[1] = c->g.Ky; K3[2] = c->g.Kz; }
   if (device_bytes) *device_bytes = c->device_bytes;
   return DNS_OK;
+}
+
+}  // extern "C"
+
+
+// ------------------------------------------------------------------------------------------
+// Batched ensembles: independent contexts advanced together by one graph launch.  The graph
+// holds a conditional WHILE node; its body enqueues one attempt of every instance, each in
+// its own branch (so instances run concurrently), then a kernel that keeps the loop going
+// while any instance is unfinished, with a hard cap on the number of iterations.
+// ------------------------------------------------------------------------------------------
+namespace {
+
+__global__ void k_batch_continue(cudaGraphConditionalHandle h, DnsCtrl* const* ctrls, int n,
+                                 unsigned long long* iter, unsigned long long max_iter) {
+  int any = 0;
+  for (int i = 0; i < n; ++i)
+    if (!ctrls[i]->done && ctrls[i]->status == 0) any = 1;
+  const unsigned long long it = ++(*iter);
+  if (it >= max_iter) any = 0;
+  cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+
+}  // namespace
+
+struct dns_batch {
+  std::vector<dns_ctx*> ctx;
+  std::vector<cudaStream_t> streams;   // one branch stream per instance
+  cudaStream_t stream = nullptr;       // launch stream
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins;
+  DnsCtrl** d_ctrls = nullptr;
+  unsigned long long* d_iter = nullptr;
+  cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
+  cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
+  int device = 0;
+  std::string err;
+};
+
+extern "C" {
+
+void dns_destroy_batch(dns_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (int m = 0; m < 3; ++m) {
+    if (b->exec[m]) cudaGraphExecDestroy(b->exec[m]);
+    if (b->graph[m]) cudaGraphDestroy(b->graph[m]);
+  }
+  for (dns_ctx* c : b->ctx) dns_destroy(c);
+  for (cudaStream_t s : b->streams) if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->joins) if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  if (b->d_ctrls) cudaFree(b->d_ctrls);
+  if (b->d_iter) cudaFree(b->d_iter);
+  delete b;
+}
+
+dns_status dns_create_batch(int count, const dns_config* cfgs, dns_batch** out) {
+  if (!out || !cfgs || count < 1) return DNS_ERR_ARG;
+  *out = nullptr;
+  dns_batch* b = new dns_batch();
+  cudaGetDevice(&b->device);
+  dns_status s = DNS_OK;
+  for (int i = 0; i < count && s == DNS_OK; ++i) {
+    dns_ctx* c = nullptr;
+    s = dns_create_ex(&cfgs[i], &c);
+    if (s == DNS_OK) b->ctx.push_back(c);
+  }
+  if (s == DNS_OK) {
+    bool ok = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaMalloc((void**)&b->d_ctrls, count * sizeof(DnsCtrl*)) == cudaSuccess &&
+              cudaMalloc((void**)&b->d_iter, sizeof(unsigned long long)) == cudaSuccess;
+    b->streams.assign(count, nullptr);
+    b->joins.assign(count, nullptr);
+    for (int i = 0; ok && i < count; ++i)
+      ok = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming) == cudaSuccess;
+    if (ok) {
+      std::vector<DnsCtrl*> h(count);
+      for (int i = 0; i < count; ++i) { h[i] = b->ctx[i]->ctrl; b->ctx[i]->stream = b->stream; }
+      ok = cudaMemcpy(b->d_ctrls, h.data(), count * sizeof(DnsCtrl*), cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    // tile variants per distinct grid from the autotuner (timed once per shape, cached)
+    for (int i = 0; ok && i < count; ++i) ok = dns_autotune(b->ctx[i], 3, nullptr) == DNS_OK;
+    if (!ok) { cudaGetLastError(); s = DNS_ERR_CUDA; }
+  }
+  if (s != DNS_OK) { dns_destroy_batch(b); return s; }
+  *out = b;
+  return DNS_OK;
+}
+
+const char* dns_batch_last_error(const dns_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+dns_status dns_batch_context(dns_batch* b, int i, dns_ctx** out) {
+  if (!b || !out || i < 0 || i >= (int)b->ctx.size()) return DNS_ERR_ARG;
+  *out = b->ctx[i];
+  return DNS_OK;
+}
+
+dns_status dns_integrate_batch(dns_batch* b, int method, const double* t_end, const double* rtol,
+                               const double* atol, const double* h0, dns_step_info* info) {
+  if (!b || !t_end || !rtol || !atol || !h0 || method < 0 || method > 2) return DNS_ERR_ARG;
+  if (cudaSetDevice(b->device) != cudaSuccess) return DNS_ERR_CUDA;
+  const int n = (int)b->ctx.size();
+  dns_status s;
+  for (int i = 0; i < n; ++i) {
+    dns_ctx* c = b->ctx[i];
+    if ((s = check_ctx(c)) != DNS_OK) { b->err = "instance failed"; return s; }
+    if (!c->has_state) { b->err = "instance without state"; return DNS_ERR_STATE; }
+    c->stream = b->stream;
+    c->prof = false;
+    if ((s = config(c, t_end[i], method, rtol[i], atol[i], h0[i], 0)) != DNS_OK) { b->err = c->err; return s; }
+  }
+  auto cuda = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess) { b->err = std::string(what) + ": " + cudaGetErrorString(e); return false; }
+    return true;
+  };
+  if (!b->exec[method]) {
+    cudaGraph_t g = nullptr;
+    if (!cuda(cudaGraphCreate(&g, 0), "graph create")) return DNS_ERR_CUDA;
+    cudaGraphConditionalHandle handle;
+    if (!cuda(cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault), "conditional handle"))
+      return DNS_ERR_CUDA;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (!cuda(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp), "conditional node")) return DNS_ERR_CUDA;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (!cuda(cudaStreamBeginCaptureToGraph(b->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed),
+              "begin capture"))
+      return DNS_ERR_CUDA;
+    bool ok = cuda(cudaEventRecord(b->fork, b->stream), "fork");
+    for (int i = 0; ok && i < n; ++i) {
+      dns_ctx* c = b->ctx[i];
+      ok = cuda(cudaStreamWaitEvent(b->streams[i], b->fork, 0), "fork wait");
+      c->stream = b->streams[i];
+      if (ok && enqueue_attempt(c, method) != DNS_OK) { b->err = c->err; ok = false; }
+      c->stream = b->stream;
+      ok = ok && cuda(cudaEventRecord(b->joins[i], b->streams[i]), "join") &&
+           cuda(cudaStreamWaitEvent(b->stream, b->joins[i], 0), "join wait");
+    }
+    if (ok) {
+      k_batch_continue<<<1, 1, 0, b->stream>>>(handle, b->d_ctrls, n, b->d_iter, 10000000ULL);
+      ok = cuda(cudaGetLastError(), "continue kernel");
+    }
+    cudaGraph_t captured = nullptr;
+    const bool ended = cuda(cudaStreamEndCapture(b->stream, &captured), "end capture");
+    if (!ok || !ended) { cudaGraphDestroy(g); return DNS_ERR_CUDA; }
+    if (!cuda(cudaGraphInstantiate(&b->exec[method], g, 0), "instantiate")) { cudaGraphDestroy(g); return DNS_ERR_CUDA; }
+    b->graph[method] = g;
+  }
+  if (!cuda(cudaMemsetAsync(b->d_iter, 0, sizeof(unsigned long long), b->stream), "reset counter") ||
+      !cuda(cudaGraphLaunch(b->exec[method], b->stream), "graph launch") ||
+      !cuda(cudaStreamSynchronize(b->stream), "synchronize"))
+    return DNS_ERR_CUDA;
+  dns_status worst = DNS_OK;
+  for (int i = 0; i < n; ++i) {
+    dns_ctx* c = b->ctx[i];
+    if ((s = read_ctrl(c)) != DNS_OK) return s;
+    if (info) fill_info(c, &info[i]);
+    if (c->host_ctrl->status != 0 && worst == DNS_OK) worst = status_from_ctrl(c);
+  }
+  return worst;
 }
 
 }  // extern "C"

@@ -35,6 +35,8 @@ struct PassArgs {
   double kf2;            // forcing band |kappa|^2 <= kf2 (0: no forcing)
   double kappa_d;        // density diffusivity (Boussinesq)
   double ri;             // Richardson number (Boussinesq)
+  int var_py;            // tile variant of the y passes (0: full, 1: half width), autotuned
+  int var_p3;            // tile variant of the z pass (0: full, 1: half the lines), autotuned
 };
 
 // Column tiles: kz-contiguous columns handled per CTA in the x and y passes (128-byte rows),
@@ -42,9 +44,11 @@ struct PassArgs {
 template <typename T, int N> __host__ __device__ constexpr int p1_cols() {
   return sizeof(T) == 4 ? (N >= 512 ? 8 : 16) : (N >= 512 ? 4 : 8);
 }
-template <typename T> __host__ __device__ constexpr int py_cols() { return sizeof(T) == 4 ? 16 : 8; }
-template <typename T, int MZ, bool BOUSS = false> __host__ __device__ constexpr int p3_lines() {
-  return BOUSS ? (MZ >= 256 ? 2 : 4) : (MZ >= 256 ? 4 : 8);
+template <typename T, int VAR = 0> __host__ __device__ constexpr int py_cols() {
+  return (sizeof(T) == 4 ? 16 : 8) >> VAR;
+}
+template <typename T, int MZ, bool BOUSS = false, int VAR = 0> __host__ __device__ constexpr int p3_lines() {
+  return (BOUSS ? (MZ >= 256 ? 2 : 4) : (MZ >= 256 ? 4 : 8)) >> VAR;
 }
 // z-pass line stride: lines whose threads share a half-warp (FP32) or quarter-warp (FP64)
 // start at bank offsets that the first Stockham stage's writes do not overlap.
@@ -208,11 +212,11 @@ k_p1(const PassArgs a) {
 // P2 / P4: DFT along y for one (field, x) and TZ kz columns.  grid (ceil(Mz/TZ), nx, nf).
 // INVERSE: retained ky -> all y.  Forward: all y -> retained ky.
 // ------------------------------------------------------------------------------------------
-template <typename T, int NY, bool INVERSE>
-__global__ void __launch_bounds__(FftPlan<NY>::G * py_cols<T>())
+template <typename T, int NY, bool INVERSE, int VAR>
+__global__ void __launch_bounds__(FftPlan<NY>::G * py_cols<T, VAR>())
 k_py(const PassArgs a) {
   using V = v2_t<T>;
-  constexpr int TZ = py_cols<T>();
+  constexpr int TZ = py_cols<T, VAR>();
   constexpr int G = FftPlan<NY>::G;
   constexpr int LD = line_ld<V, NY>();
   constexpr int NTW = twiddle_count_xy(NY);
@@ -266,11 +270,11 @@ k_py(const PassArgs a) {
 //   C2R pre-step : Z_k = (X_k + conj X_{M-k}) + i e^{+2 pi i k/nz} (X_k - conj X_{M-k})
 //   R2C post-step: X_k = (Z_k + conj Z_{M-k})/2 - (i/2) e^{-2 pi i k/nz} (Z_k - conj Z_{M-k})
 // ------------------------------------------------------------------------------------------
-template <typename T, int MZ, bool BOUSS>
-__global__ void __launch_bounds__(FftPlan<MZ>::G * (BOUSS ? 7 : 6) * p3_lines<T, MZ, BOUSS>())
+template <typename T, int MZ, bool BOUSS, int VAR>
+__global__ void __launch_bounds__(FftPlan<MZ>::G * (BOUSS ? 7 : 6) * p3_lines<T, MZ, BOUSS, VAR>())
 k_p3(const PassArgs a) {
   using V = v2_t<T>;
-  constexpr int TL = p3_lines<T, MZ, BOUSS>();
+  constexpr int TL = p3_lines<T, MZ, BOUSS, VAR>();
   constexpr int NIN = BOUSS ? 7 : 6;    // u, omega (, rho)
   constexpr int NOUT = BOUSS ? 6 : 3;   // u x omega (, rho u)
   constexpr int G = FftPlan<MZ>::G;

@@ -38,31 +38,39 @@ static cudaError_t launch_p5(const PassArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <typename T, int N, bool INV>
-static cudaError_t launch_py(const PassArgs& a, cudaStream_t s) {
+template <typename T, int N, bool INV, int VAR>
+static cudaError_t launch_py_v(const PassArgs& a, cudaStream_t s) {
   using V = v2_t<T>;
-  constexpr int TZ = py_cols<T>();
+  constexpr int TZ = py_cols<T, VAR>();
   const size_t smem = (size_t)(twiddle_count_xy(N) + TZ * line_ld<V, N>()) * sizeof(V);
-  cudaError_t e = set_smem(k_py<T, N, INV>, smem);
+  cudaError_t e = set_smem(k_py<T, N, INV, VAR>, smem);
   if (e != cudaSuccess) return e;
   const int nf = INV ? (a.g.bouss ? 7 : 6) : (a.g.bouss ? 6 : 3);
   dim3 grid((a.g.Mz + TZ - 1) / TZ, a.g.nx, nf);
-  k_py<T, N, INV><<<grid, FftPlan<N>::G * TZ, smem, s>>>(a);
+  k_py<T, N, INV, VAR><<<grid, FftPlan<N>::G * TZ, smem, s>>>(a);
   return cudaGetLastError();
 }
+template <typename T, int N, bool INV>
+static cudaError_t launch_py(const PassArgs& a, cudaStream_t s) {
+  return a.var_py ? launch_py_v<T, N, INV, 1>(a, s) : launch_py_v<T, N, INV, 0>(a, s);
+}
 
-template <typename T, int MZ, bool B>
-static cudaError_t launch_p3(const PassArgs& a, cudaStream_t s) {
+template <typename T, int MZ, bool B, int VAR>
+static cudaError_t launch_p3_v(const PassArgs& a, cudaStream_t s) {
   using V = v2_t<T>;
-  constexpr int TL = p3_lines<T, MZ, B>();
+  constexpr int TL = p3_lines<T, MZ, B, VAR>();
   constexpr int NIN = B ? 7 : 6;
   const size_t smem = (size_t)(twiddle_count_z(2 * MZ) + NIN * TL * p3_ld<V, MZ>()) * sizeof(V);
-  cudaError_t e = set_smem(k_p3<T, MZ, B>, smem);
+  cudaError_t e = set_smem(k_p3<T, MZ, B, VAR>, smem);
   if (e != cudaSuccess) return e;
   const long long nxy = (long long)a.g.nx * a.g.ny;
   dim3 grid((unsigned)((nxy + TL - 1) / TL));
-  k_p3<T, MZ, B><<<grid, FftPlan<MZ>::G * NIN * TL, smem, s>>>(a);
+  k_p3<T, MZ, B, VAR><<<grid, FftPlan<MZ>::G * NIN * TL, smem, s>>>(a);
   return cudaGetLastError();
+}
+template <typename T, int MZ, bool B>
+static cudaError_t launch_p3(const PassArgs& a, cudaStream_t s) {
+  return a.var_p3 ? launch_p3_v<T, MZ, B, 1>(a, s) : launch_p3_v<T, MZ, B, 0>(a, s);
 }
 
 #define DNS_XY_SIZES(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(256) X(512)

@@ -91,6 +91,16 @@ _SIGS = {
     "dns_mlp_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
                                 C.c_float, C.c_uint, C.c_void_p, C.c_void_p]),
 }
+_SIGS.update({
+    "dns_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+    "dns_set_tiles": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "dns_create_batch": (C.c_int, [C.c_int, C.POINTER(dns_config), C.POINTER(C.c_void_p)]),
+    "dns_destroy_batch": (None, [C.c_void_p]),
+    "dns_batch_last_error": (C.c_char_p, [C.c_void_p]),
+    "dns_batch_context": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
+    "dns_integrate_batch": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(dns_step_info)]),
+})
 TRACE_COLS = 8
 MLP_PARAMS = 5313
 CONTROLLERS = {"I": 0, "PI": 1, "MLP": 2}
@@ -145,6 +155,17 @@ def _where(x):
     if hasattr(x, "is_cuda"):
         return 0 if x.is_cuda else 1
     return 1
+
+
+def _config(nx, ny=None, nz=None, nu=0.0, precision="fp64", lengths=None):
+    cfg = dns_config()
+    cfg.nx, cfg.ny, cfg.nz = nx, (nx if ny is None else ny), (nx if nz is None else nz)
+    if lengths is not None:
+        cfg.lx, cfg.ly, cfg.lz = (float(v) for v in lengths)
+    cfg.nu = float(nu)
+    cfg.precision = {"fp64": DNS_FP64, "fp32_mixed": DNS_FP32_MIXED}[precision] \
+        if isinstance(precision, str) else int(precision)
+    return cfg
 
 
 class Dns:
@@ -268,6 +289,14 @@ class Dns:
                 out[name.value.decode()] = (n.value, ms.value)
         return out
 
+    def autotune(self, reps=3):
+        v = (C.c_int * 2)()
+        self._check(self._lib.dns_autotune(self._h, int(reps), v), "dns_autotune")
+        return tuple(v)
+
+    def set_tiles(self, var_py, var_p3):
+        self._check(self._lib.dns_set_tiles(self._h, int(var_py), int(var_p3)), "dns_set_tiles")
+
     def set_trace(self, capacity, diagnostics=False):
         self._check(self._lib.dns_set_trace(self._h, int(capacity), 1 if diagnostics else 0), "dns_set_trace")
 
@@ -322,3 +351,62 @@ def dns_mlp_train(params, x, t, steps, batch=128, lr=1e-3, seed=0, loss_hist=Non
     return load().dns_mlp_train(C.c_void_p(_ptr(params)), C.c_void_p(_ptr(x)), C.c_void_p(_ptr(t)),
                                 int(x.shape[0]), int(steps), int(batch), float(lr), int(seed) & 0xFFFFFFFF,
                                 C.c_void_p(_ptr(loss_hist)) if loss_hist is not None else None, _st(stream))
+
+
+class _Borrowed(Dns):
+    """A context owned by a batch (not destroyed by Python)."""
+
+    def __init__(self, lib, handle, shape):
+        self._lib = lib
+        self._h = handle
+        self.shape = tuple(shape)
+        self.nzh = shape[2] // 2 + 1
+        self.ncomp = 3
+
+    def close(self):
+        self._h = C.c_void_p()
+
+
+class DnsBatch:
+    """An ensemble of independent simulations advanced by one graph launch."""
+
+    def __init__(self, configs):
+        """configs: list of dicts with keys nx[, ny, nz, nu, precision, lengths]."""
+        lib = load()
+        arr = (dns_config * len(configs))()
+        for i, c in enumerate(configs):
+            arr[i] = _config(**c)
+        h = C.c_void_p()
+        st = lib.dns_create_batch(len(configs), arr, C.byref(h))
+        if st != DNS_OK:
+            raise DnsError(st, "dns_create_batch")
+        self._lib, self._h, self.n = lib, h, len(configs)
+        self.instances = []
+        for i, c in enumerate(configs):
+            ch = C.c_void_p()
+            lib.dns_batch_context(h, i, C.byref(ch))
+            nx = c["nx"]
+            self.instances.append(_Borrowed(lib, ch, (nx, c.get("ny") or nx, c.get("nz") or nx)))
+
+    def integrate(self, method, t_end, rtol, atol, h0, check=True):
+        n = self.n
+        D = C.c_double * n
+        info = (dns_step_info * n)()
+        m = METHODS[method] if isinstance(method, str) else int(method)
+        st = self._lib.dns_integrate_batch(self._h, m, D(*t_end), D(*rtol), D(*atol), D(*h0), info)
+        if check and st != DNS_OK:
+            raise DnsError(st, "dns_integrate_batch: " + (self._lib.dns_batch_last_error(self._h) or b"").decode())
+        return list(info) if check else (st, list(info))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            for inst in self.instances:
+                inst.close()
+            self._lib.dns_destroy_batch(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

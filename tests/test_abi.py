@@ -39,8 +39,8 @@ def test_library_exports_every_declared_symbol(lib):
 def test_exports_are_c_abi_only(lib):
     out = os.popen(f"nm -D --defined-only {dns.LIB_PATH}").read()
     exported = set(re.findall(r" T (\w+)", out))
-    ours = {s for s in exported if s.startswith("dns_")}
-    assert ours == set(dns.declared_symbols())
+    # only the C ABI leaves the library: every other symbol is hidden
+    assert exported == set(dns.declared_symbols())
 
 
 def test_argument_checks_before_cuda(lib):
