@@ -65,8 +65,10 @@ typedef enum {
 } dns_status;
 
 /* Time integrators of Section 2.2.  BS5 is the Bogacki-Shampine 5(4) pair of Appendix A with
- * the b-hat error estimator; BS5_FIXED takes fixed steps and still evaluates the error norm. */
-typedef enum { DNS_RK4 = 0, DNS_BS5_FIXED = 1, DNS_BS5_ADAPTIVE = 2 } dns_method;
+ * the b-hat error estimator; DP5 the Dormand-Prince 5(4) pair of Appendix A.  *_FIXED take
+ * fixed steps and still evaluate the error norm; *_ADAPTIVE use the controller. */
+typedef enum { DNS_RK4 = 0, DNS_BS5_FIXED = 1, DNS_BS5_ADAPTIVE = 2, DNS_DP5_FIXED = 3,
+               DNS_DP5_ADAPTIVE = 4 } dns_method;
 
 /* DNS_FP64: every step in double precision.  DNS_FP32_MIXED: the transforms and the
  * nonlinear term in single precision; state, stage sums, projection, viscous term, error
@@ -161,6 +163,13 @@ DNS_API dns_status dns_get_info(dns_ctx* ctx, dns_step_info* info);
  * (Section 3.1, half-spectrum weights).  eps uses one right-hand-side evaluation.
  * Synchronous. */
 DNS_API dns_status dns_diagnostics(dns_ctx* ctx, double* E, double* Omega, double* eps);
+
+/* Energy spectrum of the current state (Section 3.3): E(k) = sum over shell k of
+ * w |uhat|^2 / (2 (nx ny nz)^2), shell k = nearest integer to |kappa| (velocity components;
+ * half-spectrum weights as dns_diagnostics).  *nshells receives the number of shells
+ * (0..K|kappa|max); out[0..min(cap, nshells)-1] receives E(k).  cap <= 0 or out NULL only
+ * queries the count.  Synchronous. */
+DNS_API dns_status dns_spectrum(dns_ctx* ctx, double* out, int cap, int* nshells);
 
 /* Per-kernel timing with CUDA events on the context's stream.  enable != 0 starts recording
  * (and clears earlier records).  dns_profile_get returns, for kernel index i < count, its

@@ -34,3 +34,11 @@ def divergence_max(grid: Grid, uhat: np.ndarray) -> float:
     """max_k |kappa . uhat_k| (zero for a solenoidal field)."""
     kx, ky, kz = grid.kvec()
     return float(np.max(np.abs(kx * uhat[0] + ky * uhat[1] + kz * uhat[2])))
+
+
+def energy_spectrum(grid: Grid, uhat: np.ndarray) -> np.ndarray:
+    """Shell-summed kinetic energy E(k) = sum_{|kappa| in shell k} w |uhat|^2 / (2 N^6),
+    shell k = nearest integer to |kappa| (Section 3.3 plots this spectrum); sum_k E(k) = E."""
+    shell = np.rint(np.sqrt(grid.k2)).astype(np.int64)
+    e = grid.weight * np.sum(np.abs(uhat[:3]) ** 2, axis=0) / (2.0 * grid.n3 ** 2)
+    return np.bincount(np.broadcast_to(shell, e.shape).ravel(), weights=e.ravel())

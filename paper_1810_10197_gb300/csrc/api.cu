@@ -41,6 +41,18 @@ const Frac kBS5B[8] = {{587, 8064}, {0, 1}, {4440339, 15491840}, {24353, 124800}
                        {387, 44800}, {2152, 5985}, {7267, 94080}, {0, 1}};
 const Frac kBS5Bh[8] = {{2479, 34992}, {0, 1}, {123, 416}, {612941, 3411720},
                         {43, 1440}, {2272, 6561}, {79937, 1113912}, {3293, 556956}};
+// Dormand-Prince 5(4) pair, Appendix A (rows 2..7 of A, b, b-hat).
+const Frac kDP5A[7][6] = {
+    {},
+    {{1, 5}},
+    {{3, 40}, {9, 40}},
+    {{44, 45}, {-56, 15}, {32, 9}},
+    {{19372, 6561}, {-25360, 2187}, {64448, 6561}, {-212, 729}},
+    {{9017, 3168}, {-355, 33}, {46732, 5247}, {49, 176}, {-5103, 18656}},
+    {{35, 384}, {0, 1}, {500, 1113}, {125, 192}, {-2187, 6784}, {11, 84}},
+};
+const Frac kDP5B[7] = {{35, 384}, {0, 1}, {500, 1113}, {125, 192}, {-2187, 6784}, {11, 84}, {0, 1}};
+const Frac kDP5Bh[7] = {{5179, 57600}, {0, 1}, {7571, 16695}, {393, 640}, {-92097, 339200}, {187, 2100}, {1, 40}};
 // Classical RK4.
 const Frac kRK4A[4][3] = {{}, {{1, 2}}, {{0, 1}, {1, 2}}, {{0, 1}, {0, 1}, {1, 1}}};
 const Frac kRK4B[4] = {{1, 6}, {1, 3}, {1, 3}, {1, 6}};
@@ -257,13 +269,18 @@ dns_status enqueue_attempt(dns_ctx* c, int method) {
     if (c->trace_diag) CK(launch_trace_diag(c->g, c->ctrl, c->partials, 0, c->stream), "trace diagnostics");
     return DNS_OK;
   }
-  // BS5: k_1 only when not carried over (first same as last)
+  // BS5 / DP5 (first same as last): k_1 only when not carried over
+  const bool dp = method >= 3;
+  const int S = dp ? 7 : 8;
+  auto A = [&](int i, int j) { return dp ? kDP5A[i][j] : kBS5A[i][j]; };
+  auto Bw = [&](int j) { return dp ? kDP5B[j] : kBS5B[j]; };
+  auto Bh = [&](int j) { return dp ? kDP5Bh[j] : kBS5Bh[j]; };
   if ((st = enqueue_rhs(c, c->ctrl, SLOT_U, SLOT_K1, 1)) != DNS_OK) return st;
-  for (int i = 1; i < 8; ++i) {
+  for (int i = 1; i < S; ++i) {
     int ks[7]; double cf[7]; int n = 0;
     for (int j = 0; j < i; ++j)
-      if (kBS5A[i][j].p != 0) { ks[n] = SLOT_K1 + j; cf[n] = frac_val(kBS5A[i][j]); ++n; }
-    const int ys = (i == 7) ? SLOT_UNEW : SLOT_Y;
+      if (A(i, j).p != 0) { ks[n] = SLOT_K1 + j; cf[n] = frac_val(A(i, j)); ++n; }
+    const int ys = (i == S - 1) ? SLOT_UNEW : SLOT_Y;
     if ((st = enqueue_stage(c, n, ks, cf, ys)) != DNS_OK) return st;
     if ((st = enqueue_rhs(c, c->ctrl, ys, SLOT_K1 + i, 0)) != DNS_OK) return st;
   }
@@ -273,16 +290,16 @@ dns_status enqueue_attempt(dns_ctx* c, int method) {
   e.nc = c->g.nc;
   e.partials = c->partials;
   int n = 0;
-  for (int j = 0; j < 8; ++j) {
-    if (kBS5B[j].p * kBS5Bh[j].q == kBS5Bh[j].p * kBS5B[j].q) continue;
+  for (int j = 0; j < S; ++j) {
+    if (Bw(j).p * Bh(j).q == Bh(j).p * Bw(j).q) continue;
     e.kslot[n] = SLOT_K1 + j;
-    e.coef[n] = frac_diff(kBS5B[j], kBS5Bh[j]);
+    e.coef[n] = frac_diff(Bw(j), Bh(j));
     ++n;
   }
   e.nterms = n;
   CK(timed(c, PR_ERR, [&] { return launch_err_partials(e, c->stream); }), "error norm");
   CK(timed(c, PR_CTRL, [&] {
-       return launch_controller(c->ctrl, c->partials, method, 8, c->g.nmodes_half, c->g.nc, c->stream);
+       return launch_controller(c->ctrl, c->partials, method, S, c->g.nmodes_half, c->g.nc, c->stream);
      }), "controller");
   if (c->trace_diag) CK(launch_trace_diag(c->g, c->ctrl, c->partials, method, c->stream), "trace diagnostics");
   return DNS_OK;
@@ -513,7 +530,7 @@ dns_status dns_rhs(dns_ctx* c, const void* uhat_dev, void* f_dev) {
 
 static dns_status config(dns_ctx* c, double t_end, int method, double rtol, double atol, double h0,
                          int max_rejects) {
-  if (method < 0 || method > 2) return fail(c, DNS_ERR_ARG, "unknown method");
+  if (method < 0 || method > 4) return fail(c, DNS_ERR_ARG, "unknown method");
   if (!(t_end == t_end)) return fail(c, DNS_ERR_ARG, "t_end is NaN");
   if (method != DNS_RK4 && (!(rtol >= 0) || !(atol >= 0) || (rtol == 0 && atol == 0)))
     return fail(c, DNS_ERR_ARG, "tolerances must be >= 0 and not both 0");
@@ -630,6 +647,31 @@ dns_status dns_profile_get(dns_ctx* c, int i, const char** name, long long* laun
   if (name) *name = kPassNames[i];
   if (launches) *launches = n;
   if (total_ms) *total_ms = ms;
+  return DNS_OK;
+}
+
+dns_status dns_spectrum(dns_ctx* c, double* out, int cap, int* nshells) {
+  dns_status s = check_ctx(c);
+  if (s != DNS_OK) return s;
+  if (!c->has_state) return fail(c, DNS_ERR_STATE, "no state set");
+  const Geom& g = c->g;
+  const double kmax = std::sqrt(std::pow(g.sx * g.Kx, 2) + std::pow(g.sy * g.Ky, 2) + std::pow(g.sz * g.Kz, 2));
+  const int ns = (int)std::floor(kmax + 0.5) + 1;
+  if (nshells) *nshells = ns;
+  if (!out || cap <= 0) return DNS_OK;
+  if ((s = read_ctrl(c)) != DNS_OK) return s;
+  double* dev = nullptr;
+  // scratch: the error-norm partials buffer is too small; use the staging buffer of host copies
+  if ((s = ensure_stage(c)) != DNS_OK) return s;
+  const size_t need = (size_t)(152 + 1) * ns * sizeof(double);
+  const size_t have = (size_t)g.nc * g.nx * g.ny * g.nzh * sizeof(double2);
+  if (need > have) return fail(c, DNS_ERR_UNSUPPORTED, "spectrum scratch too small");
+  dev = reinterpret_cast<double*>(c->full_stage);
+  CK(launch_spectrum(g, c->uu[c->host_ctrl->parity], dev + ns, ns, dev, c->stream), "spectrum");
+  std::vector<double> h(ns);
+  CK(cudaMemcpyAsync(h.data(), dev, ns * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "read");
+  CK(cudaStreamSynchronize(c->stream), "synchronize");
+  for (int i = 0; i < std::min(ns, cap); ++i) out[i] = h[i];
   return DNS_OK;
 }
 
@@ -806,8 +848,8 @@ struct dns_batch {
   std::vector<cudaEvent_t> joins;
   DnsCtrl** d_ctrls = nullptr;
   unsigned long long* d_iter = nullptr;
-  cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
-  cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
+  cudaGraphExec_t exec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaGraph_t graph[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   int device = 0;
   std::string err;
 };
@@ -818,7 +860,7 @@ void dns_destroy_batch(dns_batch* b) {
   if (!b) return;
   cudaSetDevice(b->device);
   if (b->stream) cudaStreamSynchronize(b->stream);
-  for (int m = 0; m < 3; ++m) {
+  for (int m = 0; m < 5; ++m) {
     if (b->exec[m]) cudaGraphExecDestroy(b->exec[m]);
     if (b->graph[m]) cudaGraphDestroy(b->graph[m]);
   }
@@ -877,7 +919,7 @@ dns_status dns_batch_context(dns_batch* b, int i, dns_ctx** out) {
 
 dns_status dns_integrate_batch(dns_batch* b, int method, const double* t_end, const double* rtol,
                                const double* atol, const double* h0, dns_step_info* info) {
-  if (!b || !t_end || !rtol || !atol || !h0 || method < 0 || method > 2) return DNS_ERR_ARG;
+  if (!b || !t_end || !rtol || !atol || !h0 || method < 0 || method > 4) return DNS_ERR_ARG;
   if (cudaSetDevice(b->device) != cudaSuccess) return DNS_ERR_CUDA;
   const int n = (int)b->ctx.size();
   dns_status s;

@@ -93,6 +93,21 @@ __host__ __device__ inline void axis_twiddle_turns(int n, bool zaxis, int i, int
 
 template <typename V> __device__ __forceinline__ V zero2() { return mk<V>(0, 0); }
 
+// Asynchronous global->shared copy of one complex element (8 or 16 bytes); `valid` false
+// writes zeros (src-size 0: nothing is read from `src`, which must still be a valid address).
+// Every thread issues all its copies, then cp_async_wait() and a barrier: many loads stay in
+// flight per thread instead of one.
+template <typename V>
+__device__ __forceinline__ void cp_async_elem(V* dst, const V* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(V) == 16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0) : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+  }
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Visit (row, q) for row < rows, q < len: one warp per row, lanes along q (coalesced, no
 // division) when the CTA is whole warps; otherwise a flat loop.
 template <int NTH, typename F>
@@ -236,16 +251,18 @@ k_py(const PassArgs a) {
     const V* src = in + ((size_t)f * g.nx + x) * g.My * Mz;
     for (int i = tid; i < g.My * TZ; i += nth) {
       const int jy = i / TZ, c = i - jy * TZ, kz = kz0 + c;
-      const V v = kz < Mz ? src[(size_t)jy * Mz + kz] : zero2<V>();
-      lines[c * LD + pidx<V>(jy <= g.Ky ? jy : NY - g.My + jy)] = v;
+      const bool ok = kz < Mz;
+      cp_async_elem(&lines[c * LD + pidx<V>(jy <= g.Ky ? jy : NY - g.My + jy)], ok ? &src[(size_t)jy * Mz + kz] : src, ok);
     }
   } else {
     const V* src = in + ((size_t)f * g.nx + x) * NY * Mz;
     for (int i = tid; i < NY * TZ; i += nth) {
       const int y = i / TZ, c = i - y * TZ, kz = kz0 + c;
-      lines[c * LD + pidx<V>(y)] = kz < Mz ? src[(size_t)y * Mz + kz] : zero2<V>();
+      const bool ok = kz < Mz;
+      cp_async_elem(&lines[c * LD + pidx<V>(y)], ok ? &src[(size_t)y * Mz + kz] : src, ok);
     }
   }
+  cp_async_wait();
   __syncthreads();
   line_fft<V, NY, INVERSE ? +1 : -1>(lines + (tid / G) * LD, tid % G, tw);
   if (INVERSE) {
@@ -298,9 +315,10 @@ k_p3(const PassArgs a) {
   for_rows<NTH>(NIN * TL, MZ + 1, [&](int row, int kz) {
     const int f = row / TL, l = row - f * TL;
     const long long xy = xy0 + l;
-    lines[row * LD + pidx<V>(kz)] =
-        (kz < Mz && xy < nxy) ? in[((size_t)f * nxy + xy) * Mz + kz] : zero2<V>();
+    const bool ok = kz < Mz && xy < nxy;
+    cp_async_elem(&lines[row * LD + pidx<V>(kz)], ok ? &in[((size_t)f * nxy + xy) * Mz + kz] : in, ok);
   });
+  cp_async_wait();
   __syncthreads();
   // C2R pre-step on pairs (k, MZ-k), k = 0..MZ/2
   {
@@ -390,8 +408,10 @@ k_p5(const PassArgs a) {
   copy_tw(tw, reinterpret_cast<const V*>(a.tw), NTW);
   for (int i = tid; i < NF * NX * TC; i += nth) {
     const int f = i / (NX * TC), r = i - f * (NX * TC), x = r / TC, c = r - x * TC, col = col0 + c;
-    lines[(f * TC + c) * LD + pidx<V>(x)] = col < g.MyMz ? in[((size_t)f * NX + x) * g.MyMz + col] : zero2<V>();
+    const bool ok = col < g.MyMz;
+    cp_async_elem(&lines[(f * TC + c) * LD + pidx<V>(x)], ok ? &in[((size_t)f * NX + x) * g.MyMz + col] : in, ok);
   }
+  cp_async_wait();
   __syncthreads();
   line_fft<V, NX, -1>(lines + (tid / G) * LD, tid % G, tw);
   const double fc = (a.ctrl && a.kf2 > 0) ? a.ctrl->forcing_coef : 0.0;

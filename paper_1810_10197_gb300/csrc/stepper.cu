@@ -111,6 +111,9 @@ __global__ void __launch_bounds__(kRedThreads) k_err_partials(const ErrArgs a) {
   }
 }
 
+__device__ __forceinline__ bool adaptive_method(int m) { return m == 2 || m == 4; }
+__device__ __forceinline__ int method_stages(int m) { return m == 0 ? 4 : (m >= 3 ? 7 : 8); }
+
 __global__ void k_begin_attempt(DnsCtrl* c, int method) {
   if (c->done || c->status != 0) { c->skip = 1; return; }
   const double rem = c->t_end - c->t;
@@ -128,7 +131,7 @@ __global__ void k_begin_attempt(DnsCtrl* c, int method) {
   c->slot[SLOT_UNEW] = c->uu[1 - p];
   c->slot[SLOT_K1] = c->kk[p];
   for (int i = 2; i <= 7; ++i) c->slot[SLOT_K1 + i - 1] = c->kfix[i];
-  if (method != 0) c->slot[SLOT_K1 + 7] = c->kk[1 - p];   // k_8 of an FSAL pair
+  if (method != 0) c->slot[SLOT_K1 + method_stages(method) - 1] = c->kk[1 - p];   // last k of an FSAL pair
   c->need_k1 = (method == 0) ? 1 : !c->k1_valid;
 }
 
@@ -183,7 +186,7 @@ __global__ void __launch_bounds__(kRedThreads) k_controller(DnsCtrl* c, const do
     bool accept = true;
     double fac = 1.0;
     int mlp_now = 0;
-    if (method == 2) {
+    if (adaptive_method(method)) {
       const bool fin = isfinite(err);
       accept = fin && err <= 1.0;
       const double dmax = c->after_reject ? 1.0 : 2.0;
@@ -231,7 +234,7 @@ __global__ void __launch_bounds__(kRedThreads) k_controller(DnsCtrl* c, const do
   const double t_before = c->t;
   c->err = err;
   double h_new = c->h;
-  if (method == 2) h_new = c->h_try * fac;
+  if (adaptive_method(method)) h_new = c->h_try * fac;
   if (accept) {
     c->t = c->clipped ? c->t_end : c->t + c->h_try;
     c->parity ^= 1;
@@ -444,7 +447,51 @@ __global__ void __launch_bounds__(kRedThreads) k_diag_partials(const Geom g, con
   }
 }
 
+// Energy spectrum: per-block shell histograms of w |u|^2 (velocity), then a fixed-order sum.
+__global__ void __launch_bounds__(kRedThreads) k_spectrum_partials(const Geom g, const double2* __restrict__ u,
+                                                                   double* partials, int nshell) {
+  extern __shared__ double hist[];
+  for (int i = threadIdx.x; i < nshell; i += blockDim.x) hist[i] = 0.0;
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < g.M; r += stride) {
+    const int ix = (int)(r / g.MyMz), rem = (int)(r - (long long)ix * g.MyMz);
+    const int jy = rem / g.Mz, kz = rem - jy * g.Mz;
+    const double kx = g.sx * signed_mode(ix, g.Kx, g.Mx), ky = g.sy * signed_mode(jy, g.Ky, g.My);
+    const double kzz = g.sz * kz;
+    const int sh = (int)rint(sqrt(kx * kx + ky * ky + kzz * kzz));
+    const double w = kz == 0 ? 1.0 : 2.0;
+    double m2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const double2 a = u[q * g.M + r];
+      m2 += a.x * a.x + a.y * a.y;
+    }
+    if (sh < nshell) atomicAdd(&hist[sh], w * m2);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nshell; i += blockDim.x) partials[(size_t)blockIdx.x * nshell + i] = hist[i];
+}
+
+__global__ void k_spectrum_finish(const double* partials, int nblk, int nshell, double scale, double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nshell) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += partials[(size_t)b * nshell + i];
+  out[i] = s * scale;
+}
+
 }  // namespace
+
+constexpr int kSpecBlocks = 152;
+cudaError_t launch_spectrum(const Geom& g, const double2* u, double* partials, int nshell, double* out,
+                            cudaStream_t s) {
+  const size_t smem = (size_t)nshell * sizeof(double);
+  k_spectrum_partials<<<kSpecBlocks, kRedThreads, smem, s>>>(g, u, partials, nshell);
+  k_spectrum_finish<<<(nshell + 127) / 128, 128, 0, s>>>(partials, kSpecBlocks, nshell,
+                                                          0.5 * g.inv_n3 * g.inv_n3, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_stage_sum(const StageArgs& a, cudaStream_t s) {
   const int blocks = grid_for(a.n2, 256, 152 * 16);
@@ -466,6 +513,7 @@ cudaError_t launch_err_partials(const ErrArgs& a, cudaStream_t s) {
   switch (a.nterms) {
     case 6: k_err_partials<6><<<kRedBlocks, kRedThreads, 0, s>>>(a); break;
     case 7: k_err_partials<7><<<kRedBlocks, kRedThreads, 0, s>>>(a); break;
+    case 5: k_err_partials<5><<<kRedBlocks, kRedThreads, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

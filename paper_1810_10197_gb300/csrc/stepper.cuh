@@ -48,6 +48,9 @@ cudaError_t launch_copy_slot(DnsCtrl* c, int slot, double2* dst, long long n2, c
 cudaError_t launch_forcing_coef(const Geom& g, DnsCtrl* c, int yslot, double kf, double power,
                                 int gate_k1, cudaStream_t s);
 constexpr int kRedStride = 4;      // partial sums per block (components)
+// energy spectrum: partials[152][nshell] doubles of scratch, out[nshell]
+cudaError_t launch_spectrum(const Geom& g, const double2* u, double* partials, int nshell, double* out,
+                            cudaStream_t s);
 cudaError_t launch_diag_partials(const Geom& g, const double2* u, const double2* f,
                                  double* partials, cudaStream_t s);
 

@@ -21,8 +21,9 @@ DNS_OK = 0
 STATUS_NAMES = {0: "DNS_OK", 1: "DNS_ERR_ARG", 2: "DNS_ERR_CUDA", 3: "DNS_ERR_OOM",
                 4: "DNS_ERR_NONFINITE", 5: "DNS_ERR_STEP_UNDERFLOW", 6: "DNS_ERR_MAX_REJECTS",
                 7: "DNS_ERR_TIMEOUT", 8: "DNS_ERR_STATE", 9: "DNS_ERR_UNSUPPORTED"}
-DNS_RK4, DNS_BS5_FIXED, DNS_BS5_ADAPTIVE = 0, 1, 2
-METHODS = {"RK4": DNS_RK4, "BS5_FIXED": DNS_BS5_FIXED, "BS5_ADAPTIVE": DNS_BS5_ADAPTIVE}
+DNS_RK4, DNS_BS5_FIXED, DNS_BS5_ADAPTIVE, DNS_DP5_FIXED, DNS_DP5_ADAPTIVE = 0, 1, 2, 3, 4
+METHODS = {"RK4": DNS_RK4, "BS5_FIXED": DNS_BS5_FIXED, "BS5_ADAPTIVE": DNS_BS5_ADAPTIVE,
+           "DP5_FIXED": DNS_DP5_FIXED, "DP5_ADAPTIVE": DNS_DP5_ADAPTIVE}
 DNS_FP64, DNS_FP32_MIXED = 0, 1
 SUPPORTED_N = (8, 12, 16, 24, 32, 48, 64, 96, 128, 256, 512)
 
@@ -92,6 +93,7 @@ _SIGS = {
                                 C.c_float, C.c_uint, C.c_void_p, C.c_void_p]),
 }
 _SIGS.update({
+    "dns_spectrum": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "dns_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "dns_set_tiles": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "dns_create_batch": (C.c_int, [C.c_int, C.POINTER(dns_config), C.POINTER(C.c_void_p)]),
@@ -287,6 +289,15 @@ class Dns:
                         "dns_profile_get")
             if n.value:
                 out[name.value.decode()] = (n.value, ms.value)
+        return out
+
+    def spectrum(self):
+        """Shell energy spectrum E(k), k = 0..kmax, of the current state."""
+        n = C.c_int()
+        self._check(self._lib.dns_spectrum(self._h, None, 0, C.byref(n)), "dns_spectrum")
+        out = np.empty(n.value)
+        self._check(self._lib.dns_spectrum(self._h, C.c_void_p(out.ctypes.data), n.value, C.byref(n)),
+                    "dns_spectrum")
         return out
 
     def autotune(self, reps=3):

@@ -172,3 +172,30 @@ def test_step_underflow_and_nonfinite_statuses():
     d2 = make(shape, bad, nu)
     st, info = d2.integrate(1.0, "BS5_ADAPTIVE", 1e-6, 1e-6, h0=0.1, max_rejects=3, check=False)
     assert st == 4 and info.n_rej == 4 and info.t == 0.0
+
+
+@pytest.mark.parametrize("method,tol", [("DP5_ADAPTIVE", 1e-8), ("DP5_FIXED", 1e-6)])
+def test_dp5_pair_matches_oracle(method, tol):
+    # Appendix A's Dormand-Prince 5(4) pair through the same kernels (7 stages, FSAL)
+    shape, nu = (32, 32, 32), 0.01
+    g = sp.Grid(*shape)
+    uh = g.dealias(syn.taylor_green_3d_hat(*shape) + 0.1 * syn.random_solenoidal_hat(*shape, seed=2, k0=3.0))
+    ref = rk.integrate(oracle_f(g, nu), uh, 0.0, 0.5, method, 0.02, tol, tol, nmodes=g.nmodes_half)
+    d = make(shape, uh, nu)
+    info = d.integrate(0.5, method, tol, tol, h0=0.02)
+    assert (info.n_acc, info.n_rej, info.n_rhs) == (ref.n_acc, ref.n_rej, ref.n_rhs)
+    assert rel_l2(d.get_state(), ref.u) < 1e-12
+
+
+def test_energy_spectrum_matches_oracle():
+    shape = (48, 48, 48)
+    g = sp.Grid(*shape)
+    uh = g.dealias(syn.random_solenoidal_hat(*shape, seed=12, k0=4.0))
+    d = make(shape, uh, 0.01)
+    Ek = d.spectrum()
+    ref = diag.energy_spectrum(g, uh)
+    # the oracle's bincount also spans shells beyond the retained box (all zero here)
+    assert len(Ek) >= len(np.trim_zeros(ref, "b"))
+    assert np.all(ref[len(Ek):] == 0)
+    assert np.max(np.abs(Ek - ref[:len(Ek)])) < 1e-12 * np.max(ref)
+    assert abs(Ek.sum() - diag.energy(g, uh)) < 1e-12

@@ -70,3 +70,14 @@ def test_rayleigh_taylor_profile():
     mid = rho[:, :, 16]
     edge = rho[:, :, 0]
     assert np.all(mid > 0.4) and np.all(edge < -0.4)
+
+
+def test_energy_spectrum_sums_to_energy_and_places_tg_in_shell_2():
+    n = 16
+    g = sp.Grid(n, n, n)
+    uh = syn.taylor_green_3d_hat(n, n, n)
+    Ek = diag.energy_spectrum(g, uh)
+    # every TG mode has |k| = sqrt(3) -> shell 2
+    assert abs(Ek[2] - 0.125) < 1e-15 and abs(Ek.sum() - 0.125) < 1e-15
+    r = g.dealias(syn.random_solenoidal_hat(n, n, n, seed=3, k0=3.0))
+    assert abs(diag.energy_spectrum(g, r).sum() - diag.energy(g, r)) < 1e-13
