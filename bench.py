@@ -15,6 +15,7 @@ independent replicas (the method has no exchange step on one field per GPU here)
 from __future__ import annotations
 
 import argparse
+import math
 import json
 import os
 import statistics
@@ -271,6 +272,107 @@ def run_ensemble(args):
     return 0
 
 
+def run_accuracy(args):
+    """Simulated time per GPU-second at a fixed final-state L2 error (BASELINE configs[1]):
+    TG 256^3, nu = 1/1600, t in [0, T].  Error-versus-cost curves (Section 3's comparison) for
+    BS5 adaptive over tolerances, RK4 over halving steps, DP5 and the FP32-mixed form, all
+    against a time-converged FP64 reference (BS5 at tol 1e-10); comparisons at equal error
+    interpolate each curve in log-log.  Energy and enstrophy are traced every step."""
+    import torch
+
+    from paper_1810_10197_gb300 import Dns, build
+    torch.cuda.set_device(0)
+    build.build()
+    n, T = args.grid, args.t_end
+    nu = FLOWS[args.flow]["nu"]
+    u0 = make_field(args)
+    u0_dev = torch.from_numpy(u0).cuda()
+
+    def run(method, tol, h0, precision="fp64", trace=False):
+        d = Dns(n, nu=nu, precision=precision)
+        d.autotune()
+        d.set_state(u0_dev, 0.0)
+        if trace:
+            d.set_trace(100000, diagnostics=True)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        info = d.integrate(T, method, tol, tol, h0=h0)
+        ev1.record()
+        torch.cuda.synchronize()
+        sec = ev0.elapsed_time(ev1) * 1e-3
+        u = d.get_state()
+        tr = d.trace() if trace else None
+        d.close()
+        return u, info, sec, tr
+
+    t_start = time.perf_counter()
+    u_ref, i_ref, s_ref, _ = run("BS5_ADAPTIVE", 1e-10, H0)
+    nrm = np.linalg.norm(u_ref)
+
+    def rec(u, i, sec):
+        return {"l2_error": float(np.linalg.norm(u - u_ref) / nrm), "rhs_evals": int(i.n_rhs),
+                "accepted": int(i.n_acc), "rejected": int(i.n_rej), "gpu_seconds": sec,
+                "sim_time_per_gpu_s": T / sec}
+
+    curves = {"bs5_fp64": [], "rk4_fp64": [], "dp5_fp64": [], "bs5_fp32mixed": []}
+    trace = None
+    for tol in args.tols:
+        u, i, sec, tr = run("BS5_ADAPTIVE", tol, H0, trace=(tol == TOL))
+        curves["bs5_fp64"].append(dict(tol=tol, **rec(u, i, sec)))
+        if tol == TOL:
+            acc = tr[tr[:, 3] > 0.5]
+            trace = {"t": (acc[:, 0] + acc[:, 1]).tolist(), "h": acc[:, 1].tolist(), "E": acc[:, 5].tolist(),
+                     "Omega": acc[:, 6].tolist(), "eps": acc[:, 7].tolist()}
+    for tol in args.tols[:4]:
+        u, i, sec, _ = run("BS5_ADAPTIVE", tol, H0, precision="fp32_mixed")
+        curves["bs5_fp32mixed"].append(dict(tol=tol, **rec(u, i, sec)))
+    for tol in (1e-6, 1e-8):
+        u, i, sec, _ = run("DP5_ADAPTIVE", tol, H0)
+        curves["dp5_fp64"].append(dict(tol=tol, **rec(u, i, sec)))
+    dt = args.rk4_dt
+    for _ in range(args.rk4_levels):
+        u, i, sec, _ = run("RK4", 0.0, dt)
+        curves["rk4_fp64"].append(dict(dt=dt, **rec(u, i, sec)))
+        dt /= 2
+
+    def at_error(curve, e, key):
+        """log-log interpolation of `key` on a curve at error e (None outside its range)."""
+        pts = sorted((c["l2_error"], c[key]) for c in curve if c["l2_error"] > 0)
+        for (e0, v0), (e1, v1) in zip(pts, pts[1:]):
+            if e0 <= e <= e1:
+                w = (math.log(e) - math.log(e0)) / (math.log(e1) - math.log(e0)) if e1 > e0 else 0.0
+                return math.exp(math.log(v0) + w * (math.log(v1) - math.log(v0)))
+        return None
+
+    cmp = []
+    for c in curves["bs5_fp64"]:
+        e = c["l2_error"]
+        rk_rhs = at_error(curves["rk4_fp64"], e, "rhs_evals")
+        rk_sim = at_error(curves["rk4_fp64"], e, "sim_time_per_gpu_s")
+        cmp.append({"l2_error": e, "bs5_rhs": c["rhs_evals"], "rk4_rhs_at_same_error": rk_rhs,
+                    "rhs_ratio_rk4_over_bs5": (rk_rhs / c["rhs_evals"]) if rk_rhs else None,
+                    "bs5_sim_time_per_gpu_s": c["sim_time_per_gpu_s"], "rk4_sim_time_per_gpu_s": rk_sim})
+    fp32_vs_fp64 = []
+    for c in curves["bs5_fp32mixed"]:
+        e = c["l2_error"]
+        fp64_sim = at_error(curves["bs5_fp64"], e, "sim_time_per_gpu_s")
+        fp32_vs_fp64.append({"l2_error": e, "fp32_sim_time_per_gpu_s": c["sim_time_per_gpu_s"],
+                             "fp64_sim_time_per_gpu_s_at_same_error": fp64_sim,
+                             "speedup": (c["sim_time_per_gpu_s"] / fp64_sim) if fp64_sim else None})
+    main = [c for c in curves["bs5_fp64"] if c["tol"] == TOL][0]
+    out = {"metric": METRIC, "value": main["sim_time_per_gpu_s"],
+           "unit": f"sim-time/GPU-s (BS5 FP64 tol 1e-6, final L2 error {main['l2_error']:.2e})",
+           "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{'taylor_green_3d' if args.flow == 'tg' else 'hit_forced'}_{n}^3_nu{nu:g}_t0-{T:g}",
+                      "reference": "BS5 adaptive tol 1e-10, FP64", "reference_rhs_evals": int(i_ref.n_rhs),
+                      "reference_gpu_seconds": s_ref},
+           "curves": curves, "bs5_vs_rk4_at_equal_error": cmp, "fp32mixed_vs_fp64_at_equal_error": fp32_vs_fp64,
+           "trace_bs5_fp64_tol1e-6": trace, "wall_seconds": time.perf_counter() - t_start}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -468,7 +570,10 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_mixed"])
     ap.add_argument("--flow", default="tg", choices=["tg", "hit"])
     ap.add_argument("--mode", default="step", choices=["step", "rhs"])
-    ap.add_argument("--workload", default="single", choices=["single", "ensemble"])
+    ap.add_argument("--workload", default="single", choices=["single", "ensemble", "accuracy"])
+    ap.add_argument("--rk4-dt", type=float, default=0.02)
+    ap.add_argument("--rk4-levels", type=int, default=4)
+    ap.add_argument("--tols", type=float, nargs="+", default=[1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9])
     ap.add_argument("--count", type=int, default=64)
     ap.add_argument("--t-end", type=float, default=0.5)
     args = ap.parse_args()
@@ -478,6 +583,10 @@ def main():
         return run_reference(args)
     if args.workload == "ensemble":
         return run_ensemble(args)
+    if args.workload == "accuracy":
+        if args.t_end == 0.5:
+            args.t_end = T_END
+        return run_accuracy(args)
     return run_gpu(args)
 
 
