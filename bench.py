@@ -287,9 +287,15 @@ def run_accuracy(args):
     nu = FLOWS[args.flow]["nu"]
     u0 = make_field(args)
     u0_dev = torch.from_numpy(u0).cuda()
+    forcing = None
+    if args.flow == "hit":
+        d0 = Dns(n, nu=nu)
+        d0.set_state(u0_dev, 0.0)
+        forcing = (FLOWS["hit"]["forcing"][0], d0.diagnostics()[2])
+        d0.close()
 
     def run(method, tol, h0, precision="fp64", trace=False):
-        d = Dns(n, nu=nu, precision=precision)
+        d = Dns(n, nu=nu, precision=precision, forcing=forcing)
         d.autotune()
         d.set_state(u0_dev, 0.0)
         if trace:
@@ -327,7 +333,7 @@ def run_accuracy(args):
     for tol in args.tols[:4]:
         u, i, sec, _ = run("BS5_ADAPTIVE", tol, H0, precision="fp32_mixed")
         curves["bs5_fp32mixed"].append(dict(tol=tol, **rec(u, i, sec)))
-    for tol in (1e-6, 1e-8):
+    for tol in args.dp5_tols:
         u, i, sec, _ = run("DP5_ADAPTIVE", tol, H0)
         curves["dp5_fp64"].append(dict(tol=tol, **rec(u, i, sec)))
     dt = args.rk4_dt
@@ -360,15 +366,88 @@ def run_accuracy(args):
         fp32_vs_fp64.append({"l2_error": e, "fp32_sim_time_per_gpu_s": c["sim_time_per_gpu_s"],
                              "fp64_sim_time_per_gpu_s_at_same_error": fp64_sim,
                              "speedup": (c["sim_time_per_gpu_s"] / fp64_sim) if fp64_sim else None})
-    main = [c for c in curves["bs5_fp64"] if c["tol"] == TOL][0]
+    main = ([c for c in curves["bs5_fp64"] if c["tol"] == TOL] or curves["bs5_fp64"])[0]
     out = {"metric": METRIC, "value": main["sim_time_per_gpu_s"],
            "unit": f"sim-time/GPU-s (BS5 FP64 tol 1e-6, final L2 error {main['l2_error']:.2e})",
            "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
            "config": {"workload": f"{'taylor_green_3d' if args.flow == 'tg' else 'hit_forced'}_{n}^3_nu{nu:g}_t0-{T:g}",
+                      "forcing": forcing,
                       "reference": "BS5 adaptive tol 1e-10, FP64", "reference_rhs_evals": int(i_ref.n_rhs),
                       "reference_gpu_seconds": s_ref},
            "curves": curves, "bs5_vs_rk4_at_equal_error": cmp, "fp32mixed_vs_fp64_at_equal_error": fp32_vs_fp64,
            "trace_bs5_fp64_tol1e-6": trace, "wall_seconds": time.perf_counter() - t_start}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_controllers(args):
+    """BASELINE configs[4]: the learned step-size proposal against the Section 2.2.1 (I) and PI
+    controllers on periodic Boussinesq Rayleigh-Taylor (128 x 128 x 256, Atwood 0.5, tanh
+    interfaces of width 0.05, multimode perturbation 1e-3, nu = kappa = 1e-3, Ri = 1).  The
+    network is trained on the GPU from trajectories of Taylor-Green and forced-HIT flows
+    (configs[0..2] shapes at 32^3, tolerances 1e-5..1e-8); every run is measured against a
+    tol-1e-9 FP64 reference of the same problem."""
+    import torch
+
+    import synthetic as syn
+    from paper_1810_10197_gb300 import Dns, build, learned
+    torch.cuda.set_device(0)
+    build.build()
+    t_start = time.perf_counter()
+    flows = []
+    for tol in (1e-5, 1e-6, 1e-7, 1e-8):
+        for m, nu in ((32, 0.01), (32, 0.005), (48, 0.003)):
+            flows.append(((m, m, m), syn.taylor_green_3d_hat(m, m, m), nu, None, tol, 2.0))
+            flows.append(((m, m, m), syn.random_solenoidal_hat(m, m, m, seed=3 + m, k0=3.0), nu, (2.5, 0.05), tol, 1.0))
+    X, T = learned.training_set(flows, lambda shape, nu, forcing: Dns(*shape, nu=nu, forcing=forcing),
+                                lambda a: torch.from_numpy(a).cuda())
+    params, hist = learned.train(X, T, steps=3000, lr=2e-3, seed=0)
+    train_s = time.perf_counter() - t_start
+    nx, ny, nz = args.rt_shape
+    from oracle import spectral as _sp   # initial-field transform only (input construction)
+    rho, L = syn.rayleigh_taylor_fields(nx, ny, nz, seed=7)
+    g = _sp.Grid(nx, ny, nz, lengths=L)
+    Y = np.zeros((4, nx, ny, nz // 2 + 1), complex)
+    Y[3] = g.dealias(g.to_spectral(rho))
+    Yd = torch.from_numpy(Y).cuda()
+    T_end = args.t_end
+
+    def run(kind, tol):
+        d = Dns(nx, ny, nz, nu=1e-3, lengths=L, boussinesq=(1e-3, 1.0))
+        d.autotune()
+        d.set_state(Yd, 0.0)
+        if kind == "MLP":
+            d.set_controller("MLP", params)
+        elif kind == "PI":
+            d.set_controller("PI")
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        st, info = d.integrate(T_end, "BS5_ADAPTIVE", tol, tol, h0=1e-3, check=False)
+        ev1.record()
+        torch.cuda.synchronize()
+        u = d.get_state()
+        d.close()
+        return u, info, ev0.elapsed_time(ev1) * 1e-3, st
+
+    u_ref, i_ref, s_ref, _ = run("I", args.ref_tol)
+    nrm = np.linalg.norm(u_ref)
+    rows = {}
+    for kind in ("I", "PI", "MLP"):
+        u, info, sec, st = run(kind, TOL)
+        rows[kind] = {"status": st, "t": info.t, "rhs_evals": int(info.n_rhs), "accepted": int(info.n_acc),
+                      "rejected": int(info.n_rej), "l2_error": float(np.linalg.norm(u - u_ref) / nrm),
+                      "gpu_seconds": sec, "sim_time_per_gpu_s": T_end / sec}
+    out = {"metric": METRIC, "value": rows["MLP"]["sim_time_per_gpu_s"], "unit": "sim-time/GPU-s (MLP controller)",
+           "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"rayleigh_taylor_{nx}x{ny}x{nz}_atwood0.5_t0-{T_end:g}_bs5_tol1e-6",
+                      "reference": f"BS5 adaptive tol {args.ref_tol:g} (I controller)",
+                      "reference_rhs_evals": int(i_ref.n_rhs), "training_pairs": int(len(X)),
+                      "training_loss_first_last": [float(hist[:20].mean()), float(hist[-200:].mean())],
+                      "training_seconds_incl_trajectories": train_s},
+           "runs": rows,
+           "mlp_rhs_saving_vs_I": rows["I"]["rhs_evals"] / max(rows["MLP"]["rhs_evals"], 1),
+           "wall_seconds": time.perf_counter() - t_start}
     print(json.dumps(out), flush=True)
     return 0
 
@@ -570,10 +649,13 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_mixed"])
     ap.add_argument("--flow", default="tg", choices=["tg", "hit"])
     ap.add_argument("--mode", default="step", choices=["step", "rhs"])
-    ap.add_argument("--workload", default="single", choices=["single", "ensemble", "accuracy"])
+    ap.add_argument("--workload", default="single", choices=["single", "ensemble", "accuracy", "controllers"])
+    ap.add_argument("--rt-shape", type=int, nargs=3, default=[128, 128, 256])
+    ap.add_argument("--ref-tol", type=float, default=1e-9)
     ap.add_argument("--rk4-dt", type=float, default=0.02)
     ap.add_argument("--rk4-levels", type=int, default=4)
     ap.add_argument("--tols", type=float, nargs="+", default=[1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9])
+    ap.add_argument("--dp5-tols", type=float, nargs="*", default=[1e-6, 1e-8])
     ap.add_argument("--count", type=int, default=64)
     ap.add_argument("--t-end", type=float, default=0.5)
     args = ap.parse_args()
@@ -587,6 +669,10 @@ def main():
         if args.t_end == 0.5:
             args.t_end = T_END
         return run_accuracy(args)
+    if args.workload == "controllers":
+        if args.t_end == 0.5:
+            args.t_end = 5.0
+        return run_controllers(args)
     return run_gpu(args)
 
 

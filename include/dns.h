@@ -194,7 +194,8 @@ DNS_API dns_status dns_trace(dns_ctx* ctx, double* out, long long cap, long long
  * DNS_CTRL_PI: after an accepted step h_new = h min(2, max(0.01, 0.8 err^-0.14 err_prev^0.08))
  * (the PI controller the paper names as future work, Section 4, with exponents 0.7/(q+1),
  * 0.4/(q+1)).  DNS_CTRL_MLP: after an accepted step, once 4 accepted steps are known, a
- * learned proposal h_new = h exp(clamp(y, log 0.01, log 2)) from the network below (capped at
+ * learned correction of the Section 2.2.1 factor, h_new = h min(2, max(0.01,
+ * 0.8 err^(-1/5) exp(clamp(y, -log 1.5, log 1.5)))) with y from the network below (capped at
  * 1 right after a rejection).  In every variant the embedded error norm still accepts or
  * rejects each step, and rejections (and non-finite proposals) use the Section 2.2.1 factor.
  * mlp_params_dev: DNS_MLP_PARAMS floats on the device (copied in), for DNS_CTRL_MLP only. */
@@ -203,7 +204,7 @@ DNS_API dns_status dns_set_controller(dns_ctx* ctx, int kind, const float* mlp_p
 
 /* The learned proposal's network (not in the paper): inputs 16 features of the 4 newest
  * accepted steps (newest first, each [log10 err, log(h_i/h_0), rejections before it,
- * log(h_i/h_{i+1})]), output log(h_next/h).  Parameters (float): W1[64][16], b1[64],
+ * log(h_i/h_{i+1})]), output y, the log of the correction to the Section 2.2.1 factor.  Parameters (float): W1[64][16], b1[64],
  * W2[64][64], b2[64], w3[64], b3; y = w3.relu(W2 relu(W1 x + b1) + b2) + b3, evaluated with the
  * weights rounded to bfloat16 and FP32 arithmetic.  All pointers are device pointers;
  * asynchronous on `stream`.

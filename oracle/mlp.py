@@ -3,9 +3,10 @@
 TEST INFRASTRUCTURE ONLY (see the package docstring).  The paper's step-size controller is
 the elementary one of Section 2.2.1 and it names better controllers as future work
 (Section 4); this module is the reference for the learned variant built on top of it.  The
-network proposes log(h_next / h) from the recent accepted-step history; the embedded error
-estimate still accepts or rejects every step and the Section 2.2.1 controller is the
-fallback.
+network proposes a bounded correction of the Section 2.2.1 factor from the recent
+accepted-step history: h_next = h min(2, max(0.01, 0.8 err^(-1/5) exp(clamp(y, +-log 1.5)))).
+An uncertain network (y near 0) behaves like that controller; the embedded error estimate
+still accepts or rejects every step and the Section 2.2.1 controller is the fallback.
 
 Parameter vector (float, length N_PARAMS), in this order:
   W1[64][16], b1[64], W2[64][64], b2[64], w3[64], b3[1]
@@ -15,9 +16,10 @@ Loss:     L = mean_b (y_b - t_b)^2
 Features of the history (4 most recent accepted steps, newest first, i = 0..3), each
   [log10 err_i, log(h_i / h_0), rejections just before step i, log(h_i / h_{i+1})]
 with h_0 the newest accepted step (the last feature of i = 3 uses the step before it, or 0).
-Target for training at accepted step n: log(h*_n / h_n), h*_n = h_{n+1} (0.8^5/err_{n+1})^(1/5)
-with n+1 the next accepted step -- the step that, in hindsight, would have produced the
-error 0.8^5 that the Section 2.2.1 controller aims for.
+Target for training at accepted step n: log(h*_n / h_n) - log(0.8 err_n^(-1/5)), with
+h*_n = h_{n+1} (0.8^5/err_{n+1})^(1/5) and n+1 the next accepted step -- the step that, in
+hindsight, would have produced the error 0.8^5 that the Section 2.2.1 controller aims for,
+relative to what that controller proposed.
 """
 from __future__ import annotations
 
@@ -28,6 +30,7 @@ import numpy as np
 NIN, NH, NOUT = 16, 64, 1
 N_PARAMS = NH * NIN + NH + NH * NH + NH + NH + 1
 LOG_DMIN, LOG_DMAX = math.log(0.01), math.log(2.0)
+LOG_CORR = math.log(1.5)      # bound of the learned correction
 
 
 def unpack(p):
@@ -117,18 +120,22 @@ def dataset_from_history(steps):
     for n in range(3, len(acc) - 1):
         hist = [acc[n - i] for i in range(min(5, n + 1))]
         err1, h1, _ = acc[n + 1]
-        if not (err1 > 0 and math.isfinite(err1)):
+        errn = acc[n][0]
+        if not (err1 > 0 and math.isfinite(err1) and errn > 0):
             continue
         hstar = h1 * (0.8 ** 5 / err1) ** 0.2
         X.append(features(hist))
-        T.append(math.log(hstar / acc[n][1]))
+        T.append(math.log(hstar / acc[n][1]) - math.log(0.8 * errn ** -0.2))
     return np.array(X).reshape(-1, NIN), np.array(T)
 
 
 def propose_factor(p, hist):
-    """Step factor exp(clamp(y)) proposed by the network (parameters rounded to bf16)."""
+    """Step factor fac_I exp(clamp(y, +-log 1.5)) clamped to [dmin, dmax] (weights rounded to
+    bf16); hist[0] is the step just accepted.  None if y is not finite."""
     y, _ = forward(round_bf16(p), features(hist)[None, :])
     y = float(y[0])
-    if not math.isfinite(y):
+    err = hist[0][0]
+    if not math.isfinite(y) or not err > 0:
         return None
-    return math.exp(min(LOG_DMAX, max(LOG_DMIN, y)))
+    lf = math.log(0.8) - 0.2 * math.log(err) + min(LOG_CORR, max(-LOG_CORR, y))
+    return math.exp(min(LOG_DMAX, max(LOG_DMIN, lf)))

@@ -138,8 +138,9 @@ __global__ void k_begin_attempt(DnsCtrl* c, int method) {
 // Section 2.2.1: err = max_j sqrt(S_j / (nx ny (nz/2+1))); accept iff err <= 1;
 // h_new = h min(dmax, max(dmin, 0.8 err^(-1/5))), dmax = 1 right after a rejection.
 // Variants after an accepted step: PI (0.8 err^(-0.7/5) err_prev^(0.4/5)) or the learned
-// proposal exp(clamp(mlp(features))) once 4 accepted steps are known; after a rejection and
-// when the proposal is not finite the Section 2.2.1 factor is used.
+// correction 0.8 err^(-1/5) exp(clamp(mlp(features), +-log 1.5)) once 4 accepted steps are
+// known; after a rejection and when the proposal is not finite the Section 2.2.1 factor is
+// used.
 __global__ void __launch_bounds__(kRedThreads) k_controller(DnsCtrl* c, const double* partials,
                                                             int method, int nstages, int nblk,
                                                             double nmodes, int nc) {
@@ -226,8 +227,10 @@ __global__ void __launch_bounds__(kRedThreads) k_controller(DnsCtrl* c, const do
   const double err = s_err;
   const bool accept = s_accept != 0;
   double fac = s_fac;
-  if (use_mlp && isfinite(y)) {
-    const double lf = fmin(log(2.0), fmax(log(0.01), (double)y));
+  if (use_mlp && isfinite(y) && err > 0.0) {
+    // learned correction of the Section 2.2.1 factor, bounded by 1.5x either way
+    const double corr = fmin(log(1.5), fmax(-log(1.5), (double)y));
+    const double lf = fmin(log(2.0), fmax(log(0.01), log(0.8) - 0.2 * log(err) + corr));
     fac = exp(lf);
     if (c->after_reject) fac = fmin(1.0, fac);
   }

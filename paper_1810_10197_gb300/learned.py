@@ -6,8 +6,9 @@ and the network is trained on the GPU by the library's own kernels (dns_mlp_trai
 
 Features at accepted step n (newest first, i = 0..3, h_0 = h_n):
     [log10 err_i, log(h_i / h_0), rejections just before step i, log(h_i / h_{i+1})]
-Target: log(h*_n / h_n) with h*_n = h_{n+1} (0.8^5 / err_{n+1})^(1/5), n+1 the next accepted
-step: the step that in hindsight gives the error 0.8^5 the controller aims for.
+Target: log(h*_n / h_n) - log(0.8 err_n^(-1/5)) with h*_n = h_{n+1} (0.8^5 / err_{n+1})^(1/5),
+n+1 the next accepted step: the step that in hindsight gives the error 0.8^5 the controller
+aims for, relative to the Section 2.2.1 proposal (the network learns a bounded correction).
 """
 from __future__ import annotations
 
@@ -41,11 +42,12 @@ def pairs_from_trace(trace: np.ndarray):
     X, T = [], []
     for n in range(3, len(acc) - 1):
         err1, h1, _ = acc[n + 1]
-        if not (err1 > 0 and math.isfinite(err1)):
+        errn = acc[n][0]
+        if not (err1 > 0 and math.isfinite(err1) and errn > 0):
             continue
         hist = [acc[n - i] for i in range(min(5, n + 1))]
         X.append(_features(hist))
-        T.append(math.log(h1 * (0.8 ** 5 / err1) ** 0.2 / acc[n][1]))
+        T.append(math.log(h1 * (0.8 ** 5 / err1) ** 0.2 / acc[n][1]) - math.log(0.8 * errn ** -0.2))
     return np.asarray(X, dtype=np.float32).reshape(-1, 16), np.asarray(T, dtype=np.float32)
 
 
@@ -73,3 +75,18 @@ def train(X: np.ndarray, T: np.ndarray, steps=3000, batch=128, lr=2e-3, seed=0):
         raise _dns.DnsError(st, "dns_mlp_train")
     torch.cuda.synchronize()
     return p, hist.cpu().numpy()
+
+
+def training_set(flows, make_dns, to_dev):
+    """Pairs from runs of the Section 2.2.1 controller: flows = [(shape, uhat, nu, forcing, tol, T)]."""
+    Xs, Ts = [], []
+    for (shape, uh, nu, forcing, tol, T) in flows:
+        d = make_dns(shape, nu, forcing)
+        d.set_state(to_dev(uh), 0.0)
+        d.set_trace(20000)
+        d.integrate(T, "BS5_ADAPTIVE", tol, tol, h0=1e-3)
+        X, Tt = pairs_from_trace(d.trace())
+        Xs.append(X)
+        Ts.append(Tt)
+        d.close()
+    return np.concatenate(Xs), np.concatenate(Ts)

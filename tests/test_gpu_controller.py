@@ -125,28 +125,18 @@ def test_trace_diagnostics_match_oracle():
 
 def trajectories(flows):
     from paper_1810_10197_gb300 import Dns, learned
-    Xs, Ts = [], []
-    for (shape, uh, nu, forcing, tol, T) in flows:
-        d = Dns(*shape, nu=nu, forcing=forcing)
-        d.set_state(to_dev(uh), 0.0)
-        d.set_trace(4000)
-        d.integrate(T, "BS5_ADAPTIVE", tol, tol, h0=1e-3)
-        X, Tt = learned.pairs_from_trace(d.trace())
-        Xs.append(X)
-        Ts.append(Tt)
-        d.close()
-    return np.concatenate(Xs), np.concatenate(Ts)
+    return learned.training_set(flows, lambda shape, nu, forcing: Dns(*shape, nu=nu, forcing=forcing), to_dev)
 
 
 def test_learned_controller_gain_on_rayleigh_taylor():
     """Train on TG and forced-HIT trajectories, apply to a Rayleigh-Taylor run (held out)."""
     from paper_1810_10197_gb300 import Dns, learned
-    n = 32
     flows = []
     for tol in (1e-5, 1e-6, 1e-7, 1e-8):
-        flows.append(((n, n, n), syn.taylor_green_3d_hat(n, n, n), 0.01, None, tol, 2.0))
-        flows.append(((n, n, n), syn.random_solenoidal_hat(n, n, n, seed=3, k0=3.0), 0.01, (2.5, 0.05),
-                      tol, 1.0))
+        for n, nu in ((32, 0.01), (32, 0.005)):
+            flows.append(((n, n, n), syn.taylor_green_3d_hat(n, n, n), nu, None, tol, 2.0))
+            flows.append(((n, n, n), syn.random_solenoidal_hat(n, n, n, seed=3, k0=3.0), nu, (2.5, 0.05),
+                          tol, 1.0))
     X, T = trajectories(flows)
     assert len(X) > 100
     params, hist = learned.train(X, T, steps=3000, lr=2e-3, seed=0)

@@ -60,8 +60,9 @@ def test_dataset_targets_are_hindsight_steps():
              (0.3, 0.12, 0.4, True), (0.42, 0.15, 0.32768, True)]
     X, T = mlp.dataset_from_history(steps)
     assert X.shape == (1, 16)
-    # n = 3 (4th accepted: h=0.12), next accepted h=0.15 with err = 0.8^5 -> h* = 0.15
-    assert abs(T[0] - math.log(0.15 / 0.12)) < 1e-12
+    # n = 3 (4th accepted: h=0.12, err 0.4), next accepted h=0.15 with err = 0.8^5 -> h* = 0.15;
+    # the Section 2.2.1 factor at n is 0.8 * 0.4^(-1/5)
+    assert abs(T[0] - (math.log(0.15 / 0.12) - math.log(0.8 * 0.4 ** -0.2))) < 1e-12
     # features: newest accepted err 0.4 with 1 rejection before it
     assert abs(X[0, 0] - math.log10(0.4)) < 1e-12 and X[0, 2] == 1.0 and X[0, 1] == 0.0
 
@@ -72,3 +73,14 @@ def test_pi_factor_hand_worked():
     for err, errp, after, fac in rows:
         got = rk.pi_factor(float(err), float(errp), bool(int(after)))
         assert abs(got - float(fac)) < 1e-13, (err, errp, after, got, fac)
+
+
+def test_learned_proposal_is_a_bounded_correction_of_the_i_controller():
+    hist = [(0.1, 0.05, 0), (0.2, 0.04, 1), (0.3, 0.04, 0), (0.3, 0.03, 0)]
+    fac_i = 0.8 * 0.1 ** -0.2
+    p = np.zeros(mlp.N_PARAMS)
+    assert abs(mlp.propose_factor(p, hist) - fac_i) < 1e-12            # y = 0: plain controller
+    p[-1] = 10.0                                                       # y clamped to log 1.5
+    assert abs(mlp.propose_factor(p, hist) - min(2.0, 1.5 * fac_i)) < 1e-12
+    p[-1] = -10.0
+    assert abs(mlp.propose_factor(p, hist) - fac_i / 1.5) < 1e-12
