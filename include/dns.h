@@ -30,8 +30,8 @@
  *     stream).  Calls documented as "synchronous" wait for that stream before returning.
  *   - A context is not thread-safe: use one context per host thread.
  *
- * Supported sizes: nx, ny in {8,12,16,24,32,48,64,96,128,256,512};
- *                  nz in {8,12,16,24,32,48,64,96,128,256,512}.
+ * Supported transform sizes (2/3 rule: nx, ny, nz; 3/2 rule: 3nx/2, 3ny/2, 3nz/2):
+ *   {8,12,16,24,32,48,64,96,128,192,256,384,512,768}.
  */
 #ifndef DNS_H
 #define DNS_H
@@ -90,6 +90,11 @@ typedef struct {
     double nu;                   /* kinematic viscosity, 1/Re                                 */
     int precision;               /* dns_precision                                             */
     dns_forcing forcing;
+    int dealias;                 /* 0: 2/3 truncation rule (default); 1: 3/2 padding rule of
+                                    Section 2.1.1 -- the state holds N frequencies per axis
+                                    (nx ny nz = N, each a multiple of 4, 3N/2 supported),
+                                    products are formed on the (3N/2)^3 grid, the result keeps
+                                    |m| <= N/2 - 1 and the Nyquist modes are zero. */
 } dns_config;
 
 /* Outcome of the last attempt and running counters since the last dns_set_state. */

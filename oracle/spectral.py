@@ -160,3 +160,42 @@ def rhs_boussinesq(grid: Grid, uhat: np.ndarray, rhohat: np.ndarray, nu: float, 
     kx, ky, kz = grid.kvec()
     frho = -1j * (kx * flux[0] + ky * flux[1] + kz * flux[2]) - kappa * grid.k2 * rh
     return fu, grid.dealias(frho)
+
+
+def rhs_pad32(grid: Grid, uhat: np.ndarray, nu: float) -> np.ndarray:
+    """Eq. (ufdef) with the 3/2 padding rule of Section 2.1.1.
+
+    The state has N frequencies per axis; u and omega are zero-padded to 3N/2 frequencies,
+    transformed to the (3N/2)^3 grid, u x omega is formed there and transformed back, and
+    the highest frequencies are truncated to leave N per axis.  The Nyquist modes (which the
+    paper's footnote reports as a source of spurious imaginary parts) are kept at zero, so
+    the state has |m| <= N/2 - 1.  Normalisation stays that of the N-grid DFT.
+    """
+    nx, ny, nz = grid.shape
+    P = (3 * nx // 2, 3 * ny // 2, 3 * nz // 2)
+    keep = (np.abs(grid.mx) < nx / 2) & (np.abs(grid.my) < ny / 2) & (grid.mz < nz / 2)
+    y = uhat * keep
+
+    def pad(a):
+        out = np.zeros(a.shape[:-3] + (P[0], P[1], P[2] // 2 + 1), dtype=complex)
+        ix = np.concatenate([np.arange(nx // 2), np.arange(P[0] - nx // 2, P[0])])
+        iy = np.concatenate([np.arange(ny // 2), np.arange(P[1] - ny // 2, P[1])])
+        src_x = np.concatenate([np.arange(nx // 2), np.arange(nx - nx // 2, nx)])
+        src_y = np.concatenate([np.arange(ny // 2), np.arange(ny - ny // 2, ny)])
+        out[..., ix[:, None], iy[None, :], :nz // 2 + 1] = a[..., src_x[:, None], src_y[None, :], :]
+        return out
+
+    def unpad(a):
+        ix = np.concatenate([np.arange(nx // 2), np.arange(P[0] - nx // 2, P[0])])
+        iy = np.concatenate([np.arange(ny // 2), np.arange(P[1] - ny // 2, P[1])])
+        src_x = np.concatenate([np.arange(nx // 2), np.arange(nx - nx // 2, nx)])
+        src_y = np.concatenate([np.arange(ny // 2), np.arange(ny - ny // 2, ny)])
+        out = np.zeros(a.shape[:-3] + (nx, ny, nz // 2 + 1), dtype=complex)
+        out[..., src_x[:, None], src_y[None, :], :] = a[..., ix[:, None], iy[None, :], :nz // 2 + 1]
+        return out
+
+    r = (P[0] * P[1] * P[2]) / float(nx * ny * nz)
+    u = np.fft.irfftn(pad(y), s=P, axes=(-3, -2, -1)) * r
+    w = np.fft.irfftn(pad(curl_hat(grid, y)), s=P, axes=(-3, -2, -1)) * r
+    nl = unpad(np.fft.rfftn(cross(u, w), axes=(-3, -2, -1))) / r * keep
+    return (leray(grid, nl) - nu * grid.k2 * y) * keep

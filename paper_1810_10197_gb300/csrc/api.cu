@@ -71,8 +71,8 @@ double frac_val(Frac a) { return (double)a.p / (double)a.q; }
 
 bool supported(int n) {
   switch (n) {
-    case 8: case 12: case 16: case 24: case 32: case 48: case 64: case 96: case 128: case 256:
-    case 512: return true;
+    case 8: case 12: case 16: case 24: case 32: case 48: case 64: case 96: case 128: case 192:
+    case 256: case 384: case 512: case 768: return true;
   }
   return false;
 }
@@ -344,7 +344,7 @@ dns_status status_from_ctrl(dns_ctx* c) {
 
 dns_status ensure_stage(dns_ctx* c) {
   if (c->full_stage) return DNS_OK;
-  const size_t bytes = (size_t)c->g.nc * c->g.nx * c->g.ny * c->g.nzh * sizeof(double2);
+  const size_t bytes = (size_t)c->g.nc * c->g.snx * c->g.sny * c->g.snzh * sizeof(double2);
   return alloc(c, (void**)&c->full_stage, bytes);
 }
 
@@ -373,7 +373,11 @@ dns_status dns_create_boussinesq(const dns_config* cfg, double kappa, double ri,
 static dns_status create_impl(const dns_config* cfg, int bouss, double kappa, double ri, dns_ctx** out) {
   if (!cfg || !out) return DNS_ERR_ARG;
   *out = nullptr;
-  if (!supported(cfg->nx) || !supported(cfg->ny) || !supported(cfg->nz)) return DNS_ERR_UNSUPPORTED;
+  if (cfg->dealias != 0 && cfg->dealias != 1) return DNS_ERR_ARG;
+  const bool pad = cfg->dealias == 1;
+  // 3/2 rule: the state has N frequencies per axis, the transforms run on 3N/2 points
+  auto phys = [&](int n) { return pad ? ((n % 4 == 0) ? 3 * n / 2 : -1) : n; };
+  if (!supported(phys(cfg->nx)) || !supported(phys(cfg->ny)) || !supported(phys(cfg->nz))) return DNS_ERR_UNSUPPORTED;
   if (cfg->precision != DNS_FP64 && cfg->precision != DNS_FP32_MIXED) return DNS_ERR_ARG;
   if (!(cfg->nu >= 0.0) || !std::isfinite(cfg->nu)) return DNS_ERR_ARG;
   if (cfg->forcing.kind != 0 && cfg->forcing.kind != 1) return DNS_ERR_ARG;
@@ -385,7 +389,8 @@ static dns_status create_impl(const dns_config* cfg, int bouss, double kappa, do
   c->forcing = cfg->forcing;
   cudaGetDevice(&c->device);
   Geom& g = c->g;
-  g.nx = cfg->nx; g.ny = cfg->ny; g.nz = cfg->nz; g.nzh = cfg->nz / 2 + 1;
+  g.nx = phys(cfg->nx); g.ny = phys(cfg->ny); g.nz = phys(cfg->nz); g.nzh = g.nz / 2 + 1;
+  g.snx = cfg->nx; g.sny = cfg->ny; g.snz = cfg->nz; g.snzh = cfg->nz / 2 + 1;
   g.Kx = (g.nx - 1) / 3; g.Ky = (g.ny - 1) / 3; g.Kz = (g.nz - 1) / 3;
   g.Mx = 2 * g.Kx + 1; g.My = 2 * g.Ky + 1; g.Mz = g.Kz + 1;
   g.MyMz = g.My * g.Mz;
@@ -396,8 +401,9 @@ static dns_status create_impl(const dns_config* cfg, int bouss, double kappa, do
   g.sx = cfg->lx > 0 ? twopi / lx : 1.0;
   g.sy = cfg->ly > 0 ? twopi / ly : 1.0;
   g.sz = cfg->lz > 0 ? twopi / lz : 1.0;
-  g.inv_n3 = 1.0 / ((double)g.nx * g.ny * g.nz);
-  g.nmodes_half = (double)g.nx * g.ny * g.nzh;
+  g.inv_n3 = 1.0 / ((double)g.snx * g.sny * g.snz);
+  g.nmodes_half = (double)g.snx * g.sny * g.snzh;
+  g.fwd_scale = ((double)g.snx * g.sny * g.snz) / ((double)g.nx * g.ny * g.nz);
   g.nc = bouss ? 4 : 3;
   g.bouss = bouss;
 
@@ -484,7 +490,7 @@ dns_status dns_set_state(dns_ctx* c, const void* uhat, int where, double t) {
   const double2* src = reinterpret_cast<const double2*>(uhat);
   if (where == 1) {
     if ((s = ensure_stage(c)) != DNS_OK) return s;
-    const size_t bytes = (size_t)c->g.nc * c->g.nx * c->g.ny * c->g.nzh * sizeof(double2);
+    const size_t bytes = (size_t)c->g.nc * c->g.snx * c->g.sny * c->g.snzh * sizeof(double2);
     CK(cudaMemcpyAsync(c->full_stage, uhat, bytes, cudaMemcpyHostToDevice, c->stream), "state upload");
     src = c->full_stage;
   }
@@ -500,7 +506,7 @@ dns_status dns_get_state(dns_ctx* c, void* uhat, int where) {
   if (s != DNS_OK) return s;
   if (!uhat || (where != 0 && where != 1)) return fail(c, DNS_ERR_ARG, "dns_get_state: bad argument");
   if (!c->has_state) return fail(c, DNS_ERR_STATE, "no state set");
-  const size_t bytes = (size_t)c->g.nc * c->g.nx * c->g.ny * c->g.nzh * sizeof(double2);
+  const size_t bytes = (size_t)c->g.nc * c->g.snx * c->g.sny * c->g.snzh * sizeof(double2);
   double2* dst = reinterpret_cast<double2*>(uhat);
   if (where == 1) {
     if ((s = ensure_stage(c)) != DNS_OK) return s;
@@ -520,7 +526,7 @@ dns_status dns_rhs(dns_ctx* c, const void* uhat_dev, void* f_dev) {
   dns_status s = check_ctx(c);
   if (s != DNS_OK) return s;
   if (!uhat_dev || !f_dev || uhat_dev == f_dev) return fail(c, DNS_ERR_ARG, "dns_rhs: bad pointers");
-  const size_t bytes = (size_t)c->g.nc * c->g.nx * c->g.ny * c->g.nzh * sizeof(double2);
+  const size_t bytes = (size_t)c->g.nc * c->g.snx * c->g.sny * c->g.snzh * sizeof(double2);
   CK(launch_gather(c->g, reinterpret_cast<const double2*>(uhat_dev), c->rhs_in, c->stream), "gather");
   if ((s = enqueue_rhs(c, c->ctrl_rhs, SLOT_Y, SLOT_K1, 0)) != DNS_OK) return s;
   CK(cudaMemsetAsync(f_dev, 0, bytes, c->stream), "memset");
@@ -664,7 +670,7 @@ dns_status dns_spectrum(dns_ctx* c, double* out, int cap, int* nshells) {
   // scratch: the error-norm partials buffer is too small; use the staging buffer of host copies
   if ((s = ensure_stage(c)) != DNS_OK) return s;
   const size_t need = (size_t)(152 + 1) * ns * sizeof(double);
-  const size_t have = (size_t)g.nc * g.nx * g.ny * g.nzh * sizeof(double2);
+  const size_t have = (size_t)g.nc * g.snx * g.sny * g.snzh * sizeof(double2);
   if (need > have) return fail(c, DNS_ERR_UNSUPPORTED, "spectrum scratch too small");
   dev = reinterpret_cast<double*>(c->full_stage);
   CK(launch_spectrum(g, c->uu[c->host_ctrl->parity], dev + ns, ns, dev, c->stream), "spectrum");

@@ -71,10 +71,14 @@ struct Geom {
   int MyMz;
   long long M;          // Mx*My*Mz
   double sx, sy, sz;    // 2 pi / L per axis
-  double inv_n3;        // 1 / (nx ny nz)
-  double nmodes_half;   // nx ny (nz/2+1), divisor of the error norm
+  double inv_n3;        // 1 / (snx sny snz), the state grid's inverse-DFT normalisation
+  double nmodes_half;   // snx sny (snz/2+1), divisor of the error norm
   int nc;               // state components: 3 (velocity) or 4 (velocity, density)
   int bouss;            // Boussinesq form (Section 3.2)
+  // state grid (the caller's half-spectrum layout).  Equal to the transform grid nx, ny, nz
+  // for the 2/3 rule; N with a transform grid of 3N/2 for the 3/2 padding rule.
+  int snx, sny, snz, snzh;
+  double fwd_scale;     // (snx sny snz) / (nx ny nz): forward transforms on the padded grid
 };
 
 __host__ __device__ __forceinline__ int signed_mode(int i, int K, int Mc) { return i <= K ? i : i - Mc; }

@@ -28,8 +28,11 @@ __host__ __device__ constexpr int plan_radix(int n, int s) {
     case 64: return s < 2 ? 8 : 1;
     case 96: return s == 0 ? 8 : (s == 1 ? 4 : 3);
     case 128: return s == 0 ? 16 : (s == 1 ? 8 : 1);
+    case 192: return s == 0 ? 16 : (s == 1 ? 4 : 3);
     case 256: return s < 2 ? 16 : 1;
+    case 384: return s == 0 ? 16 : (s == 1 ? 8 : 3);
     case 512: return 8;
+    case 768: return s < 2 ? 16 : 3;
   }
   return 0;
 }
@@ -39,8 +42,9 @@ __host__ __device__ constexpr int plan_threads(int n) {
     case 6: return 3;
     case 12: case 16: return 4;
     case 24: case 32: case 64: case 128: return 8;
-    case 48: case 96: case 256: return 16;
-    case 512: return 32;
+    case 48: case 96: case 192: case 256: return 16;
+    case 384: case 512: return 32;
+    case 768: return 64;
   }
   return 0;
 }

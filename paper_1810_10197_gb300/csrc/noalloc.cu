@@ -99,6 +99,8 @@ extern "C" dns_status dns_rhs_noalloc(int nx, int ny, int nz, double nu, const v
   g.nmodes_half = (double)nx * ny * g.nzh;
   g.nc = 3;
   g.bouss = 0;
+  g.snx = nx; g.sny = ny; g.snz = nz; g.snzh = g.nzh;
+  g.fwd_scale = 1.0;
   DnsCtrl* ctrl = reinterpret_cast<DnsCtrl*>(base + kOffCtrl);
 
   k_na_setup<<<1, 64, 0, s>>>(base, nx, ny, nz);

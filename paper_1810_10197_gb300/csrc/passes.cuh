@@ -434,11 +434,13 @@ k_p5(const PassArgs a) {
   }
   __syncthreads();
   const T kf2 = (T)a.kf2;
+  const T fsc = (T)g.fwd_scale;
   for (int i = tid; i < g.Mx * TC; i += nth) {
     const int ix = i / TC, c = i - ix * TC, col = col0 + c;
     if (col >= g.MyMz) continue;
     const int pos = pidx<V>(ix <= g.Kx ? ix : NX - g.Mx + ix);
     V n0 = lines[(0 * TC + c) * LD + pos], n1 = lines[(1 * TC + c) * LD + pos], n2 = lines[(2 * TC + c) * LD + pos];
+    if (fsc != (T)1) { n0 = cscale(n0, fsc); n1 = cscale(n1, fsc); n2 = cscale(n2, fsc); }
     const T kx = sx * (T)signed_mode(ix, g.Kx, g.Mx);
     const T ky = colk[2 * c], kzz = colk[2 * c + 1];
     const T k2 = kx * kx + ky * ky + kzz * kzz;
@@ -468,7 +470,8 @@ k_p5(const PassArgs a) {
     K[off + 2 * g.M] = make_double2(fma(vis, y2.x, to_f64(n2.x)), fma(vis, y2.y, to_f64(n2.y)));
     if constexpr (BOUSS) {
       const V f0 = lines[(3 * TC + c) * LD + pos], f1 = lines[(4 * TC + c) * LD + pos], f2 = lines[(5 * TC + c) * LD + pos];
-      const V kd = mk<V>(kx * f0.x + ky * f1.x + kzz * f2.x, kx * f0.y + ky * f1.y + kzz * f2.y);
+      V kd = mk<V>(kx * f0.x + ky * f1.x + kzz * f2.x, kx * f0.y + ky * f1.y + kzz * f2.y);
+      if (fsc != (T)1) kd = cscale(kd, fsc);
       const double visr = -a.kappa_d * k2d;
       // -i (kappa . F) = (Im, -Re)
       K[off + 3 * g.M] = make_double2(fma(visr, rho.x, to_f64(kd.y)), fma(visr, rho.y, -to_f64(kd.x)));

@@ -73,8 +73,8 @@ static cudaError_t launch_p3(const PassArgs& a, cudaStream_t s) {
   return a.var_p3 ? launch_p3_v<T, MZ, B, 1>(a, s) : launch_p3_v<T, MZ, B, 0>(a, s);
 }
 
-#define DNS_XY_SIZES(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(256) X(512)
-#define DNS_ZH_SIZES(X) X(4) X(6) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(128) X(256)
+#define DNS_XY_SIZES(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768)
+#define DNS_ZH_SIZES(X) X(4) X(6) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384)
 
 template <typename T>
 cudaError_t launch_pass(int which, const PassArgs& a, cudaStream_t s) {

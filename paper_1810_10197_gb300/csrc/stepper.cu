@@ -363,9 +363,9 @@ __global__ void k_gather(const Geom g, const double2* __restrict__ full, double2
     const long long q = i / g.M, r = i - q * g.M;
     const int ix = (int)(r / g.MyMz), rem = (int)(r - (long long)ix * g.MyMz);
     const int jy = rem / g.Mz, kz = rem - jy * g.Mz;
-    const int fx = ix <= g.Kx ? ix : g.nx - g.Mx + ix;
-    const int fy = jy <= g.Ky ? jy : g.ny - g.My + jy;
-    cmp[i] = full[((q * g.nx + fx) * g.ny + fy) * (long long)g.nzh + kz];
+    const int fx = ix <= g.Kx ? ix : g.snx - g.Mx + ix;
+    const int fy = jy <= g.Ky ? jy : g.sny - g.My + jy;
+    cmp[i] = full[((q * g.snx + fx) * g.sny + fy) * (long long)g.snzh + kz];
   }
 }
 
@@ -376,9 +376,9 @@ __global__ void k_scatter(const Geom g, const double2* __restrict__ cmp, double2
     const long long q = i / g.M, r = i - q * g.M;
     const int ix = (int)(r / g.MyMz), rem = (int)(r - (long long)ix * g.MyMz);
     const int jy = rem / g.Mz, kz = rem - jy * g.Mz;
-    const int fx = ix <= g.Kx ? ix : g.nx - g.Mx + ix;
-    const int fy = jy <= g.Ky ? jy : g.ny - g.My + jy;
-    full[((q * g.nx + fx) * g.ny + fy) * (long long)g.nzh + kz] = cmp[i];
+    const int fx = ix <= g.Kx ? ix : g.snx - g.Mx + ix;
+    const int fy = jy <= g.Ky ? jy : g.sny - g.My + jy;
+    full[((q * g.snx + fx) * g.sny + fy) * (long long)g.snzh + kz] = cmp[i];
   }
 }
 

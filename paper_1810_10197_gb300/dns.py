@@ -25,7 +25,7 @@ DNS_RK4, DNS_BS5_FIXED, DNS_BS5_ADAPTIVE, DNS_DP5_FIXED, DNS_DP5_ADAPTIVE = 0, 1
 METHODS = {"RK4": DNS_RK4, "BS5_FIXED": DNS_BS5_FIXED, "BS5_ADAPTIVE": DNS_BS5_ADAPTIVE,
            "DP5_FIXED": DNS_DP5_FIXED, "DP5_ADAPTIVE": DNS_DP5_ADAPTIVE}
 DNS_FP64, DNS_FP32_MIXED = 0, 1
-SUPPORTED_N = (8, 12, 16, 24, 32, 48, 64, 96, 128, 256, 512)
+SUPPORTED_N = (8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768)
 
 
 class dns_forcing(C.Structure):
@@ -35,7 +35,8 @@ class dns_forcing(C.Structure):
 class dns_config(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("lx", C.c_double), ("ly", C.c_double), ("lz", C.c_double),
-                ("nu", C.c_double), ("precision", C.c_int), ("forcing", dns_forcing)]
+                ("nu", C.c_double), ("precision", C.c_int), ("forcing", dns_forcing),
+                ("dealias", C.c_int)]
 
 
 class dns_step_info(C.Structure):
@@ -174,8 +175,9 @@ class Dns:
     """One libdns context (an nx x ny x nz grid on the current CUDA device)."""
 
     def __init__(self, nx, ny=None, nz=None, nu=0.0, precision="fp64", forcing=None,
-                 lengths=None, stream=None, boussinesq=None):
-        """boussinesq=(kappa, ri) selects the Boussinesq form (state of 4 components)."""
+                 lengths=None, stream=None, boussinesq=None, dealias="2/3"):
+        """boussinesq=(kappa, ri) selects the Boussinesq form (state of 4 components);
+        dealias="3/2" selects the padding rule (state of nx x ny x nz frequencies)."""
         lib = load()
         ny = nx if ny is None else ny
         nz = nx if nz is None else nz
@@ -189,6 +191,7 @@ class Dns:
         if forcing is not None:
             cfg.forcing.kind = 1
             cfg.forcing.kf, cfg.forcing.power = float(forcing[0]), float(forcing[1])
+        cfg.dealias = {"2/3": 0, "3/2": 1}[dealias]
         h = C.c_void_p()
         if boussinesq is not None:
             st = lib.dns_create_boussinesq(C.byref(cfg), float(boussinesq[0]), float(boussinesq[1]),

@@ -57,4 +57,4 @@ def test_argument_checks_before_cuda(lib):
 
 def test_build_flags_target_sm_103a_only():
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
-    assert pkg.SUPPORTED_N == (8, 12, 16, 24, 32, 48, 64, 96, 128, 256, 512)
+    assert pkg.SUPPORTED_N == (8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768)

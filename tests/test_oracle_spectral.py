@@ -88,9 +88,9 @@ def test_curl_of_taylor_green_closed_form():
     assert np.max(np.abs(g.to_spectral(syn.taylor_green_3d(n, n, n)) - uh)) < 1e-12 * n ** 3
 
 
-def full_spectrum(g, uh):
+def full_spectrum(g, uh, cutoff=None):
     """Dict m -> coefficient vector over the retained box, expanded by Hermitian symmetry."""
-    Kx, Ky, Kz = g.cutoff
+    Kx, Ky, Kz = cutoff or g.cutoff
     out = {}
     for mx in range(-Kx, Kx + 1):
         for my in range(-Ky, Ky + 1):
@@ -102,7 +102,7 @@ def full_spectrum(g, uh):
     return out
 
 
-def brute_force_rhs(g, uh, nu):
+def brute_force_rhs(g, uh, nu, cutoff=None):
     """Eq. (ufdef) with the nonlinear term as an exact convolution over retained modes.
 
     u(x) = (1/N^3) sum_p uhat_p e^{i p.x}; the DFT of u x omega at a retained k is
@@ -110,7 +110,7 @@ def brute_force_rhs(g, uh, nu):
     """
     L = g.lengths
     scale = [2 * np.pi / l for l in L]
-    U = full_spectrum(g, uh)
+    U = full_spectrum(g, uh, cutoff)
     W = {m: 1j * np.cross(np.array(m) * scale, v) for m, v in U.items()}
     Kx, Ky, Kz = g.cutoff
     f = np.zeros_like(uh)
@@ -253,3 +253,17 @@ def test_boussinesq_rhs_equals_brute_force_convolution():
     ru, rr = brute_force_boussinesq(g, uh, rh, 0.01, 0.02, 0.7)
     assert np.max(np.abs(fu - ru)) <= 1e-12 * np.max(np.abs(ru))
     assert np.max(np.abs(fr - rr)) <= 1e-12 * np.max(np.abs(rr))
+
+
+
+@pytest.mark.parametrize("shape", [(8, 8, 8), (8, 12, 16)])
+def test_pad32_rhs_equals_brute_force_convolution(shape):
+    # the 3/2 padding rule keeps |m| <= N/2 - 1 and is alias-free: its result is the exact
+    # convolution over the state's modes, truncated to those modes
+    g = sp.Grid(*shape)
+    K = tuple(n // 2 - 1 for n in shape)
+    keep = (np.abs(g.mx) <= K[0]) & (np.abs(g.my) <= K[1]) & (g.mz <= K[2])
+    uh = syn.random_complex_hat(*shape, seed=17) * keep
+    f = sp.rhs_pad32(g, uh, 0.02)
+    ref = brute_force_rhs(g, uh, 0.02, cutoff=K)
+    assert np.max(np.abs(f - ref)) <= 1e-12 * np.max(np.abs(ref))
