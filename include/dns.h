@@ -77,7 +77,12 @@ typedef enum { DNS_FP64 = 0, DNS_FP32_MIXED = 1 } dns_precision;
 
 /* Forcing (Section 3.3.1 injects energy into 0 < |kappa| <= kf).  kind 0: none.  kind 1:
  * constant power as a right-hand-side term F_k = power/(2 E_f) uhat_k on 0 < |kappa| <= kf,
- * E_f the band energy, so that dE/dt gains exactly `power`. */
+ * E_f the band energy, so that dE/dt gains exactly `power`.  kind 2: the paper's own scheme,
+ * a rescale after every accepted step: the band 0 < |kappa| <= kf of the new state is
+ * multiplied by alpha = sqrt(1 + (E_n - E_{n+1}) / E_f), E_f the band energy of the new
+ * state, so that the total energy returns to its value before the step (`power` is unused;
+ * the right-hand side has no forcing term; a first-same-as-last pair re-evaluates k_1 after
+ * each rescale).  kf > 0 for kinds 1 and 2. */
 typedef struct {
     int kind;
     double kf;
@@ -252,6 +257,34 @@ DNS_API dns_status dns_integrate_batch(dns_batch* batch, int method, const doubl
  * tunes every instance.  dns_set_tiles sets the variants by hand.  Synchronous. */
 DNS_API dns_status dns_autotune(dns_ctx* ctx, int reps, int* variants);
 DNS_API dns_status dns_set_tiles(dns_ctx* ctx, int var_py, int var_p3);
+
+/* Checkpoint and resume (the paper restarts its turbulence runs from a spun-up state,
+ * Section 3.3.2).  dns_save writes the current state, the carried-over derivative k_1 of a
+ * first-same-as-last pair (when valid) and the controller's state (t, h, step history,
+ * counters, controller kind) to `path`; dns_load reads them into a context with the same
+ * state grid, dealiasing rule and component count.  The physical parameters (nu, forcing,
+ * precision, kappa, Ri) are the loading context's own, so a forced spin-up can be resumed
+ * as an unforced run.  A checkpoint taken with the learned controller needs
+ * dns_set_controller(ctx, DNS_CTRL_MLP, params) before dns_load (the network parameters are
+ * not stored).  Continuing a loaded context with h0 = 0 reproduces the uninterrupted run bit
+ * for bit.
+ *
+ * File layout, little-endian: "DNSCKPT1", u32 version (1), i32 nx ny nz dealias ncomp
+ * precision, f64 2pi/lx 2pi/ly 2pi/lz nu kappa Ri, i32 forcing kind, f64 kf power, f64 t h
+ * h_try err err_prev rtol atol errc[4], i32 method k1_valid after_reject accepted clipped
+ * controller hist_n rej_since hist_rej[5], f64 hist_err[5] hist_h[5], i64 n_rhs n_acc n_rej
+ * n_attempts rejects_in_row, i64 M (retained modes per component), complex128 state[ncomp][M]
+ * (retained box, kz fastest), complex128 k1[ncomp][M] when k1_valid, u32 CRC-32 of all
+ * preceding bytes.  Both calls synchronise the context's stream.  Errors: DNS_ERR_ARG for an
+ * unreadable, truncated or corrupt file or a mismatched grid (the context is left unchanged),
+ * DNS_ERR_STATE without a state (save) or for a learned-controller checkpoint without
+ * parameters (load). */
+DNS_API dns_status dns_save(dns_ctx* ctx, const char* path);
+DNS_API dns_status dns_load(dns_ctx* ctx, const char* path);
+
+/* CRC-32 of the checkpoint trailer (reflected polynomial 0xEDB88320, the checksum of zlib and
+ * PNG), continued from `crc` (0 to start).  Host-only; needs no GPU. */
+DNS_API unsigned int dns_crc32(const void* data, size_t n, unsigned int crc);
 
 /* Grid facts: retained cut-offs K[3] and the number of device bytes the context holds. */
 DNS_API dns_status dns_query(const dns_ctx* ctx, int* K3, size_t* device_bytes);

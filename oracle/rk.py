@@ -205,7 +205,8 @@ class Result:
 def integrate(f: Callable, u0: np.ndarray, t0: float, t_end: float, method: str, h0: float,
               rtol: float = 1e-6, atol: float = 1e-6, nmodes: Optional[int] = None,
               max_rejects: int = 30, max_steps: int = 10 ** 7,
-              on_accept: Optional[Callable] = None, controller="I") -> Result:
+              on_accept: Optional[Callable] = None, controller="I",
+              post_step: Optional[Callable] = None) -> Result:
     """Integrate u' = f(u) from t0 to t_end.
 
     method: "RK4" (fixed h0), "BS5_FIXED" (fixed h0, error logged), "BS5_ADAPTIVE",
@@ -213,6 +214,9 @@ def integrate(f: Callable, u0: np.ndarray, t0: float, t_end: float, method: str,
     controller (adaptive methods): "I" (Section 2.2.1), "PI", or ("MLP", params): after an
     accepted step the PI / network proposal replaces the factor; after a rejection, and for
     the first 4 accepted steps (MLP), the Section 2.2.1 factor is used.
+    post_step(u_old, u_new) -> u, if given, replaces the state after every accepted step (the
+    band rescale forcing of Section 3.3.1); when it returns a new array the derivative carried
+    over by a first-same-as-last pair no longer belongs to the state and k_1 is evaluated afresh.
     """
     from . import mlp as _mlp
     tabname, _, mode = method.partition("_")
@@ -260,8 +264,13 @@ def integrate(f: Callable, u0: np.ndarray, t0: float, t_end: float, method: str,
         res.history.append((t, h_step, err, accepted))
         if accepted:
             t = t_end if clipped else t + h_step
-            u = u_new
             k1 = ks[-1] if tab.fsal else None
+            if post_step is not None:
+                u_post = post_step(u, u_new)
+                if u_post is not u_new:      # a changed state needs a fresh k_1
+                    k1 = None
+                u_new = u_post
+            u = u_new
             after_reject = False
             rejects_in_row = 0
             rej_since = 0

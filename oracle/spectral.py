@@ -123,6 +123,27 @@ def forcing_hat(grid: Grid, uhat: np.ndarray, kf: float, power: float) -> np.nda
     return (power / (2.0 * ef)) * band * uhat
 
 
+def rescale_band(grid: Grid, u_old: np.ndarray, u_new: np.ndarray, kf: float) -> np.ndarray:
+    """The paper's deterministic forcing (Section 3.3.1), applied after an accepted step.
+
+    The modes 0 < |kappa| <= kf of the new state are multiplied by one factor alpha, chosen so
+    that the energy the step lost is put back: E(rescaled) = E(u_old).  With E_f the band
+    energy of u_new this gives alpha^2 = 1 + (E(u_old) - E(u_new)) / E_f.  Without band energy,
+    or when alpha^2 <= 0, the new state is returned unchanged.
+    """
+    def e(u):
+        return float(np.sum(grid.weight * grid.mask * np.abs(u) ** 2)) / (2.0 * grid.n3 ** 2)
+
+    ef = band_energy(grid, u_new, kf)
+    if not ef > 0.0:
+        return u_new
+    a2 = 1.0 + (e(u_old) - e(u_new)) / ef
+    if not a2 > 0.0:
+        return u_new
+    band = (grid.k2 > 0) & (grid.k2 <= kf * kf) & grid.mask
+    return np.where(band, np.sqrt(a2) * u_new, u_new)
+
+
 def rhs(grid: Grid, uhat: np.ndarray, nu: float, forcing=None) -> np.ndarray:
     """Right-hand side of Eq. (ufdef): f = P(kappa)[u x omega]^ - nu |kappa|^2 uhat (+ forcing).
 

@@ -3,6 +3,7 @@
 // hand sides, error norm, controller), all enqueued on the context's stream.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -247,6 +248,15 @@ dns_status enqueue_stage(dns_ctx* c, int nterms, const int* kslots, const double
   return DNS_OK;
 }
 
+// Forcing kind 2 (Section 3.3.1): after an accepted step the band 0 < |kappa| <= kf is
+// rescaled so that the step's energy loss is put back (decided on the device).
+dns_status enqueue_rescale(dns_ctx* c) {
+  if (c->forcing.kind != 2) return DNS_OK;
+  CK(timed(c, PR_FORCE, [&] { return launch_rescale(c->g, c->ctrl, c->partials, c->forcing.kf, c->stream); }),
+     "band rescale");
+  return DNS_OK;
+}
+
 // One attempted step (Section 2.2): all stages, error norm and the controller decision.
 dns_status enqueue_attempt(dns_ctx* c, int method) {
   dns_status st;
@@ -266,6 +276,7 @@ dns_status enqueue_attempt(dns_ctx* c, int method) {
     CK(timed(c, PR_CTRL, [&] {
          return launch_controller(c->ctrl, c->partials, 0, 4, c->g.nmodes_half, c->g.nc, c->stream);
        }), "controller");
+    if ((st = enqueue_rescale(c)) != DNS_OK) return st;
     if (c->trace_diag) CK(launch_trace_diag(c->g, c->ctrl, c->partials, 0, c->stream), "trace diagnostics");
     return DNS_OK;
   }
@@ -301,6 +312,7 @@ dns_status enqueue_attempt(dns_ctx* c, int method) {
   CK(timed(c, PR_CTRL, [&] {
        return launch_controller(c->ctrl, c->partials, method, S, c->g.nmodes_half, c->g.nc, c->stream);
      }), "controller");
+  if ((st = enqueue_rescale(c)) != DNS_OK) return st;
   if (c->trace_diag) CK(launch_trace_diag(c->g, c->ctrl, c->partials, method, c->stream), "trace diagnostics");
   return DNS_OK;
 }
@@ -380,7 +392,8 @@ static dns_status create_impl(const dns_config* cfg, int bouss, double kappa, do
   if (!supported(phys(cfg->nx)) || !supported(phys(cfg->ny)) || !supported(phys(cfg->nz))) return DNS_ERR_UNSUPPORTED;
   if (cfg->precision != DNS_FP64 && cfg->precision != DNS_FP32_MIXED) return DNS_ERR_ARG;
   if (!(cfg->nu >= 0.0) || !std::isfinite(cfg->nu)) return DNS_ERR_ARG;
-  if (cfg->forcing.kind != 0 && cfg->forcing.kind != 1) return DNS_ERR_ARG;
+  if (cfg->forcing.kind < 0 || cfg->forcing.kind > 2) return DNS_ERR_ARG;
+  if (cfg->forcing.kind != 0 && !(cfg->forcing.kf > 0.0 && std::isfinite(cfg->forcing.kf))) return DNS_ERR_ARG;
   dns_ctx* c = new dns_ctx();
   c->precision = cfg->precision;
   c->nu = cfg->nu;
@@ -716,6 +729,175 @@ dns_status dns_set_controller(dns_ctx* c, int kind, const float* mlp_params_dev)
                        c->stream), "copy network");
   }
   CK(launch_ctrl_set_controller(c->ctrl, kind, kind == 2 ? c->mlp_buf : nullptr, c->stream), "controller set");
+  return DNS_OK;
+}
+
+}  // extern "C"
+
+// ---- checkpoint and resume (dns_save / dns_load) ------------------------------------------
+#if !defined(__BYTE_ORDER__) || __BYTE_ORDER__ != __ORDER_LITTLE_ENDIAN__
+#error "the checkpoint format is little-endian; this host is not"
+#endif
+
+namespace {
+
+// CRC-32 with the reflected polynomial 0xEDB88320, pre- and post-inverted (zlib's crc32).
+uint32_t crc32_update(uint32_t crc, const void* data, size_t n) {
+  static uint32_t table[256];
+  static std::once_flag once;
+  std::call_once(once, [] {
+    for (uint32_t i = 0; i < 256; ++i) {
+      uint32_t v = i;
+      for (int k = 0; k < 8; ++k) v = (v & 1u) ? (0xEDB88320u ^ (v >> 1)) : (v >> 1);
+      table[i] = v;
+    }
+  });
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  crc = ~crc;
+  for (size_t i = 0; i < n; ++i) crc = table[(crc ^ p[i]) & 0xFFu] ^ (crc >> 8);
+  return ~crc;
+}
+
+constexpr char kCkptMagic[8] = {'D', 'N', 'S', 'C', 'K', 'P', 'T', '1'};
+constexpr uint32_t kCkptVersion = 1;
+
+// Sequential little-endian writer/reader over a FILE*, keeping a running CRC-32.
+struct CkptOut {
+  FILE* f;
+  uint32_t crc = 0;
+  bool ok = true;
+  void put(const void* p, size_t n) {
+    crc = crc32_update(crc, p, n);
+    ok = ok && std::fwrite(p, 1, n, f) == n;
+  }
+  template <typename T> void v(T x) { put(&x, sizeof(T)); }
+};
+struct CkptIn {
+  FILE* f;
+  uint32_t crc = 0;
+  bool ok = true;
+  void get(void* p, size_t n) {
+    if (!ok || std::fread(p, 1, n, f) != n) { ok = false; std::memset(p, 0, n); return; }
+    crc = crc32_update(crc, p, n);
+  }
+  template <typename T> T v() { T x; get(&x, sizeof(T)); return x; }
+};
+
+// The controller fields a checkpoint carries, in file order.
+template <typename D, typename I, typename L>
+void ckpt_ctrl_fields(DnsCtrl& h, D&& d, I&& i, L&& l) {
+  d(h.t); d(h.h); d(h.h_try); d(h.err); d(h.err_prev); d(h.rtol); d(h.atol);
+  for (int q = 0; q < 4; ++q) d(h.errc[q]);
+  i(h.method); i(h.k1_valid); i(h.after_reject); i(h.accepted); i(h.clipped); i(h.ctrl_kind);
+  i(h.hist_n); i(h.rej_since);
+  for (int q = 0; q < 5; ++q) i(h.hist_rej[q]);
+  for (int q = 0; q < 5; ++q) d(h.hist_err[q]);
+  for (int q = 0; q < 5; ++q) d(h.hist_h[q]);
+  l(h.n_rhs); l(h.n_acc); l(h.n_rej); l(h.n_attempts); l(h.rejects_in_row);
+}
+
+}  // namespace
+
+extern "C" {
+
+unsigned int dns_crc32(const void* data, size_t n, unsigned int crc) {
+  if (!data && n) return crc;
+  return crc32_update(crc, data, n);
+}
+
+dns_status dns_save(dns_ctx* c, const char* path) {
+  dns_status s = check_ctx(c);
+  if (s != DNS_OK) return s;
+  if (!path) return fail(c, DNS_ERR_ARG, "dns_save: null path");
+  if (!c->has_state) return fail(c, DNS_ERR_STATE, "dns_save: no state set");
+  if ((s = read_ctrl(c)) != DNS_OK) return s;
+  DnsCtrl h = *c->host_ctrl;
+  const Geom& g = c->g;
+  const size_t n = (size_t)g.nc * g.M;
+  std::vector<double2> u(n), k1;
+  CK(cudaMemcpy(u.data(), c->uu[h.parity], n * sizeof(double2), cudaMemcpyDeviceToHost), "state download");
+  if (h.k1_valid) {
+    k1.resize(n);
+    CK(cudaMemcpy(k1.data(), c->kk[h.parity], n * sizeof(double2), cudaMemcpyDeviceToHost), "k1 download");
+  }
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(c, DNS_ERR_ARG, std::string("dns_save: cannot open ") + path);
+  CkptOut o{f};
+  o.put(kCkptMagic, sizeof(kCkptMagic));
+  o.v<uint32_t>(kCkptVersion);
+  o.v<int32_t>(g.snx); o.v<int32_t>(g.sny); o.v<int32_t>(g.snz);
+  o.v<int32_t>(g.nx != g.snx ? 1 : 0); o.v<int32_t>(g.nc); o.v<int32_t>(c->precision);
+  o.v<double>(g.sx); o.v<double>(g.sy); o.v<double>(g.sz);
+  o.v<double>(c->nu); o.v<double>(c->kappa_d); o.v<double>(c->ri);
+  o.v<int32_t>(c->forcing.kind); o.v<double>(c->forcing.kf); o.v<double>(c->forcing.power);
+  ckpt_ctrl_fields(h, [&](double& x) { o.v<double>(x); }, [&](int& x) { o.v<int32_t>(x); },
+                            [&](long long& x) { o.v<int64_t>(x); });
+  o.v<int64_t>(g.M);
+  o.put(u.data(), n * sizeof(double2));
+  if (h.k1_valid) o.put(k1.data(), n * sizeof(double2));
+  const uint32_t crc = o.crc;
+  o.ok = o.ok && std::fwrite(&crc, 1, sizeof(crc), f) == sizeof(crc);
+  const bool closed = std::fclose(f) == 0;
+  if (!o.ok || !closed) return fail(c, DNS_ERR_ARG, std::string("dns_save: write failed: ") + path);
+  return DNS_OK;
+}
+
+dns_status dns_load(dns_ctx* c, const char* path) {
+  dns_status s = check_ctx(c);
+  if (s != DNS_OK) return s;
+  if (!path) return fail(c, DNS_ERR_ARG, "dns_load: null path");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(c, DNS_ERR_ARG, std::string("dns_load: cannot open ") + path);
+  CkptIn in{f};
+  const Geom& g = c->g;
+  char magic[8];
+  in.get(magic, sizeof(magic));
+  const uint32_t version = in.v<uint32_t>();
+  const int nx = in.v<int32_t>(), ny = in.v<int32_t>(), nz = in.v<int32_t>();
+  const int dealias = in.v<int32_t>(), nc = in.v<int32_t>();
+  (void)in.v<int32_t>();                       // precision of the saving context
+  for (int q = 0; q < 6; ++q) (void)in.v<double>();   // domain scales, nu, kappa, Ri
+  (void)in.v<int32_t>(); (void)in.v<double>(); (void)in.v<double>();   // forcing
+  std::string why;
+  if (!in.ok) why = "truncated header";
+  else if (std::memcmp(magic, kCkptMagic, sizeof(magic)) != 0) why = "not a checkpoint";
+  else if (version != kCkptVersion) why = "unknown version";
+  else if (nx != g.snx || ny != g.sny || nz != g.snz || dealias != (g.nx != g.snx ? 1 : 0) || nc != g.nc)
+    why = "grid, dealiasing rule or component count differs from the context";
+  DnsCtrl h{};
+  ckpt_ctrl_fields(h, [&](double& x) { x = in.v<double>(); }, [&](int& x) { x = in.v<int32_t>(); },
+                           [&](long long& x) { x = in.v<int64_t>(); });
+  const long long M = in.v<int64_t>();
+  if (why.empty() && (!in.ok || M != g.M)) why = in.ok ? "retained box differs" : "truncated header";
+  const size_t n = (size_t)g.nc * g.M;
+  std::vector<double2> u, k1;
+  if (why.empty()) {
+    u.resize(n);
+    in.get(u.data(), n * sizeof(double2));
+    if (h.k1_valid) { k1.resize(n); in.get(k1.data(), n * sizeof(double2)); }
+    const uint32_t want = in.crc;
+    uint32_t crc = 0;
+    if (!in.ok || std::fread(&crc, 1, sizeof(crc), f) != sizeof(crc)) why = "truncated data";
+    else if (crc != want) why = "CRC-32 mismatch";
+  }
+  std::fclose(f);
+  if (!why.empty()) return fail(c, DNS_ERR_ARG, std::string("dns_load: ") + why + ": " + path);
+  if ((s = read_ctrl(c)) != DNS_OK) return s;
+  DnsCtrl& d = *c->host_ctrl;
+  if (h.ctrl_kind == 2 && !d.mlp)
+    return fail(c, DNS_ERR_STATE, "dns_load: the checkpoint uses the learned controller; set its parameters first");
+  CK(cudaMemcpy(c->uu[0], u.data(), n * sizeof(double2), cudaMemcpyHostToDevice), "state upload");
+  if (h.k1_valid) CK(cudaMemcpy(c->kk[0], k1.data(), n * sizeof(double2), cudaMemcpyHostToDevice), "k1 upload");
+  d.t = h.t; d.h = h.h; d.h_try = h.h_try; d.err = h.err; d.err_prev = h.err_prev; d.rtol = h.rtol; d.atol = h.atol;
+  for (int q = 0; q < 4; ++q) d.errc[q] = h.errc[q];
+  d.method = h.method; d.k1_valid = h.k1_valid ? 1 : 0; d.after_reject = h.after_reject; d.accepted = h.accepted;
+  d.clipped = h.clipped; d.ctrl_kind = h.ctrl_kind; d.hist_n = h.hist_n; d.rej_since = h.rej_since;
+  for (int q = 0; q < 5; ++q) { d.hist_rej[q] = h.hist_rej[q]; d.hist_err[q] = h.hist_err[q]; d.hist_h[q] = h.hist_h[q]; }
+  d.n_rhs = h.n_rhs; d.n_acc = h.n_acc; d.n_rej = h.n_rej; d.n_attempts = h.n_attempts; d.rejects_in_row = h.rejects_in_row;
+  d.parity = 0; d.t_end = h.t; d.done = 1; d.status = 0; d.skip = 0; d.need_k1 = !d.k1_valid; d.trace_n = 0;
+  CK(cudaMemcpyAsync(c->ctrl, c->host_ctrl, sizeof(DnsCtrl), cudaMemcpyHostToDevice, c->stream), "ctrl write");
+  CK(cudaStreamSynchronize(c->stream), "synchronize");
+  c->has_state = true;
   return DNS_OK;
 }
 

@@ -420,6 +420,99 @@ __global__ void __launch_bounds__(kRedThreads) k_forcing_coef(const Geom g, DnsC
   }
 }
 
+// Band rescale forcing (Section 3.3.1), first half: per-block sums of w |u_n|^2 and
+// w |u_{n+1}|^2 over all retained modes, after an accepted step only.  w = 1 at kz = 0, else 2
+// (kz is the fastest index of the retained box; the Nyquist plane is never retained).
+__global__ void __launch_bounds__(kRedThreads) k_rescale_partials(const Geom g, const DnsCtrl* c,
+                                                                  double* partials) {
+  __shared__ double sh[2 * 32];
+  if (c->skip || !c->accepted) return;
+  const double2* __restrict__ u0 = c->uu[c->parity ^ 1];
+  const double2* __restrict__ u1 = c->uu[c->parity];
+  const long long n = (long long)g.nc * g.M;
+  double v[2] = {0.0, 0.0};
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double w = (i % g.Mz) == 0 ? 1.0 : 2.0;
+    const double2 a = u0[i], b = u1[i];
+    v[0] += w * fma(a.x, a.x, a.y * a.y);
+    v[1] += w * fma(b.x, b.x, b.y * b.y);
+  }
+  block_sum<2>(v, sh);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x * kRedStride + 0] = v[0];
+    partials[blockIdx.x * kRedStride + 1] = v[1];
+  }
+}
+
+// Second half (one block): E_f = band energy of u_{n+1} on 0 < |kappa| <= kf; the band is
+// multiplied by alpha = sqrt(1 + (E_n - E_{n+1}) / E_f), which returns the total energy to E_n.
+// Without band energy, or with alpha^2 <= 0, the state is left as it is.  A rescaled state
+// invalidates the carried-over derivative k_1 of a first-same-as-last pair.
+__global__ void __launch_bounds__(kRedThreads) k_rescale_apply(const Geom g, DnsCtrl* c, const double* partials,
+                                                               int nblk, double kf) {
+  __shared__ double sh[2][kRedThreads];
+  __shared__ double sb[3 * 32];
+  __shared__ double s_alpha;
+  if (c->skip || !c->accepted) return;
+  const int tid = threadIdx.x;
+  double s0 = 0.0, s1 = 0.0;
+  for (int b = tid; b < nblk; b += blockDim.x) {
+    s0 += partials[b * kRedStride + 0];
+    s1 += partials[b * kRedStride + 1];
+  }
+  sh[0][tid] = s0;
+  sh[1][tid] = s1;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (tid < w) { sh[0][tid] += sh[0][tid + w]; sh[1][tid] += sh[1][tid + w]; }
+    __syncthreads();
+  }
+  double2* __restrict__ u = c->uu[c->parity];
+  const int bx = min(g.Kx, (int)floor(kf / g.sx)), by = min(g.Ky, (int)floor(kf / g.sy));
+  const int bz = min(g.Kz, (int)floor(kf / g.sz));
+  const int nyb = 2 * by + 1, nzb = bz + 1, nbox = (2 * bx + 1) * nyb * nzb;
+  const double kf2 = kf * kf;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int i = tid; i < nbox; i += blockDim.x) {
+    const int mx = i / (nyb * nzb) - bx, r = i % (nyb * nzb), my = r / nzb - by, mz = r % nzb;
+    const double kx = g.sx * mx, ky = g.sy * my, kz = g.sz * mz;
+    const double k2 = kx * kx + ky * ky + kz * kz;
+    if (!(k2 > 0.0 && k2 <= kf2)) continue;
+    const int ix = mx >= 0 ? mx : mx + g.Mx, jy = my >= 0 ? my : my + g.My;
+    const long long off = ((long long)ix * g.My + jy) * g.Mz + mz;
+    const double w = mz == 0 ? 1.0 : 2.0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const double2 y = u[q * g.M + off];
+      v[q] += w * (y.x * y.x + y.y * y.y);
+    }
+  }
+  block_sum3(v, sb);
+  if (tid == 0) {
+    const double ef = v[0] + v[1] + v[2];
+    const double a2 = ef > 0.0 ? 1.0 + (sh[0][0] - sh[1][0]) / ef : 0.0;
+    s_alpha = a2 > 0.0 ? sqrt(a2) : 1.0;
+    if (a2 > 0.0) c->k1_valid = 0;
+  }
+  __syncthreads();
+  const double alpha = s_alpha;
+  if (alpha == 1.0) return;
+  for (int i = tid; i < nbox; i += blockDim.x) {
+    const int mx = i / (nyb * nzb) - bx, r = i % (nyb * nzb), my = r / nzb - by, mz = r % nzb;
+    const double kx = g.sx * mx, ky = g.sy * my, kz = g.sz * mz;
+    const double k2 = kx * kx + ky * ky + kz * kz;
+    if (!(k2 > 0.0 && k2 <= kf2)) continue;
+    const int ix = mx >= 0 ? mx : mx + g.Mx, jy = my >= 0 ? my : my + g.My;
+    const long long off = ((long long)ix * g.My + jy) * g.Mz + mz;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      double2& y = u[q * g.M + off];
+      y = make_double2(alpha * y.x, alpha * y.y);
+    }
+  }
+}
+
 // Partial sums for E, Omega, eps: sum w |u|^2, sum w |kappa|^2 |u|^2, sum w Re(conj(u).f).
 __global__ void __launch_bounds__(kRedThreads) k_diag_partials(const Geom g, const double2* __restrict__ u,
                                                                const double2* __restrict__ f,
@@ -578,6 +671,12 @@ cudaError_t launch_copy_slot(DnsCtrl* c, int slot, double2* dst, long long n2, c
 cudaError_t launch_forcing_coef(const Geom& g, DnsCtrl* c, int yslot, double kf, double power,
                                 int gate_k1, cudaStream_t s) {
   k_forcing_coef<<<1, kRedThreads, 0, s>>>(g, c, yslot, kf, power, gate_k1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rescale(const Geom& g, DnsCtrl* c, double* partials, double kf, cudaStream_t s) {
+  k_rescale_partials<<<kRedBlocks, kRedThreads, 0, s>>>(g, c, partials);
+  k_rescale_apply<<<1, kRedThreads, 0, s>>>(g, c, partials, kRedBlocks, kf);
   return cudaGetLastError();
 }
 

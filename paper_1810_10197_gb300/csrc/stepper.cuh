@@ -47,6 +47,8 @@ cudaError_t launch_scatter(const Geom& g, const double2* compact, double2* full,
 cudaError_t launch_copy_slot(DnsCtrl* c, int slot, double2* dst, long long n2, cudaStream_t s);
 cudaError_t launch_forcing_coef(const Geom& g, DnsCtrl* c, int yslot, double kf, double power,
                                 int gate_k1, cudaStream_t s);
+// band rescale forcing after an accepted step (partials: kRedBlocks x kRedStride scratch)
+cudaError_t launch_rescale(const Geom& g, DnsCtrl* c, double* partials, double kf, cudaStream_t s);
 constexpr int kRedStride = 4;      // partial sums per block (components)
 // energy spectrum: partials[152][nshell] doubles of scratch, out[nshell]
 cudaError_t launch_spectrum(const Geom& g, const double2* u, double* partials, int nshell, double* out,

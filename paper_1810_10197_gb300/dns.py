@@ -103,6 +103,9 @@ _SIGS.update({
     "dns_batch_context": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
     "dns_integrate_batch": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(dns_step_info)]),
+    "dns_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "dns_load": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "dns_crc32": (C.c_uint, [C.c_void_p, C.c_size_t, C.c_uint]),
 })
 TRACE_COLS = 8
 MLP_PARAMS = 5313
@@ -131,7 +134,7 @@ def declared_symbols():
     """Function names declared in include/dns.h."""
     import re
     txt = open(HEADER_PATH).read()
-    return sorted(set(re.findall(r"\b(dns_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(dns_[a-z0-9_]+)\s*\(", txt)))
 
 
 # ---- thin module-level wrappers with the C names ----------------------------------------
@@ -189,8 +192,16 @@ class Dns:
         cfg.precision = {"fp64": DNS_FP64, "fp32_mixed": DNS_FP32_MIXED}[precision] \
             if isinstance(precision, str) else int(precision)
         if forcing is not None:
-            cfg.forcing.kind = 1
-            cfg.forcing.kf, cfg.forcing.power = float(forcing[0]), float(forcing[1])
+            # (kf, power): constant-power right-hand-side term; ("rescale", kf): the
+            # post-step band rescale of Section 3.3.1
+            if isinstance(forcing[0], str):
+                if forcing[0] != "rescale":
+                    raise ValueError(f"unknown forcing {forcing[0]!r}")
+                cfg.forcing.kind = 2
+                cfg.forcing.kf, cfg.forcing.power = float(forcing[1]), 0.0
+            else:
+                cfg.forcing.kind = 1
+                cfg.forcing.kf, cfg.forcing.power = float(forcing[0]), float(forcing[1])
         cfg.dealias = {"2/3": 0, "3/2": 1}[dealias]
         h = C.c_void_p()
         if boussinesq is not None:
@@ -329,11 +340,23 @@ class Dns:
         self._check(self._lib.dns_set_controller(self._h, k, C.c_void_p(_ptr(params_dev)) if params_dev is not None
                                                  else None), "dns_set_controller")
 
+    def save(self, path):
+        self._check(self._lib.dns_save(self._h, os.fsencode(path)), "dns_save")
+
+    def load(self, path):
+        self._check(self._lib.dns_load(self._h, os.fsencode(path)), "dns_load")
+
     def query(self):
         K = (C.c_int * 3)()
         nb = C.c_size_t()
         self._check(self._lib.dns_query(self._h, K, C.byref(nb)), "dns_query")
         return tuple(K), nb.value
+
+
+def dns_crc32(data: bytes, crc: int = 0) -> int:
+    """CRC-32 of the checkpoint trailer (host code, no GPU needed)."""
+    buf = C.create_string_buffer(bytes(data), len(data))
+    return int(load().dns_crc32(buf, len(data), crc))
 
 
 def dns_rhs_noalloc(nx, ny, nz, nu, uhat_dev, f_dev, stream=None):

@@ -58,3 +58,20 @@ def test_argument_checks_before_cuda(lib):
 def test_build_flags_target_sm_103a_only():
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
     assert pkg.SUPPORTED_N == (8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768)
+
+
+def test_checkpoint_crc32_is_zlib_crc32(lib):
+    # the checkpoint trailer is the standard CRC-32 (reflected 0xEDB88320), pinned to zlib
+    import zlib
+    rng = __import__("numpy").random.default_rng(3)
+    data = rng.integers(0, 256, 100003, dtype="uint8").tobytes()
+    assert dns.dns_crc32(b"") == 0
+    assert dns.dns_crc32(b"123456789") == 0xCBF43926        # the published check value
+    assert dns.dns_crc32(data) == zlib.crc32(data)
+    # continuation over split buffers equals one pass
+    assert dns.dns_crc32(data[5000:], dns.dns_crc32(data[:5000])) == zlib.crc32(data)
+
+
+def test_checkpoint_calls_check_arguments_before_cuda(lib):
+    assert lib.dns_save(None, b"x") == 1
+    assert lib.dns_load(None, b"x") == 1

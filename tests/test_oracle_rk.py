@@ -274,3 +274,25 @@ def test_error_norm_closed_form_tg2d(nu, h, tol):
     expect = abs(dR) * a / (tol + tol * max(a, abs(Rb) * a)) * math.sqrt(4.0 / g.nmodes_half)
     assert abs(err - expect) < 1e-9 * expect
     assert np.max(np.abs(u_new - Rb * u0)) < 1e-13 * a
+
+
+def test_integrate_with_band_rescale_keeps_energy_and_refreshes_k1():
+    # the Section 3.3.1 forcing after every accepted step: the energy stays at its initial value
+    # and a first-same-as-last pair evaluates k_1 again for the rescaled state
+    from oracle import diag
+    n, nu, kf = 16, 0.02, 2.5
+    g = sp.Grid(n, n, n)
+    u0 = g.dealias(syn.random_solenoidal_hat(n, n, n, seed=6, k0=3.0))
+    e0 = diag.energy(g, u0)
+    energies = []
+    res = rk.integrate(lambda u: sp.rhs(g, u, nu), u0, 0.0, 0.2, "BS5_ADAPTIVE", h0=0.01,
+                       rtol=1e-6, atol=1e-6, nmodes=g.nmodes_half,
+                       post_step=lambda a, b: sp.rescale_band(g, a, b, kf),
+                       on_accept=lambda t, u, k: energies.append(diag.energy(g, u)))
+    assert res.status == "ok" and res.n_acc >= 3
+    assert max(abs(e - e0) for e in energies) < 1e-13 * e0
+    assert res.n_rhs == 8 * res.n_acc + 7 * res.n_rej
+    # without the rescale the same flow decays
+    plain = rk.integrate(lambda u: sp.rhs(g, u, nu), u0, 0.0, 0.2, "BS5_ADAPTIVE", h0=0.01,
+                         rtol=1e-6, atol=1e-6, nmodes=g.nmodes_half)
+    assert diag.energy(g, plain.u) < e0 * (1 - 1e-3)

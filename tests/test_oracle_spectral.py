@@ -196,6 +196,43 @@ def test_forcing_injects_constant_power():
     assert abs(dEdt - P) < 1e-12 * P
 
 
+def _decayed_pair(n=16, nu=0.05, h=0.05):
+    """(u_old, u_new): one viscous BS5 step of a random solenoidal field (energy is lost)."""
+    from oracle import rk
+    g = sp.Grid(n, n, n)
+    u0 = g.dealias(syn.random_solenoidal_hat(n, n, n, seed=4, k0=3.0))
+    u1, _, _ = rk.rk_attempt(lambda u: sp.rhs(g, u, nu), u0, h, rk.BS5)
+    return g, u0, u1
+
+
+def test_band_rescale_restores_the_energy_lost_in_the_step():
+    # Section 3.3.1: the low band is scaled so that the energy lost to diffusion is put back
+    g, u0, u1 = _decayed_pair()
+    e0, e1 = diag.energy(g, u0), diag.energy(g, u1)
+    assert e1 < e0 * (1 - 1e-3)
+    kf = 2.5
+    u2 = sp.rescale_band(g, u0, u1, kf)
+    assert abs(diag.energy(g, u2) - e0) < 1e-14 * e0
+    band = np.broadcast_to((g.k2 > 0) & (g.k2 <= kf * kf) & g.mask, u1.shape)
+    # outside the band nothing changes (bitwise); inside, one real factor > 1
+    assert np.array_equal(u2[~band], u1[~band])
+    nz = band & (np.abs(u1) > 1e-8 * np.max(np.abs(u1)))
+    ratio = u2[nz] / u1[nz]
+    assert np.max(np.abs(ratio.imag)) < 1e-15
+    assert np.ptp(ratio.real) < 1e-14 and ratio.real[0] > 1.0
+
+
+def test_band_rescale_special_cases():
+    g, u0, u1 = _decayed_pair()
+    # no energy lost: factor 1
+    u2 = sp.rescale_band(g, u1, u1, 2.5)
+    assert np.max(np.abs(u2 - u1)) <= 1e-15 * np.max(np.abs(u1))
+    # an empty band (kf below the smallest wavenumber) leaves the very same state
+    assert sp.rescale_band(g, u0, u1, 0.5) is u1
+    # energy gained by more than the band holds: alpha^2 <= 0, state unchanged
+    assert sp.rescale_band(g, 0.01 * u1, u1, 1.0) is u1
+
+
 def test_boussinesq_hydrostatic_rest_state():
     # u = 0 with a density depending on z only: buoyancy is a pure gradient, so the velocity
     # right-hand side vanishes and the density only diffuses.
