@@ -29,6 +29,11 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# Derived peak of the double-word form (bench --precision fp32x2): FP32 instruction rate
+# 152 SMs x 128 lanes x 2.07 GHz = 40.3e12/s; a double-word sum costs 11 FP32 instructions, a
+# product 7, a complex product 38 (6 flops): a radix-2 butterfly with its twiddle (10 flops)
+# costs 38 + 4 x 11 = 82, i.e. 8.2 FP32 instructions per nominal FFT flop.
+DW_PEAK_TFLOPS = 40.3 / 8.2
 METRIC = "sim-time/GPU-s at fixed L2 error vs FP64 oracle; RHS evals/s; % HBM roofline"
 UNIT = "RHS evals/s"
 N_GRID = 256
@@ -321,7 +326,7 @@ def run_accuracy(args):
                 "accepted": int(i.n_acc), "rejected": int(i.n_rej), "gpu_seconds": sec,
                 "sim_time_per_gpu_s": T / sec}
 
-    curves = {"bs5_fp64": [], "rk4_fp64": [], "dp5_fp64": [], "bs5_fp32mixed": []}
+    curves = {"bs5_fp64": [], "rk4_fp64": [], "dp5_fp64": [], "bs5_fp32mixed": [], "bs5_fp32x2": []}
     trace = None
     for tol in args.tols:
         u, i, sec, tr = run("BS5_ADAPTIVE", tol, H0, trace=(tol == TOL))
@@ -333,6 +338,9 @@ def run_accuracy(args):
     for tol in args.tols[:4]:
         u, i, sec, _ = run("BS5_ADAPTIVE", tol, H0, precision="fp32_mixed")
         curves["bs5_fp32mixed"].append(dict(tol=tol, **rec(u, i, sec)))
+    for tol in args.tols:
+        u, i, sec, _ = run("BS5_ADAPTIVE", tol, H0, precision="fp32x2")
+        curves["bs5_fp32x2"].append(dict(tol=tol, **rec(u, i, sec)))
     for tol in args.dp5_tols:
         u, i, sec, _ = run("DP5_ADAPTIVE", tol, H0)
         curves["dp5_fp64"].append(dict(tol=tol, **rec(u, i, sec)))
@@ -366,6 +374,18 @@ def run_accuracy(args):
         fp32_vs_fp64.append({"l2_error": e, "fp32_sim_time_per_gpu_s": c["sim_time_per_gpu_s"],
                              "fp64_sim_time_per_gpu_s_at_same_error": fp64_sim,
                              "speedup": (c["sim_time_per_gpu_s"] / fp64_sim) if fp64_sim else None})
+    dw_vs_fp64 = []
+    for c in curves["bs5_fp32x2"]:
+        e = c["l2_error"]
+        fp64_sim = at_error(curves["bs5_fp64"], e, "sim_time_per_gpu_s")
+        same_tol = [f for f in curves["bs5_fp64"] if f["tol"] == c["tol"]]
+        dw_vs_fp64.append({"tol": c["tol"], "l2_error": e, "fp32x2_sim_time_per_gpu_s": c["sim_time_per_gpu_s"],
+                           "fp64_sim_time_per_gpu_s_at_same_error": fp64_sim,
+                           "speedup": (c["sim_time_per_gpu_s"] / fp64_sim) if fp64_sim else None,
+                           "fp64_same_tol": ({"l2_error": same_tol[0]["l2_error"],
+                                              "rhs_evals": same_tol[0]["rhs_evals"],
+                                              "sim_time_per_gpu_s": same_tol[0]["sim_time_per_gpu_s"]}
+                                             if same_tol else None)})
     main = ([c for c in curves["bs5_fp64"] if c["tol"] == TOL] or curves["bs5_fp64"])[0]
     out = {"metric": METRIC, "value": main["sim_time_per_gpu_s"],
            "unit": f"sim-time/GPU-s (BS5 FP64 tol 1e-6, final L2 error {main['l2_error']:.2e})",
@@ -375,6 +395,7 @@ def run_accuracy(args):
                       "reference": "BS5 adaptive tol 1e-10, FP64", "reference_rhs_evals": int(i_ref.n_rhs),
                       "reference_gpu_seconds": s_ref},
            "curves": curves, "bs5_vs_rk4_at_equal_error": cmp, "fp32mixed_vs_fp64_at_equal_error": fp32_vs_fp64,
+           "fp32x2_vs_fp64_at_equal_error": dw_vs_fp64,
            "trace_bs5_fp64_tol1e-6": trace, "wall_seconds": time.perf_counter() - t_start}
     print(json.dumps(out), flush=True)
     return 0
@@ -573,6 +594,7 @@ def run_gpu(args):
     # ---- roofline of the dominant kernel -------------------------------------------------
     peaks, peak_src = load_peaks()
     fp32 = args.precision == "fp32_mixed"
+    dwp = args.precision == "fp32x2"
     flops = pass_flops(n)
     byts = pass_bytes(n, esz=8 if fp32 else 16)
     names = list(flops)
@@ -591,6 +613,15 @@ def run_gpu(args):
                 "unit": "GB/s", "frac": hbm_gbs / peaks["hbm_gbs"], "traffic": traffic,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
                 "flops_achieved_tflops": flops[dom] / avg_s / 1e12}
+    elif dwp:
+        achieved = flops[dom] / avg_s / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": DW_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / DW_PEAK_TFLOPS, "traffic": traffic,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz = 40.3e12 FP32 "
+                               "instructions/s over 8.2 FP32 instructions per nominal FFT flop in "
+                               "double-word arithmetic",
+                "hbm_achieved_gbs": hbm_gbs, "hbm_frac_of_measured": hbm_gbs / peaks["hbm_gbs"],
+                "hbm_peak_source": peak_src}
     else:
         fp64_peak_tflops = 1.25   # nominal FP64 rate of this part (FMA = 2 flops)
         achieved = flops[dom] / avg_s / 1e12
@@ -612,7 +643,8 @@ def run_gpu(args):
                          f"(numpy FP64, one thread, {dt:.1f} s)"}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if fp32 else "f64",
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64" if fp32 else ("f32x2+f64" if dwp else "f64"),
            "data": "synthetic",
            "config": {"workload": workload_name(args), "grid": [n, n, n], "nu": nu,
                       "method": "BS5_ADAPTIVE" if args.mode == "step" else "rhs",
@@ -646,7 +678,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--grid", type=int, default=N_GRID)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_mixed"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_mixed", "fp32x2"])
     ap.add_argument("--flow", default="tg", choices=["tg", "hit"])
     ap.add_argument("--mode", default="step", choices=["step", "rhs"])
     ap.add_argument("--workload", default="single", choices=["single", "ensemble", "accuracy", "controllers"])

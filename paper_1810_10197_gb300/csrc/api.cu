@@ -179,7 +179,7 @@ dns_status alloc(dns_ctx* c, void** p, size_t bytes) {
 // twiddle table of one axis (layout: axis_twiddle_turns), each entry rounded once from
 // long double
 dns_status make_twiddles(dns_ctx* c, int n, bool zaxis, void** out) {
-  const bool f32 = c->precision == DNS_FP32_MIXED;
+  const bool f32 = c->precision == DNS_FP32_MIXED, dwp = c->precision == DNS_FP32X2;
   const size_t esz = f32 ? sizeof(float2) : sizeof(double2);
   const int cnt = std::max(1, axis_twiddle_count(n, zaxis));
   std::vector<unsigned char> host(cnt * esz, 0);
@@ -189,8 +189,15 @@ dns_status make_twiddles(dns_ctx* c, int n, bool zaxis, void** out) {
     axis_twiddle_turns(n, zaxis, m, &num, &den);
     const long double ang = twopi * (long double)num / (long double)den;
     const long double cr = cosl(ang), ci = -sinl(ang);
-    if (f32) reinterpret_cast<float2*>(host.data())[m] = make_float2((float)cr, (float)ci);
-    else reinterpret_cast<double2*>(host.data())[m] = make_double2((double)cr, (double)ci);
+    if (f32) {
+      reinterpret_cast<float2*>(host.data())[m] = make_float2((float)cr, (float)ci);
+    } else if (dwp) {   // double-word: high part rounded to FP32, low part the rounded remainder
+      const float rh = (float)cr, ih = (float)ci;
+      float* q = reinterpret_cast<float*>(host.data()) + 4 * m;
+      q[0] = rh; q[1] = (float)(cr - (long double)rh); q[2] = ih; q[3] = (float)(ci - (long double)ih);
+    } else {
+      reinterpret_cast<double2*>(host.data())[m] = make_double2((double)cr, (double)ci);
+    }
   }
   dns_status s = alloc(c, out, cnt * esz);
   if (s != DNS_OK) return s;
@@ -199,8 +206,11 @@ dns_status make_twiddles(dns_ctx* c, int n, bool zaxis, void** out) {
 }
 
 cudaError_t pass(dns_ctx* c, int which, const PassArgs& a) {
-  return c->precision == DNS_FP32_MIXED ? launch_pass<float>(which, a, c->stream)
-                                        : launch_pass<double>(which, a, c->stream);
+  switch (c->precision) {
+    case DNS_FP32_MIXED: return launch_pass<float>(which, a, c->stream);
+    case DNS_FP32X2: return launch_pass<dw>(which, a, c->stream);
+    default: return launch_pass<double>(which, a, c->stream);
+  }
 }
 
 // One evaluation of Eq. (ufdef) on the stage input in `yslot`, result to `kslot`.
@@ -390,7 +400,12 @@ static dns_status create_impl(const dns_config* cfg, int bouss, double kappa, do
   // 3/2 rule: the state has N frequencies per axis, the transforms run on 3N/2 points
   auto phys = [&](int n) { return pad ? ((n % 4 == 0) ? 3 * n / 2 : -1) : n; };
   if (!supported(phys(cfg->nx)) || !supported(phys(cfg->ny)) || !supported(phys(cfg->nz))) return DNS_ERR_UNSUPPORTED;
-  if (cfg->precision != DNS_FP64 && cfg->precision != DNS_FP32_MIXED) return DNS_ERR_ARG;
+  if (cfg->precision != DNS_FP64 && cfg->precision != DNS_FP32_MIXED && cfg->precision != DNS_FP32X2)
+    return DNS_ERR_ARG;
+  // the double-word form: velocity only, transform lengths of 32 and more
+  if (cfg->precision == DNS_FP32X2 &&
+      (bouss || phys(cfg->nx) < 32 || phys(cfg->ny) < 32 || phys(cfg->nz) < 32))
+    return DNS_ERR_UNSUPPORTED;
   if (!(cfg->nu >= 0.0) || !std::isfinite(cfg->nu)) return DNS_ERR_ARG;
   if (cfg->forcing.kind < 0 || cfg->forcing.kind > 2) return DNS_ERR_ARG;
   if (cfg->forcing.kind != 0 && !(cfg->forcing.kf > 0.0 && std::isfinite(cfg->forcing.kf))) return DNS_ERR_ARG;
@@ -939,6 +954,11 @@ dns_status dns_autotune(dns_ctx* c, int reps, int* variants) {
   dns_status s = check_ctx(c);
   if (s != DNS_OK) return s;
   if (reps < 1) reps = 3;
+  if (c->precision == DNS_FP32X2) {   // one tile shape per pass in this form
+    c->var_py = c->var_p3 = 0;
+    if (variants) { variants[0] = 0; variants[1] = 0; }
+    return DNS_OK;
+  }
   const TuneKey key(c->g.nx, c->g.ny, c->g.nz, c->precision, c->g.bouss);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -6,9 +6,94 @@
 
 namespace dns {
 
+// the FP64/FP32 fma overloads stay visible next to the double-word one declared below
+using ::fma;
+
+// ---- double-word numbers ("float-float"): x = hi + lo, two FP32 values -------------------
+// On this part FP32 instructions issue at 64 times the FP64 rate.  A number held as an
+// unevaluated sum of two FP32 values has about 48 significant bits, and its arithmetic costs
+// a handful of FP32 instructions per operation, so transforms in this form run several times
+// faster than in FP64 at a rounding error near 2^-47 per operation (FP64: 2^-53).
+// Building blocks, written from their published definitions:
+//   TwoSum (Knuth, TAOCP vol. 2): s + e = a + b exactly, no condition on a, b;
+//   Fast2Sum (Dekker 1971): the same in 3 operations when |a| >= |b| (or a = 0);
+//   TwoProd with FMA: p + e = a b exactly (e = fma(a, b, -p)).
+// The sum adds the high parts exactly and the low parts once (normwise error <= 2u^2 (|x|+|y|),
+// u = 2^-24); the product keeps the three leading partial products (relative error <= 4u^2)
+// -- the double-word algorithms analysed by Joldes, Muller and Popescu (ACM TOMS 44, 2017).
+// Every step uses the _rn intrinsics, which the compiler neither contracts into FMAs nor
+// reorders.  The exponent range is FP32's: values below about 1e-30 keep fewer bits, which is
+// harmless here because errors are measured against the norm of each field.
+struct __align__(8) dw {
+  float hi, lo;
+  dw() = default;
+  __host__ __device__ constexpr dw(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ constexpr dw(int i) : hi((float)i), lo(0.0f) {}
+  // exact split of an FP64 value to 48 bits (compile-time constants fold; a run-time value
+  // costs one FP64 subtraction -- the hot conversions use from_f64<dw>)
+  __host__ __device__ constexpr dw(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+};
+struct __align__(16) dw2 { dw x, y; };
+
+__device__ __forceinline__ dw two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return dw(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ dw fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return dw(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ dw operator+(dw x, dw y) {
+  const dw s = two_sum(x.hi, y.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ dw operator-(dw x) { return dw(-x.hi, -x.lo); }
+__device__ __forceinline__ dw operator-(dw x, dw y) { return x + (-y); }
+__device__ __forceinline__ dw operator*(dw x, dw y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return fast_two_sum(p, e);
+}
+// x y + z with one normalisation
+__device__ __forceinline__ dw fma(dw x, dw y, dw z) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  const dw s = two_sum(p, z.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, z.lo)));
+}
+// a b + c d (the parts of a complex product) with one normalisation
+__device__ __forceinline__ dw dot2(dw a, dw b, dw c, dw d) {
+  const float p = __fmul_rn(a.hi, b.hi), q = __fmul_rn(c.hi, d.hi);
+  float ep = __fmaf_rn(a.hi, b.hi, -p);
+  ep = __fmaf_rn(a.hi, b.lo, ep);
+  ep = __fmaf_rn(a.lo, b.hi, ep);
+  float eq = __fmaf_rn(c.hi, d.hi, -q);
+  eq = __fmaf_rn(c.hi, d.lo, eq);
+  eq = __fmaf_rn(c.lo, d.hi, eq);
+  const dw s = two_sum(p, q);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(ep, eq)));
+}
+// 1 / y: the FP32 reciprocal refined by one Newton step in double-word arithmetic
+__device__ __forceinline__ dw recip(dw y) {
+  const float r = __frcp_rn(y.hi);
+  float e = __fmaf_rn(-y.hi, r, 1.0f);
+  e = __fmaf_rn(-y.lo, r, e);
+  return fast_two_sum(r, __fmul_rn(r, e));
+}
+__device__ __forceinline__ dw operator/(dw x, dw y) { return x * recip(y); }
+__device__ __forceinline__ bool operator==(dw x, dw y) { return x.hi == y.hi && x.lo == y.lo; }
+__device__ __forceinline__ bool operator!=(dw x, dw y) { return !(x == y); }
+__device__ __forceinline__ bool operator>(dw x, dw y) { return x.hi > y.hi || (x.hi == y.hi && x.lo > y.lo); }
+__device__ __forceinline__ bool operator<=(dw x, dw y) { return !(x > y); }
+
 template <typename T> struct V2;
 template <> struct V2<double> { using type = double2; };
 template <> struct V2<float> { using type = float2; };
+template <> struct V2<dw> { using type = dw2; };
 template <typename T> using v2_t = typename V2<T>::type;
 
 template <typename V> __device__ __forceinline__ V mk(decltype(V::x) a, decltype(V::x) b) {
@@ -30,6 +115,13 @@ template <int S, typename V> __device__ __forceinline__ V mul_si(V a) {
 }
 template <typename V> __device__ __forceinline__ V cscale(V a, decltype(V::x) s) { return mk<V>(a.x * s, a.y * s); }
 template <typename V> __device__ __forceinline__ V cconj(V a) { return mk<V>(a.x, -a.y); }
+// double-word complex products: each part is one a b + c d with a single normalisation
+template <> __device__ __forceinline__ dw2 cmul<dw2>(dw2 a, dw2 b) {
+  return mk<dw2>(dot2(a.x, b.x, -a.y, b.y), dot2(a.x, b.y, a.y, b.x));
+}
+template <> __device__ __forceinline__ dw2 cmulc<dw2>(dw2 a, dw2 b) {
+  return mk<dw2>(dot2(a.x, b.x, a.y, b.y), dot2(a.y, b.x, -a.x, b.y));
+}
 
 // Conversions between FP64 and FP32 with integer bit arithmetic.  On this part FP64<->FP32
 // conversion instructions issue on the FP64 pipe (1/64 of the FP32 rate); the mixed-precision
@@ -59,8 +151,14 @@ __device__ __forceinline__ double f2d_bits(float f) {
 template <typename T> __device__ __forceinline__ T from_f64(double x);
 template <> __device__ __forceinline__ double from_f64<double>(double x) { return x; }
 template <> __device__ __forceinline__ float from_f64<float>(double x) { return d2f_bits(x); }
+// x = hi + lo: hi rounded to FP32, lo the rounded remainder (x - hi is exact in FP64)
+template <> __device__ __forceinline__ dw from_f64<dw>(double x) {
+  const float h = d2f_bits(x);
+  return dw(h, d2f_bits(x - f2d_bits(h)));
+}
 __device__ __forceinline__ double to_f64(double x) { return x; }
 __device__ __forceinline__ double to_f64(float x) { return f2d_bits(x); }
+__device__ __forceinline__ double to_f64(dw x) { return f2d_bits(x.hi) + f2d_bits(x.lo); }
 
 // Grid geometry shared by every kernel.  Retained ("compact") spectral arrays are
 // [3][Mx][My][Mz] with Mx = 2Kx+1 (kx = i for i <= Kx, i - Mx above), Mz = Kz+1.

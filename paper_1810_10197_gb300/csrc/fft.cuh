@@ -162,19 +162,19 @@ template <int SIGN, typename V> struct Dft<16, SIGN, V> {
       y[n2][0] = v[n2]; y[n2][1] = v[4 + n2]; y[n2][2] = v[8 + n2]; y[n2][3] = v[12 + n2];
       Dft<4, SIGN, V>::run(y[n2]);
     }
-    const T sg = (T)SIGN;
+    const T ps1 = SIGN > 0 ? s1 : -s1, pc1 = SIGN > 0 ? c1 : -c1;   // SIGN s1, SIGN c1
     // n2 = 1: W^0, W^1, W^2, W^3
-    y[1][1] = cmul(y[1][1], mk<V>(c1, sg * s1));
+    y[1][1] = cmul(y[1][1], mk<V>(c1, ps1));
     y[1][2] = w8_1<SIGN>(y[1][2]);
-    y[1][3] = cmul(y[1][3], mk<V>(s1, sg * c1));
+    y[1][3] = cmul(y[1][3], mk<V>(s1, pc1));
     // n2 = 2: W^0, W^2, W^4, W^6
     y[2][1] = w8_1<SIGN>(y[2][1]);
     y[2][2] = mul_si<SIGN>(y[2][2]);
     y[2][3] = w8_3<SIGN>(y[2][3]);
     // n2 = 3: W^0, W^3, W^6, W^9
-    y[3][1] = cmul(y[3][1], mk<V>(s1, sg * c1));
+    y[3][1] = cmul(y[3][1], mk<V>(s1, pc1));
     y[3][2] = w8_3<SIGN>(y[3][2]);
-    y[3][3] = cmul(y[3][3], mk<V>(-c1, -sg * s1));
+    y[3][3] = cmul(y[3][3], mk<V>(-c1, -ps1));
 #pragma unroll
     for (int k1 = 0; k1 < 4; ++k1) {
       V z[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};

@@ -1,0 +1,5 @@
+// Double-word pass P3 (see passes_dw.cu).
+#include "passes_impl.cuh"
+namespace dns {
+template cudaError_t launch_pass_w<dw, 3>(const PassArgs&, cudaStream_t);
+}

@@ -75,45 +75,83 @@ static cudaError_t launch_p3(const PassArgs& a, cudaStream_t s) {
 
 #define DNS_XY_SIZES(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768)
 #define DNS_ZH_SIZES(X) X(4) X(6) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384)
+// the double-word form: lines of 32 points and more, velocity only, default tiles (its kernels
+// are large; every instantiation costs seconds of compile time)
+#define DNS_XY_SIZES_DW(X) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768)
+#define DNS_ZH_SIZES_DW(X) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384)
 
-template <typename T>
-cudaError_t launch_pass(int which, const PassArgs& a, cudaStream_t s) {
-  switch (which) {
-    case 1:
+template <typename T> constexpr bool is_dw() { return false; }
+template <> constexpr bool is_dw<dw>() { return true; }
+
+// Pass WHICH (1..5) for element type T; cudaErrorInvalidValue for an unsupported line length.
+template <typename T, int WHICH>
+cudaError_t launch_pass_w(const PassArgs& a, cudaStream_t s) {
+  if constexpr (is_dw<T>()) {
+    if (a.g.bouss) return cudaErrorInvalidValue;
+    if constexpr (WHICH == 1 || WHICH == 5) {
+      switch (a.g.nx) {
+#define CD(N) case N: return WHICH == 1 ? launch_p1<T, N, false>(a, s) : launch_p5<T, N, false>(a, s);
+        DNS_XY_SIZES_DW(CD)
+#undef CD
+      }
+    } else if constexpr (WHICH == 2 || WHICH == 4) {
+      switch (a.g.ny) {
+#define CD(N) case N: return launch_py_v<T, N, WHICH == 2, 0>(a, s);
+        DNS_XY_SIZES_DW(CD)
+#undef CD
+      }
+    } else {
+      switch (a.g.nz / 2) {
+#define CD(N) case N: return launch_p3_v<T, N, false, 0>(a, s);
+        DNS_ZH_SIZES_DW(CD)
+#undef CD
+      }
+    }
+    return cudaErrorInvalidValue;
+  } else {
+    if constexpr (WHICH == 1) {
       switch (a.g.nx) {
 #define C1(N) case N: return a.g.bouss ? launch_p1<T, N, true>(a, s) : launch_p1<T, N, false>(a, s);
         DNS_XY_SIZES(C1)
 #undef C1
       }
-      break;
-    case 2:
+    } else if constexpr (WHICH == 2) {
       switch (a.g.ny) {
 #define C2(N) case N: return launch_py<T, N, true>(a, s);
         DNS_XY_SIZES(C2)
 #undef C2
       }
-      break;
-    case 3:
+    } else if constexpr (WHICH == 3) {
       switch (a.g.nz / 2) {
 #define C3(N) case N: return a.g.bouss ? launch_p3<T, N, true>(a, s) : launch_p3<T, N, false>(a, s);
         DNS_ZH_SIZES(C3)
 #undef C3
       }
-      break;
-    case 4:
+    } else if constexpr (WHICH == 4) {
       switch (a.g.ny) {
 #define C4(N) case N: return launch_py<T, N, false>(a, s);
         DNS_XY_SIZES(C4)
 #undef C4
       }
-      break;
-    case 5:
+    } else {
       switch (a.g.nx) {
 #define C5(N) case N: return a.g.bouss ? launch_p5<T, N, true>(a, s) : launch_p5<T, N, false>(a, s);
         DNS_XY_SIZES(C5)
 #undef C5
       }
-      break;
+    }
+    return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+cudaError_t launch_pass(int which, const PassArgs& a, cudaStream_t s) {
+  switch (which) {
+    case 1: return launch_pass_w<T, 1>(a, s);
+    case 2: return launch_pass_w<T, 2>(a, s);
+    case 3: return launch_pass_w<T, 3>(a, s);
+    case 4: return launch_pass_w<T, 4>(a, s);
+    case 5: return launch_pass_w<T, 5>(a, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -24,7 +24,8 @@ STATUS_NAMES = {0: "DNS_OK", 1: "DNS_ERR_ARG", 2: "DNS_ERR_CUDA", 3: "DNS_ERR_OO
 DNS_RK4, DNS_BS5_FIXED, DNS_BS5_ADAPTIVE, DNS_DP5_FIXED, DNS_DP5_ADAPTIVE = 0, 1, 2, 3, 4
 METHODS = {"RK4": DNS_RK4, "BS5_FIXED": DNS_BS5_FIXED, "BS5_ADAPTIVE": DNS_BS5_ADAPTIVE,
            "DP5_FIXED": DNS_DP5_FIXED, "DP5_ADAPTIVE": DNS_DP5_ADAPTIVE}
-DNS_FP64, DNS_FP32_MIXED = 0, 1
+DNS_FP64, DNS_FP32_MIXED, DNS_FP32X2 = 0, 1, 2
+PRECISIONS = {"fp64": DNS_FP64, "fp32_mixed": DNS_FP32_MIXED, "fp32x2": DNS_FP32X2}
 SUPPORTED_N = (8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768)
 
 
@@ -169,7 +170,7 @@ def _config(nx, ny=None, nz=None, nu=0.0, precision="fp64", lengths=None):
     if lengths is not None:
         cfg.lx, cfg.ly, cfg.lz = (float(v) for v in lengths)
     cfg.nu = float(nu)
-    cfg.precision = {"fp64": DNS_FP64, "fp32_mixed": DNS_FP32_MIXED}[precision] \
+    cfg.precision = PRECISIONS[precision] \
         if isinstance(precision, str) else int(precision)
     return cfg
 
@@ -189,7 +190,7 @@ class Dns:
         if lengths is not None:
             cfg.lx, cfg.ly, cfg.lz = (float(v) for v in lengths)
         cfg.nu = float(nu)
-        cfg.precision = {"fp64": DNS_FP64, "fp32_mixed": DNS_FP32_MIXED}[precision] \
+        cfg.precision = PRECISIONS[precision] \
             if isinstance(precision, str) else int(precision)
         if forcing is not None:
             # (kf, power): constant-power right-hand-side term; ("rescale", kf): the
