@@ -954,11 +954,6 @@ dns_status dns_autotune(dns_ctx* c, int reps, int* variants) {
   dns_status s = check_ctx(c);
   if (s != DNS_OK) return s;
   if (reps < 1) reps = 3;
-  if (c->precision == DNS_FP32X2) {   // one tile shape per pass in this form
-    c->var_py = c->var_p3 = 0;
-    if (variants) { variants[0] = 0; variants[1] = 0; }
-    return DNS_OK;
-  }
   const TuneKey key(c->g.nx, c->g.ny, c->g.nz, c->precision, c->g.bouss);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);

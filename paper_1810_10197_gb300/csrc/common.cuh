@@ -90,6 +90,9 @@ __device__ __forceinline__ bool operator!=(dw x, dw y) { return !(x == y); }
 __device__ __forceinline__ bool operator>(dw x, dw y) { return x.hi > y.hi || (x.hi == y.hi && x.lo > y.lo); }
 __device__ __forceinline__ bool operator<=(dw x, dw y) { return !(x > y); }
 
+template <typename T> __host__ __device__ constexpr bool is_dw() { return false; }
+template <> __host__ __device__ constexpr bool is_dw<dw>() { return true; }
+
 template <typename T> struct V2;
 template <> struct V2<double> { using type = double2; };
 template <> struct V2<float> { using type = float2; };
@@ -115,6 +118,21 @@ template <int S, typename V> __device__ __forceinline__ V mul_si(V a) {
 }
 template <typename V> __device__ __forceinline__ V cscale(V a, decltype(V::x) s) { return mk<V>(a.x * s, a.y * s); }
 template <typename V> __device__ __forceinline__ V cconj(V a) { return mk<V>(a.x, -a.y); }
+// Complex sums of double-word values inside the transforms: the exact TwoSum of the high parts
+// and one rounded sum of the low parts, without renormalising (8 FP32 instructions instead of
+// 11).  A butterfly chains a few of these, so |lo| may grow to a few ulp of hi; the normwise
+// error stays O(u^2), products take un-normalised operands as they are, and cnorm
+// renormalises (Fast2Sum) when a stage stores its results.
+__device__ __forceinline__ dw add_u(dw x, dw y) {
+  const dw s = two_sum(x.hi, y.hi);
+  return dw(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+template <> __device__ __forceinline__ dw2 cadd<dw2>(dw2 a, dw2 b) { return mk<dw2>(add_u(a.x, b.x), add_u(a.y, b.y)); }
+template <> __device__ __forceinline__ dw2 csub<dw2>(dw2 a, dw2 b) { return mk<dw2>(add_u(a.x, -b.x), add_u(a.y, -b.y)); }
+template <typename V> __device__ __forceinline__ V cnorm(V a) { return a; }
+template <> __device__ __forceinline__ dw2 cnorm<dw2>(dw2 a) {
+  return mk<dw2>(fast_two_sum(a.x.hi, a.x.lo), fast_two_sum(a.y.hi, a.y.lo));
+}
 // double-word complex products: each part is one a b + c d with a single normalisation
 template <> __device__ __forceinline__ dw2 cmul<dw2>(dw2 a, dw2 b) {
   return mk<dw2>(dot2(a.x, b.x, -a.y, b.y), dot2(a.x, b.y, a.y, b.x));

@@ -224,7 +224,46 @@ __device__ __forceinline__ void fft_stage(V* x, int g, const V* tws, bool active
       const int jm = j % NS;
       const int base = (j - jm) * R + jm;
 #pragma unroll
-      for (int r = 0; r < R; ++r) x[pidx<V>(base + r * NS)] = v[p][r];
+      for (int r = 0; r < R; ++r) x[pidx<V>(base + r * NS)] = cnorm(v[p][r]);
+    }
+  }
+  __syncthreads();
+}
+
+// The same stage with NS and the twiddle offset known at run time only (NS a power of two):
+// consecutive stages of equal radix share one copy of this code (see line_fft).
+template <typename V, int N, int SIGN, int R>
+__device__ __forceinline__ void fft_stage_rt(V* x, int g, const V* tws, bool active, int ns, int twoff) {
+  constexpr int B = N / R;
+  constexpr int G = FftPlan<N>::G;
+  constexpr int PER = (B + G - 1) / G;
+  V v[PER][R];
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int j = g + p * G;
+    if (active && ((B % G == 0) || j < B)) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[p][r] = x[pidx<V>(j + r * B)];
+      if (ns > 1) {
+        const V* t = tws + twoff + (j & (ns - 1)) * (R - 1) - 1;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const V w = t[r];
+          v[p][r] = SIGN < 0 ? cmul(v[p][r], w) : cmulc(v[p][r], w);
+        }
+      }
+      Dft<R, SIGN, V>::run(v[p]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int j = g + p * G;
+    if (active && ((B % G == 0) || j < B)) {
+      const int jm = j & (ns - 1);
+      const int base = (j - jm) * R + jm;
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[pidx<V>(base + r * ns)] = cnorm(v[p][r]);
     }
   }
   __syncthreads();
@@ -232,12 +271,28 @@ __device__ __forceinline__ void fft_stage(V* x, int g, const V* tws, bool active
 
 // Transform the line at x (length N, padded layout) with G = FftPlan<N>::G threads
 // (g = 0..G-1).  Every thread of the CTA must call this (it contains barriers); the caller
-// syncs before.  Threads with active = false only take part in the barriers.
+// syncs before.  Threads with active = false only take part in the barriers.  In double-word
+// arithmetic (dw2 elements) leading stages of equal radix run as a loop over one copy of the
+// stage code: those butterflies are long, and unrolled copies of them overflow the
+// instruction cache.  The FP32 and FP64 forms keep every stage unrolled (their code is short,
+// and compile-time strides schedule better).
 template <typename V, int N, int SIGN>
 __device__ __forceinline__ void line_fft(V* x, int g, const V* tws, bool active = true) {
-  fft_stage<V, N, SIGN, 0>(x, g, tws, active);
-  if constexpr (FftPlan<N>::S > 1) fft_stage<V, N, SIGN, 1>(x, g, tws, active);
-  if constexpr (FftPlan<N>::S > 2) fft_stage<V, N, SIGN, 2>(x, g, tws, active);
+  constexpr int S = FftPlan<N>::S, R0 = FftPlan<N>::R0, R1 = FftPlan<N>::R1, R2 = FftPlan<N>::R2;
+  constexpr bool share = is_dw<decltype(V::x)>();
+  constexpr int RUN = (share && S >= 2 && R1 == R0) ? ((S == 3 && R2 == R0) ? 3 : 2) : 1;
+  if constexpr (RUN > 1) {
+#pragma unroll 1
+    for (int st = 0; st < RUN; ++st) {
+      const int ns = st == 0 ? 1 : (st == 1 ? R0 : R0 * R0);
+      const int twoff = st <= 1 ? 0 : R0 * (R0 - 1);
+      fft_stage_rt<V, N, SIGN, R0>(x, g, tws, active, ns, twoff);
+    }
+  } else {
+    fft_stage<V, N, SIGN, 0>(x, g, tws, active);
+  }
+  if constexpr (S > 1 && RUN < 2) fft_stage<V, N, SIGN, 1>(x, g, tws, active);
+  if constexpr (S > 2 && RUN < 3) fft_stage<V, N, SIGN, 2>(x, g, tws, active);
 }
 
 }  // namespace dns

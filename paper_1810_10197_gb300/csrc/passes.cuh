@@ -15,6 +15,8 @@
 // so the work and traffic skip the modes the 2/3 rule zeroes.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "fft.cuh"
 
@@ -42,7 +44,9 @@ struct PassArgs {
 // Column tiles: kz-contiguous columns handled per CTA in the x and y passes (128-byte rows),
 // and z lines per CTA in the z pass.
 template <typename T, int N> __host__ __device__ constexpr int p1_cols() {
-  return sizeof(T) == 4 ? (N >= 512 ? 8 : 16) : (N >= 512 ? 4 : 8);
+  // double-word: half the FP64 tile, so that two or three CTAs share an SM (its kernels are
+  // issue-bound and need the extra warps; the FP64 ones are bound by the FP64 pipe)
+  return is_dw<T>() ? (N >= 512 ? 2 : 4) : sizeof(T) == 4 ? (N >= 512 ? 8 : 16) : (N >= 512 ? 4 : 8);
 }
 template <typename T, int VAR = 0> __host__ __device__ constexpr int py_cols() {
   return (sizeof(T) == 4 ? 16 : 8) >> VAR;
@@ -320,45 +324,71 @@ k_p3(const PassArgs a) {
   });
   cp_async_wait();
   __syncthreads();
-  // C2R pre-step on pairs (k, MZ-k), k = 0..MZ/2
-  {
+  // C2R pre-step on pairs (k, MZ-k), k = 0..MZ/2, of the NIN input lines
+  auto prestep = [&]() {
     constexpr int NP = MZ / 2 + 1;
     for (int i = tid; i < NIN * TL * NP; i += nth) {
       const int l = i / NP, k = i - l * NP;
       V* L = lines + l * LD;
       const int m = MZ - k;
       const V xk = L[pidx<V>(k)], xm = L[pidx<V>(m)];
-      const V s = cadd(xk, cconj(xm)), d = csub(xk, cconj(xm));
-      const V zk = cadd(s, mul_si<+1>(cmul(cconj(tw[k]), d)));      // e^{+2 pi i k / nz}
-      if (k != 0 && k != m) {
-        const V s2 = cadd(xm, cconj(xk)), d2 = csub(xm, cconj(xk));
-        L[pidx<V>(m)] = cadd(s2, mul_si<+1>(cmul(cconj(tw[m]), d2)));
+      // s = X_k + conj X_m, t = e^{+2 pi i k/nz} (X_k - conj X_m); Z_k = s + i t.  The partner
+      // k' = m has s' = conj s and t' = conj t (e^{+2 pi i m/nz} = -e^{-2 pi i k/nz}), so
+      // Z_m = conj(s) + i conj(t) costs two more additions.
+      const V s = cadd(xk, cconj(xm));
+      const V t = cmul(cconj(tw[k]), csub(xk, cconj(xm)));
+      if (k != 0 && k != m) L[pidx<V>(m)] = mk<V>(s.x + t.y, t.x - s.y);
+      L[pidx<V>(k)] = mk<V>(s.x - t.y, s.y + t.x);
+    }
+  };
+  // u x omega (and rho u) on both packed halves (real part: even z, imaginary part: odd z);
+  // conjugated when CJ (see below)
+  auto cross = [&](auto cj) {
+    constexpr bool CJ = decltype(cj)::value;
+    for (int i = tid; i < TL * MZ; i += nth) {
+      const int l = i / MZ, n = pidx<V>(i - l * MZ);
+      const V u0 = lines[(0 * TL + l) * LD + n], u1 = lines[(1 * TL + l) * LD + n], u2 = lines[(2 * TL + l) * LD + n];
+      const V w0 = lines[(3 * TL + l) * LD + n], w1 = lines[(4 * TL + l) * LD + n], w2 = lines[(5 * TL + l) * LD + n];
+      V p0 = mk<V>(u1.x * w2.x - u2.x * w1.x, u1.y * w2.y - u2.y * w1.y);
+      V p1 = mk<V>(u2.x * w0.x - u0.x * w2.x, u2.y * w0.y - u0.y * w2.y);
+      V p2 = mk<V>(u0.x * w1.x - u1.x * w0.x, u0.y * w1.y - u1.y * w0.y);
+      if constexpr (CJ) { p0 = cconj(p0); p1 = cconj(p1); p2 = cconj(p2); }
+      lines[(0 * TL + l) * LD + n] = p0;
+      lines[(1 * TL + l) * LD + n] = p1;
+      lines[(2 * TL + l) * LD + n] = p2;
+      if constexpr (BOUSS) {
+        const V r = lines[(6 * TL + l) * LD + n];
+        V q0 = mk<V>(r.x * u0.x, r.y * u0.y), q1 = mk<V>(r.x * u1.x, r.y * u1.y), q2 = mk<V>(r.x * u2.x, r.y * u2.y);
+        if constexpr (CJ) { q0 = cconj(q0); q1 = cconj(q1); q2 = cconj(q2); }
+        lines[(3 * TL + l) * LD + n] = q0;
+        lines[(4 * TL + l) * LD + n] = q1;
+        lines[(5 * TL + l) * LD + n] = q2;
       }
-      L[pidx<V>(k)] = zk;
     }
-  }
-  __syncthreads();
-  line_fft<V, MZ, +1>(lines + (tid / G) * LD, tid % G, tws);
-  // u x omega (and rho u) on both packed halves (real part: even z, imaginary part: odd z)
-  for (int i = tid; i < TL * MZ; i += nth) {
-    const int l = i / MZ, n = pidx<V>(i - l * MZ);
-    const V u0 = lines[(0 * TL + l) * LD + n], u1 = lines[(1 * TL + l) * LD + n], u2 = lines[(2 * TL + l) * LD + n];
-    const V w0 = lines[(3 * TL + l) * LD + n], w1 = lines[(4 * TL + l) * LD + n], w2 = lines[(5 * TL + l) * LD + n];
-    lines[(0 * TL + l) * LD + n] = mk<V>(u1.x * w2.x - u2.x * w1.x, u1.y * w2.y - u2.y * w1.y);
-    lines[(1 * TL + l) * LD + n] = mk<V>(u2.x * w0.x - u0.x * w2.x, u2.y * w0.y - u0.y * w2.y);
-    lines[(2 * TL + l) * LD + n] = mk<V>(u0.x * w1.x - u1.x * w0.x, u0.y * w1.y - u1.y * w0.y);
-    if constexpr (BOUSS) {
-      const V r = lines[(6 * TL + l) * LD + n];
-      lines[(3 * TL + l) * LD + n] = mk<V>(r.x * u0.x, r.y * u0.y);
-      lines[(4 * TL + l) * LD + n] = mk<V>(r.x * u1.x, r.y * u1.y);
-      lines[(5 * TL + l) * LD + n] = mk<V>(r.x * u2.x, r.y * u2.y);
+  };
+  const int line = tid / G;
+  // Double-word: the two phases share one copy of the line transform (its butterflies are
+  // long; two inlined copies overflow the instruction cache).  The products are stored
+  // conjugated, transformed by the same inverse DFT -- conj(DFT^+(conj z)) is the forward DFT
+  // of z -- and the post-step conjugates on reading.  FP32/FP64: two unrolled transforms.
+  // Threads on lines past the active count idle in the second transform but take part in
+  // the barriers.
+  constexpr bool SHARE = is_dw<T>();
+  if constexpr (SHARE) {
+#pragma unroll 1
+    for (int ph = 0; ph < 2; ++ph) {
+      if (ph == 0) prestep();
+      else cross(std::true_type{});
+      __syncthreads();
+      const int nact = ph == 0 ? NIN * TL : NOUT * TL;
+      line_fft<V, MZ, +1>(lines + (line < nact ? line : 0) * LD, tid % G, tws, line < nact);
     }
-  }
-  __syncthreads();
-  // forward complex DFT of the packed product lines; threads on lines >= NOUT TL idle but
-  // still take part in the barriers
-  {
-    const int line = tid / G;
+  } else {
+    prestep();
+    __syncthreads();
+    line_fft<V, MZ, +1>(lines + line * LD, tid % G, tws);
+    cross(std::false_type{});
+    __syncthreads();
     line_fft<V, MZ, -1>(lines + (line < NOUT * TL ? line : 0) * LD, tid % G, tws, line < NOUT * TL);
   }
   // R2C post-step, keep kz <= Kz
@@ -367,7 +397,8 @@ k_p3(const PassArgs a) {
     const long long xy = xy0 + l;
     if (xy >= nxy) return;
     const V* L = lines + row * LD;
-    const V zk = L[pidx<V>(k)], zm = L[pidx<V>((MZ - k) % MZ)];
+    V zk = L[pidx<V>(k)], zm = L[pidx<V>((MZ - k) % MZ)];
+    if constexpr (SHARE) { zk = cconj(zk); zm = cconj(zm); }
     const V s = cadd(zk, cconj(zm)), d = csub(zk, cconj(zm));
     const V od = cmul(tw[k], d);                   // e^{-2 pi i k / nz} (Z_k - conj Z_{M-k})
     const T hf = (T)0.5;

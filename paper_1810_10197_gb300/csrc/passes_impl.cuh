@@ -75,13 +75,10 @@ static cudaError_t launch_p3(const PassArgs& a, cudaStream_t s) {
 
 #define DNS_XY_SIZES(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768)
 #define DNS_ZH_SIZES(X) X(4) X(6) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384)
-// the double-word form: lines of 32 points and more, velocity only, default tiles (its kernels
-// are large; every instantiation costs seconds of compile time)
+// the double-word form: lines of 32 points and more, velocity only (its kernels are large;
+// every instantiation costs seconds of compile time)
 #define DNS_XY_SIZES_DW(X) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768)
 #define DNS_ZH_SIZES_DW(X) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384)
-
-template <typename T> constexpr bool is_dw() { return false; }
-template <> constexpr bool is_dw<dw>() { return true; }
 
 // Pass WHICH (1..5) for element type T; cudaErrorInvalidValue for an unsupported line length.
 template <typename T, int WHICH>
@@ -96,13 +93,13 @@ cudaError_t launch_pass_w(const PassArgs& a, cudaStream_t s) {
       }
     } else if constexpr (WHICH == 2 || WHICH == 4) {
       switch (a.g.ny) {
-#define CD(N) case N: return launch_py_v<T, N, WHICH == 2, 0>(a, s);
+#define CD(N) case N: return launch_py<T, N, WHICH == 2>(a, s);
         DNS_XY_SIZES_DW(CD)
 #undef CD
       }
     } else {
       switch (a.g.nz / 2) {
-#define CD(N) case N: return launch_p3_v<T, N, false, 0>(a, s);
+#define CD(N) case N: return launch_p3<T, N, false>(a, s);
         DNS_ZH_SIZES_DW(CD)
 #undef CD
       }

@@ -6,11 +6,13 @@ of the operands' magnitude and a product at most 4 u^2; an FFT of length N adds
 O(u_dw log2 N) normwise (log2 N <= 9 here), five axis passes and one product give a bound
 near 50 u_dw = 3.6e-13 in the worst case; typical errors are a few u_dw.  Bounds used:
   * one right-hand side: 2e-13 relative max-norm (the FP64 path is held to 1e-13);
-  * ten adaptive BS5 steps: 5e-12 relative L2, with decisions (accept/reject, counts)
-    identical to the oracle's.  Rounding errors of the state scale with the unit roundoff,
-    which is 64 times FP64's (2^-47 against 2^-53).  The FP64 path, run on the same case in
-    the same test, lands at 1.0e-13 (its bound: 1e-12); this form at 2.1e-12, 21 times more,
-    so it does not meet the FP64 path's 1e-12 bound on this case.
+  * ten adaptive BS5 steps: decisions (accept/reject, counts) identical to the oracle's; the
+    final time within 2e-10 relative (the embedded error is a cancellation that amplifies the
+    right-hand side's rounding, see the test); the state, moved to the same time, within
+    1e-12 relative L2, the FP64 path's bound.  Measured: FP64 2e-16, this form 9e-16.
+    Compared without moving to the same time, the FP64 state differs by 1e-13 and this form's
+    by about 7e-12: almost all of that is the state's change over the slightly different
+    final time, not rounding of the state.
 """
 import numpy as np
 import pytest
@@ -96,12 +98,18 @@ def test_ten_adaptive_steps():
         d.enqueue_attempts(10, "BS5_ADAPTIVE", tol, tol, t_end=1e9, h0=1e-3)
         info = d.info()
         assert (info.n_acc, info.n_rej, info.n_rhs) == (ref.n_acc, ref.n_rej, ref.n_rhs)
-        assert info.t == pytest.approx(ref.t, rel=1e-12)
-        errs[prec] = rel_l2(d.get_state(), ref.u)
+        # err is a cancellation: |e| ~ tol |u| while its terms are ~ h |k| ~ 0.1 |u|, so a
+        # right-hand-side rounding eps moves err by ~ 0.05 eps 0.1 / tol = 5e3 eps, and h by a
+        # fifth of that: 2e-11 per step at eps = 2e-14 (FP64: 5e-13 at 5e-16)
+        assert info.t == pytest.approx(ref.t, rel=2e-10 if prec == "fp32x2" else 1e-12)
+        # compare at the same time: move the oracle's state to the GPU's t to first order
+        # (u + dt f(u)); what remains is the rounding of the state itself
+        u_at = ref.u + (info.t - ref.t) * sp.rhs(g, ref.u, nu)
+        errs[prec] = rel_l2(d.get_state(), u_at)
         d.close()
     print("ten-step relative L2 error:", errs)
     assert errs["fp64"] < 1e-12
-    assert errs["fp32x2"] < 5e-12
+    assert errs["fp32x2"] < 1e-12
 
 
 def test_unsupported_configurations_are_refused():
