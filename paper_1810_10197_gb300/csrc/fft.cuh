@@ -187,6 +187,15 @@ template <int SIGN, typename V> struct Dft<16, SIGN, V> {
 
 // ---- one Stockham stage and the whole line transform ------------------------------------
 
+// The G threads of a line are consecutive (line = tid / G) and, when G divides 32, lie in one
+// warp: the stages of a line then need only warp-level ordering, and line_fft ends
+// with one block barrier for what the caller does next.
+template <int N> __host__ __device__ constexpr bool warp_local() { return 32 % plan_threads(N) == 0; }
+template <int N> __device__ __forceinline__ void stage_sync() {
+  if constexpr (warp_local<N>()) __syncwarp();
+  else __syncthreads();
+}
+
 // tws: the stage twiddle tables of this line length; stage s >= 1 holds, at
 // TWOFF + jm (R-1) + (r-1), exp(SIGN' 2 pi i jm r / (NS R)) with SIGN' = -1 (conjugated for
 // inverse transforms).
@@ -216,7 +225,7 @@ __device__ __forceinline__ void fft_stage(V* x, int g, const V* tws, bool active
       Dft<R, SIGN, V>::run(v[p]);
     }
   }
-  __syncthreads();
+  stage_sync<N>();
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     const int j = g + p * G;
@@ -227,7 +236,7 @@ __device__ __forceinline__ void fft_stage(V* x, int g, const V* tws, bool active
       for (int r = 0; r < R; ++r) x[pidx<V>(base + r * NS)] = cnorm(v[p][r]);
     }
   }
-  __syncthreads();
+  stage_sync<N>();
 }
 
 // The same stage with NS and the twiddle offset known at run time only (NS a power of two):
@@ -255,7 +264,7 @@ __device__ __forceinline__ void fft_stage_rt(V* x, int g, const V* tws, bool act
       Dft<R, SIGN, V>::run(v[p]);
     }
   }
-  __syncthreads();
+  stage_sync<N>();
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     const int j = g + p * G;
@@ -266,12 +275,12 @@ __device__ __forceinline__ void fft_stage_rt(V* x, int g, const V* tws, bool act
       for (int r = 0; r < R; ++r) x[pidx<V>(base + r * ns)] = cnorm(v[p][r]);
     }
   }
-  __syncthreads();
+  stage_sync<N>();
 }
 
 // Transform the line at x (length N, padded layout) with G = FftPlan<N>::G threads
 // (g = 0..G-1).  Every thread of the CTA must call this (it contains barriers); the caller
-// syncs before.  Threads with active = false only take part in the barriers.  In double-word
+// syncs before, and the CTA is synchronised on return.  Threads with active = false only take part in the barriers.  In double-word
 // arithmetic (dw2 elements) leading stages of equal radix run as a loop over one copy of the
 // stage code: those butterflies are long, and unrolled copies of them overflow the
 // instruction cache.  The FP32 and FP64 forms keep every stage unrolled (their code is short,
@@ -293,6 +302,7 @@ __device__ __forceinline__ void line_fft(V* x, int g, const V* tws, bool active 
   }
   if constexpr (S > 1 && RUN < 2) fft_stage<V, N, SIGN, 1>(x, g, tws, active);
   if constexpr (S > 2 && RUN < 3) fft_stage<V, N, SIGN, 2>(x, g, tws, active);
+  if constexpr (warp_local<N>()) __syncthreads();
 }
 
 }  // namespace dns
