@@ -234,7 +234,8 @@ def run_ensemble(args):
     specs = ensemble_specs(args.count)
     t_end = args.t_end
     fields = [syn.random_solenoidal_hat(n, n, n, seed=i, k0=k0) for (n, k0, nu, i) in specs]
-    b = DnsBatch([dict(nx=n, nu=nu) for (n, k0, nu, i) in specs])
+    prec = args.precision
+    b = DnsBatch([dict(nx=n, nu=nu, precision=prec) for (n, k0, nu, i) in specs])
     tiles = [inst.autotune() for inst in b.instances]
     # warm-up: one short batched integration
     for inst, f in zip(b.instances, fields):
@@ -252,7 +253,7 @@ def run_ensemble(args):
     # the same instances, one after another through dns_integrate
     seq_s, seq_rhs = 0.0, 0
     for (n, k0, nu, i), f in zip(specs, fields):
-        d = Dns(n, nu=nu)
+        d = Dns(n, nu=nu, precision=prec)
         d.autotune()
         d.set_state(torch.from_numpy(f).cuda(), 0.0)
         torch.cuda.synchronize()
@@ -265,9 +266,10 @@ def run_ensemble(args):
     sim = len(specs) * t_end
     out = {"metric": METRIC, "value": n_rhs / batched_s, "unit": UNIT, "n_gpus": 1, "steps": 1,
            "warmup": 1, "ms_per_step": batched_s * 1e3, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "vs_baseline": None, "dtype": {"fp64": "f64", "fp32_mixed": "f32+f64", "fp32x2": "f32x2+f64"}[prec],
+           "data": "synthetic",
            "config": {"workload": f"ensemble_{len(specs)}x(24x64^3,24x96^3,16x128^3)_bs5_tol1e-6_to_t{t_end:g}",
-                      "tiles": tiles},
+                      "precision": prec, "tiles": tiles},
            "sim_time_per_gpu_s": sim / batched_s,
            "sequential": {"rhs_evals_per_s": seq_rhs / seq_s, "sim_time_per_gpu_s": sim / seq_s,
                           "seconds": seq_s},
