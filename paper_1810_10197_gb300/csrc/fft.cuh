@@ -125,12 +125,14 @@ template <int SIGN, typename V> struct Dft<4, SIGN, V> {
 template <int SIGN, typename V> __device__ __forceinline__ V w8_1(V a) {
   using T = decltype(V::x);
   const T r = (T)0.70710678118654752440;
-  return SIGN < 0 ? mk<V>((a.x + a.y) * r, (a.y - a.x) * r) : mk<V>((a.x - a.y) * r, (a.y + a.x) * r);
+  return SIGN < 0 ? mk<V>(bmul(badd(a.x, a.y), r), bmul(bsub(a.y, a.x), r))
+                  : mk<V>(bmul(bsub(a.x, a.y), r), bmul(badd(a.y, a.x), r));
 }
 template <int SIGN, typename V> __device__ __forceinline__ V w8_3(V a) {
   using T = decltype(V::x);
   const T r = (T)0.70710678118654752440;
-  return SIGN < 0 ? mk<V>((a.y - a.x) * r, -(a.x + a.y) * r) : mk<V>(-(a.x + a.y) * r, (a.x - a.y) * r);
+  return SIGN < 0 ? mk<V>(bmul(bsub(a.y, a.x), r), -bmul(badd(a.x, a.y), r))
+                  : mk<V>(-bmul(badd(a.x, a.y), r), bmul(bsub(a.x, a.y), r));
 }
 
 template <int SIGN, typename V> struct Dft<8, SIGN, V> {
