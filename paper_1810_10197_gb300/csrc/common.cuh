@@ -150,6 +150,11 @@ __device__ __forceinline__ dw dot2_u(dw a, dw b, dw c, dw d) {
 template <typename T> __device__ __forceinline__ T badd(T a, T b) { return a + b; }
 template <typename T> __device__ __forceinline__ T bsub(T a, T b) { return a - b; }
 template <typename T> __device__ __forceinline__ T bmul(T a, T b) { return a * b; }
+// a b + c d, and x / 2 (exact in every form)
+template <typename T> __device__ __forceinline__ T bdot2(T a, T b, T c, T d) { return fma(a, b, c * d); }
+template <typename T> __device__ __forceinline__ T bhalf(T x) { return x * (T)0.5; }
+template <> __device__ __forceinline__ dw bdot2<dw>(dw a, dw b, dw c, dw d) { return dot2_u(a, b, c, d); }
+template <> __device__ __forceinline__ dw bhalf<dw>(dw x) { return dw(__fmul_rn(x.hi, 0.5f), __fmul_rn(x.lo, 0.5f)); }
 template <> __device__ __forceinline__ dw badd<dw>(dw a, dw b) { return add_u(a, b); }
 template <> __device__ __forceinline__ dw bsub<dw>(dw a, dw b) { return add_u(a, -b); }
 template <> __device__ __forceinline__ dw bmul<dw>(dw a, dw b) { return mul_u(a, b); }

@@ -337,8 +337,8 @@ k_p3(const PassArgs a) {
       // Z_m = conj(s) + i conj(t) costs two more additions.
       const V s = cadd(xk, cconj(xm));
       const V t = cmul(cconj(tw[k]), csub(xk, cconj(xm)));
-      if (k != 0 && k != m) L[pidx<V>(m)] = mk<V>(s.x + t.y, t.x - s.y);
-      L[pidx<V>(k)] = mk<V>(s.x - t.y, s.y + t.x);
+      if (k != 0 && k != m) L[pidx<V>(m)] = mk<V>(badd(s.x, t.y), bsub(t.x, s.y));
+      L[pidx<V>(k)] = mk<V>(bsub(s.x, t.y), badd(s.y, t.x));
     }
   };
   // u x omega (and rho u) on both packed halves (real part: even z, imaginary part: odd z);
@@ -349,9 +349,9 @@ k_p3(const PassArgs a) {
       const int l = i / MZ, n = pidx<V>(i - l * MZ);
       const V u0 = lines[(0 * TL + l) * LD + n], u1 = lines[(1 * TL + l) * LD + n], u2 = lines[(2 * TL + l) * LD + n];
       const V w0 = lines[(3 * TL + l) * LD + n], w1 = lines[(4 * TL + l) * LD + n], w2 = lines[(5 * TL + l) * LD + n];
-      V p0 = mk<V>(u1.x * w2.x - u2.x * w1.x, u1.y * w2.y - u2.y * w1.y);
-      V p1 = mk<V>(u2.x * w0.x - u0.x * w2.x, u2.y * w0.y - u0.y * w2.y);
-      V p2 = mk<V>(u0.x * w1.x - u1.x * w0.x, u0.y * w1.y - u1.y * w0.y);
+      V p0 = mk<V>(bdot2(u1.x, w2.x, -u2.x, w1.x), bdot2(u1.y, w2.y, -u2.y, w1.y));
+      V p1 = mk<V>(bdot2(u2.x, w0.x, -u0.x, w2.x), bdot2(u2.y, w0.y, -u0.y, w2.y));
+      V p2 = mk<V>(bdot2(u0.x, w1.x, -u1.x, w0.x), bdot2(u0.y, w1.y, -u1.y, w0.y));
       if constexpr (CJ) { p0 = cconj(p0); p1 = cconj(p1); p2 = cconj(p2); }
       lines[(0 * TL + l) * LD + n] = p0;
       lines[(1 * TL + l) * LD + n] = p1;
@@ -401,9 +401,8 @@ k_p3(const PassArgs a) {
     if constexpr (SHARE) { zk = cconj(zk); zm = cconj(zm); }
     const V s = cadd(zk, cconj(zm)), d = csub(zk, cconj(zm));
     const V od = cmul(tw[k], d);                   // e^{-2 pi i k / nz} (Z_k - conj Z_{M-k})
-    const T hf = (T)0.5;
     // X = s/2 - (i/2) od
-    out[((size_t)c * nxy + xy) * Mz + k] = mk<V>(hf * (s.x + od.y), hf * (s.y - od.x));
+    out[((size_t)c * nxy + xy) * Mz + k] = mk<V>(bhalf(badd(s.x, od.y)), bhalf(bsub(s.y, od.x)));
   });
 }
 
