@@ -80,7 +80,7 @@ template <int N, int s> struct StageInfo {
 // Shared-memory layout of a line: element p sits at p + p / (128 B / element size), so
 // stride-R butterfly writes spread over all banks; LD is the (odd) line stride.
 template <typename V> __host__ __device__ constexpr int pad_shift() { return sizeof(V) == 8 ? 4 : 3; }
-template <typename V> __device__ __forceinline__ int pidx(int p) { return p + (p >> pad_shift<V>()); }
+template <typename V> __host__ __device__ __forceinline__ constexpr int pidx(int p) { return p + (p >> pad_shift<V>()); }
 template <typename V, int N> __host__ __device__ constexpr int line_ld() {
   return (N + (N >> pad_shift<V>())) | 1;
 }
@@ -189,6 +189,29 @@ template <int SIGN, typename V> struct Dft<16, SIGN, V> {
 
 // ---- one Stockham stage and the whole line transform ------------------------------------
 
+// Linear padded indexing.  A stage reads j + r B (j < B) and writes q + r NS with
+// q = (j - j mod NS) R + j mod NS.  When pidx(j + r B) = pidx(j) + pidx(r B) for every j, r
+// (and likewise for the writes), each element's padded index is one run-time base per
+// butterfly plus a compile-time offset: no per-element index arithmetic.  Power-of-two
+// strides satisfy this; stages next to a radix-3 stage may not, and keep the general form.
+// Checked exhaustively at compile time.
+template <typename V, int N, int s> __host__ __device__ constexpr bool stage_loads_linear() {
+  constexpr int R = StageInfo<N, s>::R, B = N / R;
+  for (int j = 0; j < B; ++j)
+    for (int r = 0; r < R; ++r)
+      if (pidx<V>(j + r * B) != pidx<V>(j) + pidx<V>(r * B)) return false;
+  return true;
+}
+template <typename V, int N, int s> __host__ __device__ constexpr bool stage_stores_linear() {
+  constexpr int R = StageInfo<N, s>::R, B = N / R, NS = StageInfo<N, s>::NS;
+  for (int j = 0; j < B; ++j) {
+    const int q = (j - j % NS) * R + j % NS;
+    for (int r = 0; r < R; ++r)
+      if (pidx<V>(q + r * NS) != pidx<V>(q) + pidx<V>(r * NS)) return false;
+  }
+  return true;
+}
+
 // The G threads of a line are consecutive (line = tid / G) and, when G divides 32, lie in one
 // warp: the stages of a line then need only warp-level ordering, and line_fft ends
 // with one block barrier for what the caller does next.
@@ -213,8 +236,14 @@ __device__ __forceinline__ void fft_stage(V* x, int g, const V* tws, bool active
   for (int p = 0; p < PER; ++p) {
     const int j = g + p * G;
     if (active && ((B % G == 0) || j < B)) {
+      if constexpr (stage_loads_linear<V, N, s>()) {
+        const V* xj = x + pidx<V>(j);
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[p][r] = x[pidx<V>(j + r * B)];
+        for (int r = 0; r < R; ++r) v[p][r] = xj[pidx<V>(r * B)];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[p][r] = x[pidx<V>(j + r * B)];
+      }
       if (NS > 1) {
         const int jm = j % NS;
         const V* t = tws + StageInfo<N, s>::TWOFF + jm * (R - 1) - 1;
@@ -234,8 +263,14 @@ __device__ __forceinline__ void fft_stage(V* x, int g, const V* tws, bool active
     if (active && ((B % G == 0) || j < B)) {
       const int jm = j % NS;
       const int base = (j - jm) * R + jm;
+      if constexpr (stage_stores_linear<V, N, s>()) {
+        V* xq = x + pidx<V>(base);
 #pragma unroll
-      for (int r = 0; r < R; ++r) x[pidx<V>(base + r * NS)] = cnorm(v[p][r]);
+        for (int r = 0; r < R; ++r) xq[pidx<V>(r * NS)] = cnorm(v[p][r]);
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[pidx<V>(base + r * NS)] = cnorm(v[p][r]);
+      }
     }
   }
   stage_sync<N>();
