@@ -220,6 +220,8 @@ template <int N> __device__ __forceinline__ void stage_sync() {
   if constexpr (warp_local<N>()) __syncwarp();
   else __syncthreads();
 }
+// ordering for work a line's own G threads did on it before line_fft
+template <int N> __device__ __forceinline__ void line_sync() { stage_sync<N>(); }
 
 // tws: the stage twiddle tables of this line length; stage s >= 1 holds, at
 // TWOFF + jm (R-1) + (r-1), exp(SIGN' 2 pi i jm r / (NS R)) with SIGN' = -1 (conjugated for

@@ -190,10 +190,13 @@ k_p1(const PassArgs a) {
     colk[2 * tid + 1] = sz * (T)kz;
   }
   __syncthreads();
-  for (int i = tid; i < g.Mx * TC; i += nth) {
-    const int ix = i / TC, c = i - ix * TC, col = col0 + c;
+  // thread tid owns column c = tid mod TC and rows r0 + k RS: constant strides, no division
+  constexpr int RS = NTH / TC;
+  const int c = tid % TC, r0 = tid / TC, col = col0 + c;
+  const bool ok = col < g.MyMz;
+  for (int ix = r0; ix < g.Mx; ix += RS) {
     V f0 = zero2<V>(), f1 = f0, f2 = f0;
-    if (col < g.MyMz) {
+    if (ok) {
       const size_t off = (size_t)ix * g.MyMz + col;
       const double2 d0 = Y[off], d1 = Y[off + g.M], d2 = Y[off + 2 * g.M];
       const V y0 = mk<V>(from_f64<T>(d0.x), from_f64<T>(d0.y));
@@ -250,37 +253,38 @@ k_py(const PassArgs a) {
   const int tid = threadIdx.x, nth = blockDim.x;
   const int Mz = g.Mz;
   copy_tw(tw, reinterpret_cast<const V*>(a.tw), NTW);
+  // The CTA has G TZ threads: thread tid owns column c = tid mod TZ and rows y0 + k G, so the
+  // element loops advance by constant strides (no per-element division).
+  const int c = tid % TZ, y0 = tid / TZ, kz = kz0 + c;
+  const bool ok = kz < Mz;
+  V* const line = lines + c * LD;
   if (INVERSE) {
-    for_rows<G * TZ>(TZ, NY - g.My, [&](int l, int q) { lines[l * LD + pidx<V>(g.Ky + 1 + q)] = zero2<V>(); });
-    const V* src = in + ((size_t)f * g.nx + x) * g.My * Mz;
-    for (int i = tid; i < g.My * TZ; i += nth) {
-      const int jy = i / TZ, c = i - jy * TZ, kz = kz0 + c;
-      const bool ok = kz < Mz;
-      cp_async_elem(&lines[c * LD + pidx<V>(jy <= g.Ky ? jy : NY - g.My + jy)], ok ? &src[(size_t)jy * Mz + kz] : src, ok);
+    // rows |ky| <= Ky from the retained box, the band between zero-filled
+    const V* src = in + ((size_t)f * g.nx + x) * g.My * Mz + (ok ? kz : 0);
+    const int Ky = g.Ky, shift = NY - g.My;
+    for (int y = y0; y < NY; y += G) {
+      const bool load = ok && (y <= Ky || y > Ky + shift);
+      const int jy = y <= Ky ? y : y - shift;
+      cp_async_elem(&line[pidx<V>(y)], load ? src + (size_t)jy * Mz : src, load);
     }
   } else {
-    const V* src = in + ((size_t)f * g.nx + x) * NY * Mz;
-    for (int i = tid; i < NY * TZ; i += nth) {
-      const int y = i / TZ, c = i - y * TZ, kz = kz0 + c;
-      const bool ok = kz < Mz;
-      cp_async_elem(&lines[c * LD + pidx<V>(y)], ok ? &src[(size_t)y * Mz + kz] : src, ok);
-    }
+    const V* src = in + ((size_t)f * g.nx + x) * NY * Mz + (ok ? kz : 0);
+    const size_t step = (size_t)G * Mz;
+    const V* sp = src + (size_t)y0 * Mz;
+    for (int y = y0; y < NY; y += G, sp += step) cp_async_elem(&line[pidx<V>(y)], ok ? sp : src, ok);
   }
   cp_async_wait();
   __syncthreads();
   line_fft<V, NY, INVERSE ? +1 : -1>(lines + (tid / G) * LD, tid % G, tw);
+  if (!ok) return;
   if (INVERSE) {
-    V* dst = out + ((size_t)f * g.nx + x) * NY * Mz;
-    for (int i = tid; i < NY * TZ; i += nth) {
-      const int y = i / TZ, c = i - y * TZ, kz = kz0 + c;
-      if (kz < Mz) dst[(size_t)y * Mz + kz] = lines[c * LD + pidx<V>(y)];
-    }
+    V* dp = out + ((size_t)f * g.nx + x) * NY * Mz + kz + (size_t)y0 * Mz;
+    const size_t step = (size_t)G * Mz;
+    for (int y = y0; y < NY; y += G, dp += step) *dp = line[pidx<V>(y)];
   } else {
-    V* dst = out + ((size_t)f * g.nx + x) * g.My * Mz;
-    for (int i = tid; i < g.My * TZ; i += nth) {
-      const int jy = i / TZ, c = i - jy * TZ, kz = kz0 + c;
-      if (kz < Mz) dst[(size_t)jy * Mz + kz] = lines[c * LD + pidx<V>(jy <= g.Ky ? jy : NY - g.My + jy)];
-    }
+    V* dst = out + ((size_t)f * g.nx + x) * g.My * Mz + kz;
+    const int Ky = g.Ky, shift = NY - g.My;
+    for (int jy = y0; jy < g.My; jy += G) dst[(size_t)jy * Mz] = line[pidx<V>(jy <= Ky ? jy : jy + shift)];
   }
 }
 
@@ -324,12 +328,11 @@ k_p3(const PassArgs a) {
   });
   cp_async_wait();
   __syncthreads();
-  // C2R pre-step on pairs (k, MZ-k), k = 0..MZ/2, of the NIN input lines
+  // C2R pre-step on pairs (k, MZ-k), k = 0..MZ/2, of the NIN input lines; each line by the G
+  // threads that transform it
   auto prestep = [&]() {
-    constexpr int NP = MZ / 2 + 1;
-    for (int i = tid; i < NIN * TL * NP; i += nth) {
-      const int l = i / NP, k = i - l * NP;
-      V* L = lines + l * LD;
+    V* L = lines + (tid / G) * LD;
+    for (int k = tid % G; k <= MZ / 2; k += G) {
       const int m = MZ - k;
       const V xk = L[pidx<V>(k)], xm = L[pidx<V>(m)];
       // s = X_k + conj X_m, t = e^{+2 pi i k/nz} (X_k - conj X_m); Z_k = s + i t.  The partner
@@ -377,15 +380,19 @@ k_p3(const PassArgs a) {
   if constexpr (SHARE) {
 #pragma unroll 1
     for (int ph = 0; ph < 2; ++ph) {
-      if (ph == 0) prestep();
-      else cross(std::true_type{});
-      __syncthreads();
+      if (ph == 0) {
+        prestep();
+        line_sync<MZ>();
+      } else {
+        cross(std::true_type{});
+        __syncthreads();
+      }
       const int nact = ph == 0 ? NIN * TL : NOUT * TL;
       line_fft<V, MZ, +1>(lines + (line < nact ? line : 0) * LD, tid % G, tws, line < nact);
     }
   } else {
     prestep();
-    __syncthreads();
+    line_sync<MZ>();
     line_fft<V, MZ, +1>(lines + line * LD, tid % G, tws);
     cross(std::false_type{});
     __syncthreads();
@@ -436,10 +443,17 @@ k_p5(const PassArgs a) {
   const int col0 = blockIdx.x * TC;
   const int tid = threadIdx.x, nth = blockDim.x;
   copy_tw(tw, reinterpret_cast<const V*>(a.tw), NTW);
-  for (int i = tid; i < NF * NX * TC; i += nth) {
-    const int f = i / (NX * TC), r = i - f * (NX * TC), x = r / TC, c = r - x * TC, col = col0 + c;
-    const bool ok = col < g.MyMz;
-    cp_async_elem(&lines[(f * TC + c) * LD + pidx<V>(x)], ok ? &in[((size_t)f * NX + x) * g.MyMz + col] : in, ok);
+  // thread tid owns column c = tid mod TC and rows r0 + k RS: constant strides, no division
+  constexpr int RS = G * NF;
+  const int cc = tid % TC, r0 = tid / TC, ccol = col0 + cc;
+  const bool cok = ccol < g.MyMz;
+  {
+    const V* ip = in + (size_t)r0 * g.MyMz + (cok ? ccol : 0);
+    const size_t istep = (size_t)RS * g.MyMz;
+    for (int row = r0; row < NF * NX; row += RS, ip += istep) {
+      const int f = row / NX, x = row - f * NX;
+      cp_async_elem(&lines[(f * TC + cc) * LD + pidx<V>(x)], cok ? ip : in, cok);
+    }
   }
   cp_async_wait();
   __syncthreads();
@@ -465,9 +479,9 @@ k_p5(const PassArgs a) {
   __syncthreads();
   const T kf2 = (T)a.kf2;
   const T fsc = (T)g.fwd_scale;
-  for (int i = tid; i < g.Mx * TC; i += nth) {
-    const int ix = i / TC, c = i - ix * TC, col = col0 + c;
-    if (col >= g.MyMz) continue;
+  const int c = cc, col = ccol;
+  if (!cok) return;
+  for (int ix = r0; ix < g.Mx; ix += RS) {
     const int pos = pidx<V>(ix <= g.Kx ? ix : NX - g.Mx + ix);
     V n0 = lines[(0 * TC + c) * LD + pos], n1 = lines[(1 * TC + c) * LD + pos], n2 = lines[(2 * TC + c) * LD + pos];
     if (fsc != (T)1) { n0 = cscale(n0, fsc); n1 = cscale(n1, fsc); n2 = cscale(n2, fsc); }
