@@ -162,7 +162,10 @@ DNS_API dns_status dns_step(dns_ctx* ctx, int method, double h, double rtol, dou
  * first proposal (adaptive); h0 <= 0 keeps the controller's current proposal.  The last step
  * is clipped to land on t_end.  max_rejects consecutive rejections (default 30 when <= 0)
  * end the run with DNS_ERR_MAX_REJECTS (DNS_ERR_NONFINITE if err was not finite).
- * Synchronous; fills info if non-NULL. */
+ * The attempts run as one CUDA graph launch (a device-side loop; at most 1e8 attempts, else
+ * DNS_ERR_STATE), built once per method and context and rebuilt after dns_set_tiles,
+ * dns_autotune or dns_set_trace; with dns_profile_enable on, attempts are enqueued from the
+ * host instead.  Synchronous; fills info if non-NULL. */
 DNS_API dns_status dns_integrate(dns_ctx* ctx, double t_end, int method, double rtol, double atol,
                          double h0, int max_rejects, dns_step_info* info);
 

@@ -124,6 +124,11 @@ struct dns_ctx {
   std::vector<ProfRec> recs;
   std::vector<cudaEvent_t> pool;
   size_t pool_used = 0;
+  // dns_integrate's graph per method: a conditional WHILE node around one attempt
+  cudaGraphExec_t gexec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaGraph_t graph[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t cap_stream = nullptr;
+  unsigned long long* d_iter = nullptr;
 };
 
 namespace {
@@ -370,6 +375,72 @@ dns_status ensure_stage(dns_ctx* c) {
   return alloc(c, (void**)&c->full_stage, bytes);
 }
 
+// The captured attempt bakes in the tile variants and whether the trace records diagnostics:
+// a change of either drops the cached graphs.
+void drop_graphs(dns_ctx* c) {
+  for (int m = 0; m < 5; ++m) {
+    if (c->gexec[m]) cudaGraphExecDestroy(c->gexec[m]);
+    if (c->graph[m]) cudaGraphDestroy(c->graph[m]);
+    c->gexec[m] = nullptr;
+    c->graph[m] = nullptr;
+  }
+}
+
+__global__ void k_ctx_continue(cudaGraphConditionalHandle h, const DnsCtrl* c, unsigned long long* iter,
+                               unsigned long long max_iter) {
+  const unsigned long long it = ++(*iter);
+  cudaGraphSetConditional(h, (!c->done && c->status == 0 && it < max_iter) ? 1u : 0u);
+}
+
+// Attempts until the controller reports done or a failure (at most 1e8), as one graph launch:
+// no host round trip per attempt.
+dns_status integrate_graph(dns_ctx* c, int method) {
+  if (!c->d_iter) {
+    dns_status s = alloc(c, (void**)&c->d_iter, sizeof(unsigned long long));
+    if (s != DNS_OK) return s;
+  }
+  if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream");
+  if (!c->gexec[method]) {
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0), "graph create");
+    cudaGraphConditionalHandle handle;
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = handle;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+    }
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(c->cap_stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(c, e, "graph build"); }
+    cudaStream_t user = c->stream;
+    c->stream = c->cap_stream;
+    dns_status st = enqueue_attempt(c, method);
+    if (st == DNS_OK) {
+      k_ctx_continue<<<1, 1, 0, c->cap_stream>>>(handle, c->ctrl, c->d_iter, 100000000ULL);
+      e = cudaGetLastError();
+    }
+    c->stream = user;
+    cudaGraph_t captured = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &captured);
+    if (st != DNS_OK || e != cudaSuccess || e2 != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return st != DNS_OK ? st : cuda_fail(c, e != cudaSuccess ? e : e2, "graph capture");
+    }
+    e = cudaGraphInstantiate(&c->gexec[method], g, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(c, e, "graph instantiate"); }
+    c->graph[method] = g;
+  }
+  CK(cudaMemsetAsync(c->d_iter, 0, sizeof(unsigned long long), c->stream), "reset counter");
+  CK(cudaGraphLaunch(c->gexec[method], c->stream), "graph launch");
+  return DNS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -492,9 +563,11 @@ void dns_destroy(dns_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
+  drop_graphs(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   void* ptrs[] = {c->uu[0], c->uu[1], c->kk[0], c->kk[1], c->ystage, c->rhs_in, c->rhs_out,
                   c->full_stage, c->bufA, c->bufB, c->tw[0], c->tw[1], c->tw[2], c->ctrl,
-                  c->ctrl_rhs, c->partials, c->trace_buf, c->mlp_buf};
+                  c->ctrl_rhs, c->partials, c->trace_buf, c->mlp_buf, c->d_iter};
   for (void* p : ptrs) if (p) cudaFree(p);
   for (int i = 2; i <= 7; ++i) if (c->kfix[i]) cudaFree(c->kfix[i]);
   if (c->host_ctrl) cudaFreeHost(c->host_ctrl);
@@ -597,6 +670,14 @@ dns_status dns_integrate(dns_ctx* c, double t_end, int method, double rtol, doub
   if ((s = read_ctrl(c)) != DNS_OK) return s;
   if (!(h0 > 0) && !(c->host_ctrl->h > 0)) return fail(c, DNS_ERR_ARG, "no step size: pass h0 > 0");
   if ((s = config(c, t_end, method, rtol, atol, h0, max_rejects)) != DNS_OK) return s;
+  if (!c->prof) {
+    // one graph launch runs every attempt (per-kernel profiling needs the host loop below)
+    if ((s = integrate_graph(c, method)) != DNS_OK) return s;
+    if ((s = read_ctrl(c)) != DNS_OK) return s;
+    if (!c->host_ctrl->done && c->host_ctrl->status == 0) return fail(c, DNS_ERR_STATE, "step limit reached");
+    fill_info(c, info);
+    return status_from_ctrl(c);
+  }
   const double cells = (double)c->g.nx * c->g.ny * c->g.nz;
   int chunk = (int)std::max(1.0, std::min(32.0, 4.0 * 1048576.0 / cells));
   long long guard = 0;
@@ -718,6 +799,7 @@ dns_status dns_set_trace(dns_ctx* c, long long capacity, int diagnostics) {
   if (capacity > 0 && (s = alloc(c, (void**)&c->trace_buf, (size_t)capacity * kTraceCols * sizeof(double))) != DNS_OK)
     return s;
   c->trace_diag = capacity > 0 && diagnostics != 0;
+  drop_graphs(c);
   CK(launch_ctrl_set_trace(c->ctrl, c->trace_buf, capacity, c->trace_diag, c->stream), "trace set");
   return DNS_OK;
 }
@@ -960,6 +1042,7 @@ dns_status dns_autotune(dns_ctx* c, int reps, int* variants) {
     tune_load_file();
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
+      if (c->var_py != it->second.first || c->var_p3 != it->second.second) drop_graphs(c);
       c->var_py = it->second.first;
       c->var_p3 = it->second.second;
       if (variants) { variants[0] = c->var_py; variants[1] = c->var_p3; }
@@ -995,6 +1078,7 @@ dns_status dns_autotune(dns_ctx* c, int reps, int* variants) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  drop_graphs(c);
   c->var_py = best[0][1] < best[0][0] ? 1 : 0;
   c->var_p3 = best[1][1] < best[1][0] ? 1 : 0;
   {
@@ -1008,6 +1092,7 @@ dns_status dns_autotune(dns_ctx* c, int reps, int* variants) {
 
 dns_status dns_set_tiles(dns_ctx* c, int var_py, int var_p3) {
   if (!c || var_py < 0 || var_py > 1 || var_p3 < 0 || var_p3 > 1) return DNS_ERR_ARG;
+  if (c->var_py != var_py || c->var_p3 != var_p3) drop_graphs(c);
   c->var_py = var_py;
   c->var_p3 = var_p3;
   return DNS_OK;

@@ -199,3 +199,33 @@ def test_energy_spectrum_matches_oracle():
     assert np.all(ref[len(Ek):] == 0)
     assert np.max(np.abs(Ek - ref[:len(Ek)])) < 1e-12 * np.max(ref)
     assert abs(Ek.sum() - diag.energy(g, uh)) < 1e-12
+
+
+def test_integrate_graph_matches_host_enqueued_attempts():
+    # dns_integrate runs its attempts as one graph launch; the same attempts enqueued one by
+    # one from the host (dns_enqueue_attempts) must give the identical state, bit for bit,
+    # also after a tile change rebuilds the graph and when a second call continues the run
+    shape, nu, tol = (32, 32, 32), 0.01, 1e-6
+    g = sp.Grid(*shape)
+    uh = g.dealias(syn.random_solenoidal_hat(*shape, seed=21, k0=3.0))
+    a = make(shape, uh, nu)
+    ia = a.integrate(0.2, "BS5_ADAPTIVE", tol, tol, h0=0.05)
+    a.set_tiles(1, 1)
+    ia2 = a.integrate(0.3, "BS5_ADAPTIVE", tol, tol, h0=0.0)
+    b = make(shape, uh, nu)
+    b.enqueue_attempts(ia.n_acc + ia.n_rej + 5, "BS5_ADAPTIVE", tol, tol, t_end=0.2, h0=0.05)
+    ib = b.info()
+    b.set_tiles(1, 1)
+    b.enqueue_attempts(ia2.n_acc + ia2.n_rej - ib.n_acc - ib.n_rej + 5, "BS5_ADAPTIVE", tol, tol, t_end=0.3)
+    ib2 = b.info()
+    assert (ia.t, ia.n_acc, ia.n_rej) == (ib.t, ib.n_acc, ib.n_rej)
+    assert (ia2.t, ia2.n_acc, ia2.n_rej, ia2.n_rhs) == (ib2.t, ib2.n_acc, ib2.n_rej, ib2.n_rhs)
+    assert a.get_state().tobytes() == b.get_state().tobytes()
+    # with per-kernel profiling on, the host loop gives the same result
+    c = make(shape, uh, nu)
+    c.profile_enable(True)
+    c.integrate(0.2, "BS5_ADAPTIVE", tol, tol, h0=0.05)
+    c.profile_enable(False)
+    d = make(shape, uh, nu)
+    d.integrate(0.2, "BS5_ADAPTIVE", tol, tol, h0=0.05)
+    assert c.get_state().tobytes() == d.get_state().tobytes()
