@@ -154,6 +154,25 @@ def dist_env():
     return ws, rank, local
 
 
+def shard(items, ws, rank):
+    """The units of an ensemble that rank `rank` of `ws` runs: every ws-th, from `rank` on.
+    The instances are independent, so the ranks exchange nothing while they run."""
+    return list(items)[rank::ws]
+
+
+def aggregate(dist, ws, ms, n_rhs, sim, device):
+    """Whole-job figures over the ranks: the slowest rank's time, the work summed."""
+    if ws <= 1:
+        return ms, float(n_rhs), sim
+    import torch
+    t = torch.tensor([ms, float(n_rhs), sim], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return mx[0].item(), sm[1].item(), sm[2].item()
+
+
 def cpu_sample(n_rhs=2, n_warm=1):
     """Oracle (FP64 numpy, one core) right-hand sides of the same 256^3 TG field."""
     import synthetic as syn
@@ -225,13 +244,18 @@ def run_ensemble(args):
     """Config: 64 independent simulations, BS5 adaptive tol 1e-6 each to t_end; one graph
     launch (dns_integrate_batch) against the same instances integrated one after another."""
     import torch
+    import torch.distributed as dist
 
     import synthetic as syn
     from paper_1810_10197_gb300 import Dns, build
     from paper_1810_10197_gb300.dns import DnsBatch
-    torch.cuda.set_device(0)
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
     build.build()
-    specs = ensemble_specs(args.count)
+    all_specs = ensemble_specs(args.count)
+    specs = shard(all_specs, ws, rank)      # each rank its own instances (weak scaling)
     t_end = args.t_end
     fields = [syn.random_solenoidal_hat(n, n, n, seed=i, k0=k0) for (n, k0, nu, i) in specs]
     prec = args.precision
@@ -263,20 +287,29 @@ def run_ensemble(args):
         seq_s += time.perf_counter() - t0
         seq_rhs += info.n_rhs
         d.close()
-    sim = len(specs) * t_end
-    out = {"metric": METRIC, "value": n_rhs / batched_s, "unit": UNIT, "n_gpus": 1, "steps": 1,
+    _, n_rej, _ = aggregate(dist, ws, 0.0, sum(i.n_rej for i in infos), 0.0, "cuda")
+    batched_s, n_rhs, _ = aggregate(dist, ws, batched_s, n_rhs, 0.0, "cuda")
+    seq_s, seq_rhs, _ = aggregate(dist, ws, seq_s, seq_rhs, 0.0, "cuda")
+    if rank != 0:
+        b.close()
+        dist.destroy_process_group()
+        return 0
+    sim = len(all_specs) * t_end
+    out = {"metric": METRIC, "value": n_rhs / batched_s, "unit": UNIT, "n_gpus": ws, "steps": 1,
            "warmup": 1, "ms_per_step": batched_s * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32_mixed": "f32+f64", "fp32x2": "f32x2+f64"}[prec],
            "data": "synthetic",
-           "config": {"workload": f"ensemble_{len(specs)}x(24x64^3,24x96^3,16x128^3)_bs5_tol1e-6_to_t{t_end:g}",
-                      "precision": prec, "tiles": tiles},
+           "config": {"workload": f"ensemble_{len(all_specs)}x(24x64^3,24x96^3,16x128^3)_bs5_tol1e-6_to_t{t_end:g}",
+                      "precision": prec, "tiles": tiles, "parallelism": f"instances sharded over {ws} rank(s)"},
            "sim_time_per_gpu_s": sim / batched_s,
            "sequential": {"rhs_evals_per_s": seq_rhs / seq_s, "sim_time_per_gpu_s": sim / seq_s,
                           "seconds": seq_s},
            "batched_seconds": batched_s, "speedup_vs_sequential": seq_s / batched_s,
-           "rhs_evals": n_rhs, "rejected": sum(i.n_rej for i in infos)}
+           "rhs_evals": int(n_rhs), "rejected": int(n_rej)}
     print(json.dumps(out), flush=True)
     b.close()
+    if ws > 1:
+        dist.destroy_process_group()
     return 0
 
 
@@ -538,13 +571,7 @@ def run_gpu(args):
     d.profile_enable(False)
     n_rhs = (i1.n_rhs - i0.n_rhs) if args.mode == "step" else args.steps
     sim = (i1.t - i0.t) if args.mode == "step" else 0.0
-    if ws > 1:
-        t = torch.tensor([ms, float(n_rhs), sim], dtype=torch.float64, device="cuda")
-        mx = t.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms_max, n_rhs_tot, sim_tot = mx[0].item(), sm[1].item(), sm[2].item()
-    else:
-        ms_max, n_rhs_tot, sim_tot = ms, float(n_rhs), sim
+    ms_max, n_rhs_tot, sim_tot = aggregate(dist, ws, ms, n_rhs, sim, "cuda")
     value = n_rhs_tot / (ms_max * 1e-3)
 
     # ---- end to end through the public API with host buffers (pinned) -------------------
