@@ -293,6 +293,13 @@ DNS_API dns_status dns_load(dns_ctx* ctx, const char* path);
  * PNG), continued from `crc` (0 to start).  Host-only; needs no GPU. */
 DNS_API unsigned int dns_crc32(const void* data, size_t n, unsigned int crc);
 
+/* Debug aid (the paper has no counterpart): with on != 0 both scratch buffers of the passes
+ * are filled with all-ones bytes -- a NaN in every element type -- before every right-hand
+ * side, so a pass that reads a scratch element that no earlier pass wrote makes the result NaN
+ * (a correct build gives results identical to a run without it).  Costs two memsets per
+ * right-hand side; takes effect for work enqueued after the call. */
+DNS_API dns_status dns_debug_poison(dns_ctx* ctx, int on);
+
 /* Grid facts: retained cut-offs K[3] and the number of device bytes the context holds. */
 DNS_API dns_status dns_query(const dns_ctx* ctx, int* K3, size_t* device_bytes);
 

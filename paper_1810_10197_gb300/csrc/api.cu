@@ -129,6 +129,7 @@ struct dns_ctx {
   cudaGraph_t graph[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   cudaStream_t cap_stream = nullptr;
   unsigned long long* d_iter = nullptr;
+  bool poison = false;             // dns_debug_poison: NaN-fill the scratch before each RHS
 };
 
 namespace {
@@ -220,6 +221,10 @@ cudaError_t pass(dns_ctx* c, int which, const PassArgs& a) {
 
 // One evaluation of Eq. (ufdef) on the stage input in `yslot`, result to `kslot`.
 dns_status enqueue_rhs(dns_ctx* c, DnsCtrl* ctrl, int yslot, int kslot, int gate_k1) {
+  if (c->poison) {   // all-ones bytes are a NaN in every element type
+    CK(cudaMemsetAsync(c->bufA, 0xFF, c->bytesA, c->stream), "poison");
+    CK(cudaMemsetAsync(c->bufB, 0xFF, c->bytesB, c->stream), "poison");
+  }
   if (c->forcing.kind == 1) {
     CK(timed(c, PR_FORCE, [&] {
          return launch_forcing_coef(c->g, ctrl, yslot, c->forcing.kf, c->forcing.power, gate_k1, c->stream);
@@ -1087,6 +1092,13 @@ dns_status dns_autotune(dns_ctx* c, int reps, int* variants) {
     tune_save(key, {c->var_py, c->var_p3});
   }
   if (variants) { variants[0] = c->var_py; variants[1] = c->var_p3; }
+  return DNS_OK;
+}
+
+dns_status dns_debug_poison(dns_ctx* c, int on) {
+  if (!c) return DNS_ERR_ARG;
+  if (c->poison != (on != 0)) drop_graphs(c);
+  c->poison = on != 0;
   return DNS_OK;
 }
 
