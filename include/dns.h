@@ -293,6 +293,13 @@ DNS_API dns_status dns_load(dns_ctx* ctx, const char* path);
  * PNG), continued from `crc` (0 to start).  Host-only; needs no GPU. */
 DNS_API unsigned int dns_crc32(const void* data, size_t n, unsigned int crc);
 
+/* Fault injection for tests (the paper has no counterpart; no GPU fault is involved): the
+ * right-hand side with running index rhs_index (0-based, counted like dns_step_info.n_rhs
+ * since dns_set_state) returns NaN in the (0,0,0) mode of its first component, once.  The
+ * embedded error of that attempt is then not finite, so the controller rejects it with the
+ * smallest factor (Section 2.2.1 reading) and the run goes on; rhs_index < 0 disarms. */
+DNS_API dns_status dns_debug_inject(dns_ctx* ctx, long long rhs_index);
+
 /* Debug aid (the paper has no counterpart): with on != 0 both scratch buffers of the passes
  * are filled with all-ones bytes -- a NaN in every element type -- before every right-hand
  * side, so a pass that reads a scratch element that no earlier pass wrote makes the result NaN

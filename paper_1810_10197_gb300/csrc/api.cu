@@ -546,11 +546,12 @@ static dns_status create_impl(const dns_config* cfg, int bouss, double kappa, do
     h.slot[SLOT_K1] = c->kk[0];
     for (int i = 2; i <= 7; ++i) h.slot[SLOT_K1 + i - 1] = c->kfix[i];
     h.slot[SLOT_K1 + 7] = c->kk[1];
-    h.done = 1; h.max_rejects = 30; h.method = DNS_BS5_ADAPTIVE;
+    h.done = 1; h.max_rejects = 30; h.method = DNS_BS5_ADAPTIVE; h.inject_rhs = -1;
     DnsCtrl r{};
     r.slot[SLOT_Y] = c->rhs_in;
     r.slot[SLOT_K1] = c->rhs_out;
     r.need_k1 = 1;
+    r.inject_rhs = -1;
     if (cudaMemcpy(c->ctrl, &h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->ctrl_rhs, &r, sizeof(r), cudaMemcpyHostToDevice) != cudaSuccess)
       s = DNS_ERR_CUDA;
@@ -1092,6 +1093,13 @@ dns_status dns_autotune(dns_ctx* c, int reps, int* variants) {
     tune_save(key, {c->var_py, c->var_p3});
   }
   if (variants) { variants[0] = c->var_py; variants[1] = c->var_p3; }
+  return DNS_OK;
+}
+
+dns_status dns_debug_inject(dns_ctx* c, long long rhs_index) {
+  dns_status s = check_ctx(c);
+  if (s != DNS_OK) return s;
+  CK(launch_ctrl_inject(c->ctrl, rhs_index < 0 ? -1 : rhs_index, c->stream), "inject");
   return DNS_OK;
 }
 

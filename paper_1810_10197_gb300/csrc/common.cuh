@@ -274,6 +274,7 @@ struct DnsCtrl {
   const float* mlp;     // network parameters of the learned proposal
   double* trace;        // [trace_cap][kTraceCols] attempt records
   long long trace_cap, trace_n;
+  long long inject_rhs;   // debug: the right-hand side with this running index returns NaN (-1: none)
 };
 
 // attempt record: t at the start, h used, err, accepted, n_rhs so far, E, Omega, eps

@@ -52,6 +52,7 @@ __global__ void k_na_setup(double2* base, int nx, int ny, int nz) {
     c->skip = 0;
     c->need_k1 = 1;
     c->forcing_coef = 0.0;
+    c->inject_rhs = -1;
   }
   const int n3[3] = {nx, ny, nz};
   for (int a = 0; a < 3; ++a) {

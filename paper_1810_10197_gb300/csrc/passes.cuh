@@ -512,6 +512,16 @@ k_p5(const PassArgs a) {
     K[off] = make_double2(fma(vis, y0.x, to_f64(n0.x)), fma(vis, y0.y, to_f64(n0.y)));
     K[off + g.M] = make_double2(fma(vis, y1.x, to_f64(n1.x)), fma(vis, y1.y, to_f64(n1.y)));
     K[off + 2 * g.M] = make_double2(fma(vis, y2.x, to_f64(n2.x)), fma(vis, y2.y, to_f64(n2.y)));
+    if (off == 0 && a.ctrl && a.kslot >= SLOT_K1 && a.ctrl->inject_rhs >= 0) {
+      // debug fault injection (dns_debug_inject): this evaluation's running index is the count
+      // before the attempt plus its position in the attempt (k_1 first when it is evaluated)
+      DnsCtrl* cw = const_cast<DnsCtrl*>(a.ctrl);
+      const long long idx = cw->n_rhs + (a.kslot - SLOT_K1) - (cw->need_k1 ? 0 : 1);
+      if (idx == cw->inject_rhs) {
+        K[0] = make_double2(__longlong_as_double(0x7ff8000000000000ULL), 0.0);
+        cw->inject_rhs = -1;
+      }
+    }
     if constexpr (BOUSS) {
       const V f0 = lines[(3 * TC + c) * LD + pos], f1 = lines[(4 * TC + c) * LD + pos], f2 = lines[(5 * TC + c) * LD + pos];
       V kd = mk<V>(kx * f0.x + ky * f1.x + kzz * f2.x, kx * f0.y + ky * f1.y + kzz * f2.y);

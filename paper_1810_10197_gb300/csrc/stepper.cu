@@ -334,7 +334,8 @@ __global__ void __launch_bounds__(kRedThreads) k_trace_finish(const Geom g, DnsC
 __global__ void k_ctrl_set(DnsCtrl* c, int what, int kind, const float* mlp, double* trace,
                            long long cap, int diag) {
   if (what == 0) { c->ctrl_kind = kind; c->mlp = mlp; c->hist_n = 0; }
-  else { c->trace = trace; c->trace_cap = cap; c->trace_n = 0; c->trace_diag = diag; }
+  else if (what == 1) { c->trace = trace; c->trace_cap = cap; c->trace_n = 0; c->trace_diag = diag; }
+  else { c->inject_rhs = cap; }
 }
 
 __global__ void k_ctrl_reset(DnsCtrl* c, double t) {
@@ -639,6 +640,11 @@ cudaError_t launch_ctrl_set_controller(DnsCtrl* c, int kind, const float* mlp, c
 
 cudaError_t launch_ctrl_set_trace(DnsCtrl* c, double* trace, long long cap, int diag, cudaStream_t s) {
   k_ctrl_set<<<1, 1, 0, s>>>(c, 1, 0, nullptr, trace, cap, diag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ctrl_inject(DnsCtrl* c, long long rhs_index, cudaStream_t s) {
+  k_ctrl_set<<<1, 1, 0, s>>>(c, 2, 0, nullptr, nullptr, rhs_index, 0);
   return cudaGetLastError();
 }
 

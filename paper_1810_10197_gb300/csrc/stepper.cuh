@@ -37,6 +37,7 @@ cudaError_t launch_begin_attempt(DnsCtrl* c, int method, cudaStream_t s);
 cudaError_t launch_controller(DnsCtrl* c, const double* partials, int method, int nstages,
                               double nmodes, int nc, cudaStream_t s);
 cudaError_t launch_ctrl_reset(DnsCtrl* c, double t, cudaStream_t s);
+cudaError_t launch_ctrl_inject(DnsCtrl* c, long long rhs_index, cudaStream_t s);
 cudaError_t launch_trace_diag(const Geom& g, DnsCtrl* c, double* partials, int method, cudaStream_t s);
 cudaError_t launch_ctrl_set_controller(DnsCtrl* c, int kind, const float* mlp, cudaStream_t s);
 cudaError_t launch_ctrl_set_trace(DnsCtrl* c, double* trace, long long cap, int diag, cudaStream_t s);

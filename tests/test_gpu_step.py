@@ -229,3 +229,45 @@ def test_integrate_graph_matches_host_enqueued_attempts():
     d = make(shape, uh, nu)
     d.integrate(0.2, "BS5_ADAPTIVE", tol, tol, h0=0.05)
     assert c.get_state().tobytes() == d.get_state().tobytes()
+
+
+@pytest.mark.parametrize("index", [17, 40])
+def test_injected_nan_is_rejected_and_the_run_recovers(index):
+    # a one-shot NaN in right-hand side `index` (host-armed, no GPU fault): the attempt's err
+    # is not finite, the controller rejects it with the smallest factor and the run finishes;
+    # the oracle with the same fault in the same evaluation takes the same decisions
+    shape, nu, tol, T = (32, 32, 32), 0.01, 1e-7, 0.3
+    g = sp.Grid(*shape)
+    uh = g.dealias(syn.random_solenoidal_hat(*shape, seed=8, k0=3.0))
+    calls = [0]
+
+    def f_inj(y):
+        out = sp.rhs(g, y, nu)
+        if calls[0] == index:
+            out = out.copy()
+            out[0, 0, 0, 0] = np.nan
+        calls[0] += 1
+        return out
+
+    ref = rk.integrate(f_inj, uh, 0.0, T, "BS5_ADAPTIVE", 0.01, tol, tol, nmodes=g.nmodes_half)
+    clean = rk.integrate(oracle_f(g, nu), uh, 0.0, T, "BS5_ADAPTIVE", 0.01, tol, tol, nmodes=g.nmodes_half)
+    assert ref.status == "ok" and ref.n_rej >= clean.n_rej + 1
+    assert any(not math.isfinite(e) for (_, _, e, _) in ref.history)
+    d = make(shape, uh, nu)
+    d.debug_inject(index)
+    info = d.integrate(T, "BS5_ADAPTIVE", tol, tol, h0=0.01)
+    assert info.t == T
+    assert (info.n_acc, info.n_rej, info.n_rhs) == (ref.n_acc, ref.n_rej, ref.n_rhs)
+    assert rel_l2(d.get_state(), ref.u) < 1e-12
+
+
+def test_injected_nan_in_a_carried_k1_ends_nonfinite():
+    # the very first evaluation is k_1 of u_0; a first-same-as-last pair reuses it after the
+    # rejection, so every retry fails: DNS_ERR_NONFINITE after max_rejects, as in the oracle
+    shape, nu = (16, 16, 16), 0.01
+    g = sp.Grid(*shape)
+    uh = g.dealias(syn.random_solenoidal_hat(*shape, seed=9, k0=3.0))
+    d = make(shape, uh, nu)
+    d.debug_inject(0)
+    st, info = d.integrate(1.0, "BS5_ADAPTIVE", 1e-6, 1e-6, h0=0.05, max_rejects=3, check=False)
+    assert st == 4 and info.n_rej == 4 and info.t == 0.0 and info.n_rhs == 8 + 3 * 7
