@@ -76,7 +76,8 @@ typedef enum { DNS_RK4 = 0, DNS_BS5_FIXED = 1, DNS_BS5_ADAPTIVE = 2, DNS_DP5_FIX
  * and the projection in double-word arithmetic -- each number an unevaluated sum of two FP32
  * values, about 48 significant bits (rounding near 2^-47 per operation instead of FP64's
  * 2^-53) at the FP32 instruction rate; state, stage sums, viscous term, error norm and step
- * control in double precision.  The paper fixes no precision; its runs were FP64. */
+ * control in double precision.  DNS_FP32X2 needs transform lengths of 32 or more on every
+ * axis (else DNS_ERR_UNSUPPORTED).  The paper fixes no precision; its runs were FP64. */
 typedef enum { DNS_FP64 = 0, DNS_FP32_MIXED = 1, DNS_FP32X2 = 2 } dns_precision;
 
 /* Forcing (Section 3.3.1 injects energy into 0 < |kappa| <= kf).  kind 0: none.  kind 1:

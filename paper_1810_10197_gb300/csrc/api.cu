@@ -478,9 +478,8 @@ static dns_status create_impl(const dns_config* cfg, int bouss, double kappa, do
   if (!supported(phys(cfg->nx)) || !supported(phys(cfg->ny)) || !supported(phys(cfg->nz))) return DNS_ERR_UNSUPPORTED;
   if (cfg->precision != DNS_FP64 && cfg->precision != DNS_FP32_MIXED && cfg->precision != DNS_FP32X2)
     return DNS_ERR_ARG;
-  // the double-word form: velocity only, transform lengths of 32 and more
-  if (cfg->precision == DNS_FP32X2 &&
-      (bouss || phys(cfg->nx) < 32 || phys(cfg->ny) < 32 || phys(cfg->nz) < 32))
+  // the double-word form: transform lengths of 32 and more
+  if (cfg->precision == DNS_FP32X2 && (phys(cfg->nx) < 32 || phys(cfg->ny) < 32 || phys(cfg->nz) < 32))
     return DNS_ERR_UNSUPPORTED;
   if (!(cfg->nu >= 0.0) || !std::isfinite(cfg->nu)) return DNS_ERR_ARG;
   if (cfg->forcing.kind < 0 || cfg->forcing.kind > 2) return DNS_ERR_ARG;

@@ -75,8 +75,8 @@ static cudaError_t launch_p3(const PassArgs& a, cudaStream_t s) {
 
 #define DNS_XY_SIZES(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768)
 #define DNS_ZH_SIZES(X) X(4) X(6) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384)
-// the double-word form: lines of 32 points and more, velocity only (its kernels are large;
-// every instantiation costs seconds of compile time)
+// the double-word form: lines of 32 points and more (its kernels are large; every
+// instantiation costs seconds of compile time)
 #define DNS_XY_SIZES_DW(X) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768)
 #define DNS_ZH_SIZES_DW(X) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384)
 
@@ -84,10 +84,12 @@ static cudaError_t launch_p3(const PassArgs& a, cudaStream_t s) {
 template <typename T, int WHICH>
 cudaError_t launch_pass_w(const PassArgs& a, cudaStream_t s) {
   if constexpr (is_dw<T>()) {
-    if (a.g.bouss) return cudaErrorInvalidValue;
     if constexpr (WHICH == 1 || WHICH == 5) {
       switch (a.g.nx) {
-#define CD(N) case N: return WHICH == 1 ? launch_p1<T, N, false>(a, s) : launch_p5<T, N, false>(a, s);
+#define CD(N)                                                                           \
+  case N:                                                                               \
+    if (WHICH == 1) return a.g.bouss ? launch_p1<T, N, true>(a, s) : launch_p1<T, N, false>(a, s); \
+    return a.g.bouss ? launch_p5<T, N, true>(a, s) : launch_p5<T, N, false>(a, s);
         DNS_XY_SIZES_DW(CD)
 #undef CD
       }
@@ -99,7 +101,7 @@ cudaError_t launch_pass_w(const PassArgs& a, cudaStream_t s) {
       }
     } else {
       switch (a.g.nz / 2) {
-#define CD(N) case N: return launch_p3<T, N, false>(a, s);
+#define CD(N) case N: return a.g.bouss ? launch_p3<T, N, true>(a, s) : launch_p3<T, N, false>(a, s);
         DNS_ZH_SIZES_DW(CD)
 #undef CD
       }

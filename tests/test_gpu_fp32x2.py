@@ -112,12 +112,43 @@ def test_ten_adaptive_steps():
     assert errs["fp32x2"] < 1e-12
 
 
-def test_unsupported_configurations_are_refused():
+def test_unsupported_sizes_are_refused():
     from paper_1810_10197_gb300 import Dns, DnsError
     for kw in ({"nx": 16}, {"nx": 32, "nz": 16}):
         with pytest.raises(DnsError) as ex:
             Dns(kw["nx"], 32, kw.get("nz", 32), nu=0.01, precision="fp32x2")
         assert ex.value.status == 9          # DNS_ERR_UNSUPPORTED
-    with pytest.raises(DnsError) as ex:
-        Dns(32, 32, 64, nu=0.01, precision="fp32x2", boussinesq=(0.01, 1.0))
-    assert ex.value.status == 9
+
+
+def test_boussinesq_rhs_and_steps():
+    # Section 3.2's Boussinesq right-hand side in the double-word form: one evaluation at the
+    # RHS bound, then 10 adaptive steps with identical decisions
+    from paper_1810_10197_gb300 import Dns
+    shape, nu, kap, ri = (32, 32, 64), 1e-2, 1e-2, 1.0
+    L = (2 * np.pi, 2 * np.pi, 4 * np.pi)
+    g = sp.Grid(*shape, lengths=L)
+    u = g.dealias(syn.random_solenoidal_hat(*shape, seed=3, k0=3.0))
+    r = g.dealias(syn.random_complex_hat(*shape, seed=4, ncomp=1)[0]) * 1e3
+    st = np.concatenate([u, r[None]])
+    fu, fr = sp.rhs_boussinesq(g, u, r, nu, kap, ri)
+    ref = np.concatenate([fu, fr[None]])
+    d = Dns(*shape, nu=nu, precision="fp32x2", boussinesq=(kap, ri), lengths=L)
+    x = to_dev(st)
+    f = torch.empty_like(x)
+    d.rhs(x, f)
+    torch.cuda.synchronize()
+    assert rel_max(f.cpu().numpy(), ref) < DW_TOL
+
+    def fb(y):
+        a, b = sp.rhs_boussinesq(g, y[:3], y[3], nu, kap, ri)
+        return np.concatenate([a, b[None]])
+    tol = 1e-6
+    res = rk.integrate(fb, g.dealias(st), 0.0, 1e9, "BS5_ADAPTIVE", 1e-3, tol, tol,
+                       nmodes=g.nmodes_half, max_steps=10)
+    d.set_state(x, 0.0)
+    d.enqueue_attempts(10, "BS5_ADAPTIVE", tol, tol, t_end=1e9, h0=1e-3)
+    info = d.info()
+    assert (info.n_acc, info.n_rej, info.n_rhs) == (res.n_acc, res.n_rej, res.n_rhs)
+    assert info.t == pytest.approx(res.t, rel=2e-10)
+    u_at = res.u + (info.t - res.t) * fb(res.u)
+    assert rel_l2(d.get_state(), u_at) < 1e-12
