@@ -469,8 +469,8 @@ def run_controllers(args):
     Yd = torch.from_numpy(Y).cuda()
     T_end = args.t_end
 
-    def run(kind, tol):
-        d = Dns(nx, ny, nz, nu=1e-3, lengths=L, boussinesq=(1e-3, 1.0))
+    def run(kind, tol, precision=args.precision):
+        d = Dns(nx, ny, nz, nu=1e-3, lengths=L, boussinesq=(1e-3, 1.0), precision=precision)
         d.autotune()
         d.set_state(Yd, 0.0)
         if kind == "MLP":
@@ -487,7 +487,7 @@ def run_controllers(args):
         d.close()
         return u, info, ev0.elapsed_time(ev1) * 1e-3, st
 
-    u_ref, i_ref, s_ref, _ = run("I", args.ref_tol)
+    u_ref, i_ref, s_ref, _ = run("I", args.ref_tol, "fp64")
     nrm = np.linalg.norm(u_ref)
     rows = {}
     for kind in ("I", "PI", "MLP"):
@@ -496,8 +496,11 @@ def run_controllers(args):
                       "rejected": int(info.n_rej), "l2_error": float(np.linalg.norm(u - u_ref) / nrm),
                       "gpu_seconds": sec, "sim_time_per_gpu_s": T_end / sec}
     out = {"metric": METRIC, "value": rows["MLP"]["sim_time_per_gpu_s"], "unit": "sim-time/GPU-s (MLP controller)",
-           "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+           "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True,
+           "dtype": {"fp64": "f64", "fp32_mixed": "f32+f64", "fp32x2": "f32x2+f64"}[args.precision],
+           "data": "synthetic",
            "config": {"workload": f"rayleigh_taylor_{nx}x{ny}x{nz}_atwood0.5_t0-{T_end:g}_bs5_tol1e-6",
+                      "precision": args.precision,
                       "reference": f"BS5 adaptive tol {args.ref_tol:g} (I controller)",
                       "reference_rhs_evals": int(i_ref.n_rhs), "training_pairs": int(len(X)),
                       "training_loss_first_last": [float(hist[:20].mean()), float(hist[-200:].mean())],
