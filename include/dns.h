@@ -59,7 +59,7 @@ typedef enum {
     DNS_ERR_NONFINITE = 4,       /* the error estimate stayed non-finite through max rejects */
     DNS_ERR_STEP_UNDERFLOW = 5,  /* step size fell below 1e-12 max(1,|t|)                   */
     DNS_ERR_MAX_REJECTS = 6,     /* more than max_rejects rejections in a row               */
-    DNS_ERR_TIMEOUT = 7,         /* reserved: a bounded device wait ran out                  */
+    DNS_ERR_TIMEOUT = 7,         /* a bounded device wait ran out (see dns_debug_stall)      */
     DNS_ERR_STATE = 8,           /* context failed earlier, or no state was set             */
     DNS_ERR_UNSUPPORTED = 9      /* grid size outside the supported set                     */
 } dns_status;
@@ -256,13 +256,19 @@ DNS_API dns_status dns_batch_context(dns_batch* batch, int i, dns_ctx** out);
 DNS_API dns_status dns_integrate_batch(dns_batch* batch, int method, const double* t_end, const double* rtol,
                                const double* atol, const double* h0, dns_step_info* info);
 
-/* Autotuner of the FFT tile shapes.  The y passes (columns per CTA) and the z pass (lines
- * per CTA) each have two compiled tile variants (0: full, 1: half); dns_autotune times
- * `reps` launches of each variant on this context's buffers with CUDA events on its stream,
- * keeps the faster one, and caches the choice per (grid, precision, form) for the process
- * and, if the environment variable DNS_TUNE_CACHE names a file, in that file (read on first
- * use, appended to).  variants (may be NULL) receives {y pass, z pass}.  dns_create_batch
- * tunes every instance.  dns_set_tiles sets the variants by hand.  Synchronous. */
+/* Autotuner of the FFT tile shapes.  The y passes (columns per CTA) have two compiled tile
+ * variants (0: full, 1: half).  The z pass has four codes: bit 0 the tile variant (lines per
+ * CTA, full or half), bit 1 set = input rows copied element by element instead of by bulk
+ * copies (the TMA engine, completing on a shared-memory barrier; used where a row is a
+ * multiple of 16 bytes and the staging fits in shared memory, else element copies anyway).
+ * dns_autotune times `reps` launches of each choice on this context's buffers with CUDA
+ * events on its stream, keeps the fastest, and caches the choice per (grid, precision, form)
+ * for the process and, if the environment variable DNS_TUNE_CACHE names a file, in that file
+ * (read on first use, appended to).  variants (may be NULL) receives {y pass, z pass code}.
+ * dns_create_batch tunes every instance.  dns_set_tiles sets them by hand (var_py 0..1,
+ * var_p3 0..3; the default is 0, 0).  Synchronous.
+ * A bulk copy's completion is awaited with a bound (about half a second); a wait that runs
+ * out marks the step controller DNS_ERR_TIMEOUT instead of hanging. */
 DNS_API dns_status dns_autotune(dns_ctx* ctx, int reps, int* variants);
 DNS_API dns_status dns_set_tiles(dns_ctx* ctx, int var_py, int var_p3);
 
@@ -300,6 +306,13 @@ DNS_API unsigned int dns_crc32(const void* data, size_t n, unsigned int crc);
  * embedded error of that attempt is then not finite, so the controller rejects it with the
  * smallest factor (Section 2.2.1 reading) and the run goes on; rhs_index < 0 disarms. */
 DNS_API dns_status dns_debug_inject(dns_ctx* ctx, long long rhs_index);
+
+/* Test hook for the bounded wait (the paper has no counterpart; no GPU fault is involved):
+ * the next z pass enqueued from the host (dns_step, dns_rhs, dns_enqueue_attempts; not the
+ * graph of dns_integrate) makes its first CTA wait for 16 bytes that no bulk copy delivers,
+ * so that CTA's bounded wait runs out: the attempt ends with DNS_ERR_TIMEOUT and the context
+ * stays usable.  One-shot; no effect when the z pass copies element by element. */
+DNS_API dns_status dns_debug_stall(dns_ctx* ctx);
 
 /* Debug aid (the paper has no counterpart): with on != 0 both scratch buffers of the passes
  * are filled with all-ones bytes -- a NaN in every element type -- before every right-hand

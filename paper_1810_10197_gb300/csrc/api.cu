@@ -119,6 +119,9 @@ struct dns_ctx {
   int trace_diag = 0;
   float* mlp_buf = nullptr;        // learned-controller parameters (dns_set_controller)
   int var_py = 0, var_p3 = 0;      // tile variants (dns_autotune)
+  int p3_bulk = 1;                 // z pass input by bulk copies where possible (dns_autotune)
+  bool stall_pending = false;      // dns_debug_stall: the next host-enqueued z pass stalls
+  bool capturing = false;          // building dns_integrate's graph
   size_t bytesA = 0, bytesB = 0;   // sizes of the scratch buffers A and B
   bool prof = false;
   std::vector<ProfRec> recs;
@@ -242,6 +245,11 @@ dns_status enqueue_rhs(dns_ctx* c, DnsCtrl* ctrl, int yslot, int kslot, int gate
   a.ri = c->ri;
   a.var_py = c->var_py;
   a.var_p3 = c->var_p3;
+  a.p3_bulk = c->p3_bulk;
+  if (c->stall_pending && !c->capturing) {
+    a.p3_stall = 16;
+    c->stall_pending = false;
+  }
   a.out = c->bufA; a.tw = c->tw[0];
   CK(timed(c, PR_P1, [&] { return pass(c, 1, a); }), "pass P1");
   a.in = c->bufA; a.out = c->bufB; a.tw = c->tw[1];
@@ -370,6 +378,7 @@ dns_status status_from_ctrl(dns_ctx* c) {
     case ST_NONFINITE: return fail(c, DNS_ERR_NONFINITE, "error estimate not finite through max_rejects retries");
     case ST_UNDERFLOW: return fail(c, DNS_ERR_STEP_UNDERFLOW, "step size underflow");
     case ST_MAX_REJECTS: return fail(c, DNS_ERR_MAX_REJECTS, "too many rejected steps in a row");
+    case ST_TIMEOUT: return fail(c, DNS_ERR_TIMEOUT, "a bounded device wait ran out (z-pass bulk copies)");
   }
   return fail(c, DNS_ERR_STATE, "unknown device status");
 }
@@ -425,7 +434,9 @@ dns_status integrate_graph(dns_ctx* c, int method) {
     if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(c, e, "graph build"); }
     cudaStream_t user = c->stream;
     c->stream = c->cap_stream;
+    c->capturing = true;
     dns_status st = enqueue_attempt(c, method);
+    c->capturing = false;
     if (st == DNS_OK) {
       k_ctx_continue<<<1, 1, 0, c->cap_stream>>>(handle, c->ctrl, c->d_iter, 100000000ULL);
       e = cudaGetLastError();
@@ -1047,10 +1058,12 @@ dns_status dns_autotune(dns_ctx* c, int reps, int* variants) {
     tune_load_file();
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      if (c->var_py != it->second.first || c->var_p3 != it->second.second) drop_graphs(c);
+      const int z = it->second.second;
+      if (c->var_py != it->second.first || c->var_p3 != (z & 1) || c->p3_bulk != !(z & 2)) drop_graphs(c);
       c->var_py = it->second.first;
-      c->var_p3 = it->second.second;
-      if (variants) { variants[0] = c->var_py; variants[1] = c->var_p3; }
+      c->var_p3 = z & 1;
+      c->p3_bulk = !(z & 2);
+      if (variants) { variants[0] = c->var_py; variants[1] = z; }
       return DNS_OK;
     }
   }
@@ -1065,11 +1078,14 @@ dns_status dns_autotune(dns_ctx* c, int reps, int* variants) {
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0), "event");
   CK(cudaEventCreate(&e1), "event");
-  float best[2][2] = {{0, 0}, {0, 0}};
+  // y pass: tile variants 0, 1; z pass: codes 0..3 (bit 0 tile variant, bit 1 per-element
+  // copies instead of bulk copies)
+  float best[2][4] = {{0, 0, 1e30f, 1e30f}, {0, 0, 0, 0}};
   for (int which = 0; which < 2; ++which) {        // 0: y pass (P2), 1: z pass (P3)
-    for (int v = 0; v < 2; ++v) {
+    for (int v = 0; v < (which == 0 ? 2 : 4); ++v) {
       a.var_py = which == 0 ? v : 0;
-      a.var_p3 = which == 1 ? v : 0;
+      a.var_p3 = which == 1 ? (v & 1) : 0;
+      a.p3_bulk = which == 1 ? !(v & 2) : 1;
       if (which == 0) { a.in = c->bufA; a.out = c->bufB; a.tw = c->tw[1]; }
       else { a.in = c->bufB; a.out = c->bufA; a.tw = c->tw[2]; }
       const int pass_id = which == 0 ? 2 : 3;
@@ -1085,13 +1101,16 @@ dns_status dns_autotune(dns_ctx* c, int reps, int* variants) {
   cudaEventDestroy(e1);
   drop_graphs(c);
   c->var_py = best[0][1] < best[0][0] ? 1 : 0;
-  c->var_p3 = best[1][1] < best[1][0] ? 1 : 0;
+  int z = 0;
+  for (int v = 1; v < 4; ++v) if (best[1][v] < best[1][z]) z = v;
+  c->var_p3 = z & 1;
+  c->p3_bulk = !(z & 2);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[key] = {c->var_py, c->var_p3};
-    tune_save(key, {c->var_py, c->var_p3});
+    g_tune[key] = {c->var_py, z};
+    tune_save(key, {c->var_py, z});
   }
-  if (variants) { variants[0] = c->var_py; variants[1] = c->var_p3; }
+  if (variants) { variants[0] = c->var_py; variants[1] = z; }
   return DNS_OK;
 }
 
@@ -1099,6 +1118,12 @@ dns_status dns_debug_inject(dns_ctx* c, long long rhs_index) {
   dns_status s = check_ctx(c);
   if (s != DNS_OK) return s;
   CK(launch_ctrl_inject(c->ctrl, rhs_index < 0 ? -1 : rhs_index, c->stream), "inject");
+  return DNS_OK;
+}
+
+dns_status dns_debug_stall(dns_ctx* c) {
+  if (!c) return DNS_ERR_ARG;
+  c->stall_pending = true;
   return DNS_OK;
 }
 
@@ -1110,10 +1135,11 @@ dns_status dns_debug_poison(dns_ctx* c, int on) {
 }
 
 dns_status dns_set_tiles(dns_ctx* c, int var_py, int var_p3) {
-  if (!c || var_py < 0 || var_py > 1 || var_p3 < 0 || var_p3 > 1) return DNS_ERR_ARG;
-  if (c->var_py != var_py || c->var_p3 != var_p3) drop_graphs(c);
+  if (!c || var_py < 0 || var_py > 1 || var_p3 < 0 || var_p3 > 3) return DNS_ERR_ARG;
+  if (c->var_py != var_py || c->var_p3 != (var_p3 & 1) || c->p3_bulk != !(var_p3 & 2)) drop_graphs(c);
   c->var_py = var_py;
-  c->var_p3 = var_p3;
+  c->var_p3 = var_p3 & 1;
+  c->p3_bulk = !(var_p3 & 2);
   return DNS_OK;
 }
 

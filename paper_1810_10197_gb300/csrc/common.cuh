@@ -311,6 +311,6 @@ __device__ __forceinline__ bool gated_off(const DnsCtrl* c, int only_if_need_k1)
   return only_if_need_k1 && !c->need_k1;
 }
 
-enum DnsStatusDev : int { ST_OK = 0, ST_NONFINITE = 4, ST_UNDERFLOW = 5, ST_MAX_REJECTS = 6 };
+enum DnsStatusDev : int { ST_OK = 0, ST_NONFINITE = 4, ST_UNDERFLOW = 5, ST_MAX_REJECTS = 6, ST_TIMEOUT = 7 };
 
 }  // namespace dns

@@ -39,7 +39,39 @@ struct PassArgs {
   double ri;             // Richardson number (Boussinesq)
   int var_py;            // tile variant of the y passes (0: full, 1: half width), autotuned
   int var_p3;            // tile variant of the z pass (0: full, 1: half the lines), autotuned
+  int p3_bulk;           // z pass: stage input rows with bulk copies (rows a multiple of 16 B)
+  int p3_stall;          // debug: block 0's bulk-copy barrier expects this many extra bytes
 };
+
+// ---- bulk copies (TMA engine) completing on a CTA-local mbarrier ---------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// global -> shared, `bytes` a multiple of 16, both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+               : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after about half a second (1e9 clock cycles) or 2^24 polls.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+  const long long t0 = clock64();
+  for (int it = 0; it < (1 << 24); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (clock64() - t0 > 1000000000LL) return false;
+  }
+  return false;
+}
 
 // Column tiles: kz-contiguous columns handled per CTA in the x and y passes (128-byte rows),
 // and z lines per CTA in the z pass.
@@ -295,6 +327,11 @@ k_py(const PassArgs a) {
 //   C2R pre-step : Z_k = (X_k + conj X_{M-k}) + i e^{+2 pi i k/nz} (X_k - conj X_{M-k})
 //   R2C post-step: X_k = (Z_k + conj Z_{M-k})/2 - (i/2) e^{-2 pi i k/nz} (Z_k - conj Z_{M-k})
 // ------------------------------------------------------------------------------------------
+// byte offset of the z pass's staging rows: after `elems` elements of V, rounded up to 16
+template <typename V> __host__ __device__ constexpr size_t p3_stage_offset(size_t elems) {
+  return (elems * sizeof(V) + 15) / 16 * 16;
+}
+
 template <typename T, int MZ, bool BOUSS, int VAR>
 __global__ void __launch_bounds__(FftPlan<MZ>::G * (BOUSS ? 7 : 6) * p3_lines<T, MZ, BOUSS, VAR>())
 k_p3(const PassArgs a) {
@@ -318,23 +355,57 @@ k_p3(const PassArgs a) {
   const int Mz = g.Mz;
   const int tid = threadIdx.x, nth = blockDim.x;
   constexpr int NTH = G * NIN * TL;
+  // bulk path: unpadded staging rows [NIN TL][Mz] after the lines (16-byte aligned), then the
+  // mbarrier; the C2R pre-step reads the staging rows
+  V* stage = reinterpret_cast<V*>(smem_raw + p3_stage_offset<V>(NTW + NIN * TL * LD));
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(stage + (size_t)NIN * TL * Mz);
+  const bool bulk = a.p3_bulk != 0;
+  if (bulk && tid == 0) mbar_init(bar, 1);
   copy_tw(tw, reinterpret_cast<const V*>(a.tw), NTW);
-  // rows (field, line): kz < Mz from memory, Mz..MZ zero
-  for_rows<NTH>(NIN * TL, MZ + 1, [&](int row, int kz) {
-    const int f = row / TL, l = row - f * TL;
-    const long long xy = xy0 + l;
-    const bool ok = kz < Mz && xy < nxy;
-    cp_async_elem(&lines[row * LD + pidx<V>(kz)], ok ? &in[((size_t)f * nxy + xy) * Mz + kz] : in, ok);
-  });
-  cp_async_wait();
-  __syncthreads();
+  if (bulk) {
+    __syncthreads();
+    if (tid == 0) {
+      const unsigned row_bytes = (unsigned)(Mz * sizeof(V));
+      const long long rows_here = (nxy - xy0) < TL ? (nxy - xy0) : TL;
+      const unsigned extra = blockIdx.x == 0 ? (unsigned)a.p3_stall : 0u;
+      mbar_expect_tx(bar, (unsigned)(NIN * rows_here) * row_bytes + extra);
+      for (int f = 0; f < NIN; ++f)
+        for (int l = 0; l < rows_here; ++l)
+          bulk_g2s(stage + (size_t)(f * TL + l) * Mz, in + ((size_t)f * nxy + xy0 + l) * Mz, row_bytes, bar);
+    }
+    // every thread polls (bounded); the block agrees on the outcome
+    const bool arrived = mbar_wait_bounded(bar, 0);
+    if (!__syncthreads_and(arrived)) {
+      if (tid == 0) {
+        if (a.ctrl) {
+          DnsCtrl* cw = const_cast<DnsCtrl*>(a.ctrl);
+          cw->status = ST_TIMEOUT;
+          cw->done = 1;
+        }
+        mbar_wait_bounded(bar, 0);   // let copies still in flight land before the block exits
+      }
+      return;
+    }
+  } else {
+    // rows (field, line): kz < Mz from memory, Mz..MZ zero
+    for_rows<NTH>(NIN * TL, MZ + 1, [&](int row, int kz) {
+      const int f = row / TL, l = row - f * TL;
+      const long long xy = xy0 + l;
+      const bool ok = kz < Mz && xy < nxy;
+      cp_async_elem(&lines[row * LD + pidx<V>(kz)], ok ? &in[((size_t)f * nxy + xy) * Mz + kz] : in, ok);
+    });
+    cp_async_wait();
+    __syncthreads();
+  }
   // C2R pre-step on pairs (k, MZ-k), k = 0..MZ/2, of the NIN input lines; each line by the G
   // threads that transform it
   auto prestep = [&]() {
     V* L = lines + (tid / G) * LD;
+    const V* S = stage + (size_t)(tid / G) * Mz;
     for (int k = tid % G; k <= MZ / 2; k += G) {
       const int m = MZ - k;
-      const V xk = L[pidx<V>(k)], xm = L[pidx<V>(m)];
+      const V xk = bulk ? (k < Mz ? S[k] : zero2<V>()) : L[pidx<V>(k)];
+      const V xm = bulk ? (m < Mz ? S[m] : zero2<V>()) : L[pidx<V>(m)];
       // s = X_k + conj X_m, t = e^{+2 pi i k/nz} (X_k - conj X_m); Z_k = s + i t.  The partner
       // k' = m has s' = conj s and t' = conj t (e^{+2 pi i m/nz} = -e^{-2 pi i k/nz}), so
       // Z_m = conj(s) + i conj(t) costs two more additions.

@@ -60,12 +60,20 @@ static cudaError_t launch_p3_v(const PassArgs& a, cudaStream_t s) {
   using V = v2_t<T>;
   constexpr int TL = p3_lines<T, MZ, B, VAR>();
   constexpr int NIN = B ? 7 : 6;
-  const size_t smem = (size_t)(twiddle_count_z(2 * MZ) + NIN * TL * p3_ld<V, MZ>()) * sizeof(V);
+  const size_t lines_elems = (size_t)twiddle_count_z(2 * MZ) + NIN * TL * p3_ld<V, MZ>();
+  size_t smem = lines_elems * sizeof(V);
+  // bulk path: staging rows and the mbarrier, when a row is a multiple of 16 bytes and the
+  // whole fits in a CTA's shared memory
+  const size_t smem_bulk = p3_stage_offset<V>(lines_elems) + (size_t)NIN * TL * a.g.Mz * sizeof(V) + 16;
+  PassArgs b = a;
+  b.p3_bulk = a.p3_bulk && (a.g.Mz * sizeof(V)) % 16 == 0 && smem_bulk <= 232448;
+  if (!b.p3_bulk) b.p3_stall = 0;
+  if (b.p3_bulk) smem = smem_bulk;
   cudaError_t e = set_smem(k_p3<T, MZ, B, VAR>, smem);
   if (e != cudaSuccess) return e;
   const long long nxy = (long long)a.g.nx * a.g.ny;
   dim3 grid((unsigned)((nxy + TL - 1) / TL));
-  k_p3<T, MZ, B, VAR><<<grid, FftPlan<MZ>::G * NIN * TL, smem, s>>>(a);
+  k_p3<T, MZ, B, VAR><<<grid, FftPlan<MZ>::G * NIN * TL, smem, s>>>(b);
   return cudaGetLastError();
 }
 template <typename T, int MZ, bool B>

@@ -106,6 +106,7 @@ _SIGS.update({
                                       C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(dns_step_info)]),
     "dns_debug_poison": (C.c_int, [C.c_void_p, C.c_int]),
     "dns_debug_inject": (C.c_int, [C.c_void_p, C.c_longlong]),
+    "dns_debug_stall": (C.c_int, [C.c_void_p]),
     "dns_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "dns_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "dns_crc32": (C.c_uint, [C.c_void_p, C.c_size_t, C.c_uint]),
@@ -345,6 +346,9 @@ class Dns:
 
     def debug_inject(self, rhs_index):
         self._check(self._lib.dns_debug_inject(self._h, int(rhs_index)), "dns_debug_inject")
+
+    def debug_stall(self):
+        self._check(self._lib.dns_debug_stall(self._h), "dns_debug_stall")
 
     def debug_poison(self, on=True):
         self._check(self._lib.dns_debug_poison(self._h, 1 if on else 0), "dns_debug_poison")
