@@ -282,7 +282,7 @@ k_py(const PassArgs a) {
   const V* __restrict__ in = reinterpret_cast<const V*>(a.in);
   V* __restrict__ out = reinterpret_cast<V*>(a.out);
   const int f = blockIdx.z, x = blockIdx.y, kz0 = blockIdx.x * TZ;
-  const int tid = threadIdx.x, nth = blockDim.x;
+  const int tid = threadIdx.x;
   const int Mz = g.Mz;
   copy_tw(tw, reinterpret_cast<const V*>(a.tw), NTW);
   // The CTA has G TZ threads: thread tid owns column c = tid mod TZ and rows y0 + k G, so the
