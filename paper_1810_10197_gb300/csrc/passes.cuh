@@ -164,17 +164,20 @@ __device__ __forceinline__ void copy_tw(V* dst, const V* __restrict__ src, int n
 }
 
 // ------------------------------------------------------------------------------------------
-// P1: x-inverse with the curl fused in.  grid (ceil(MyMz/TC), 2 or 3): y = 0 -> u,
-// 1 -> omega, 2 -> density (Boussinesq: one field over 3 TC columns, output field 6).
+// P1: x-inverse with the curl fused in.  grid (ceil(MyMz/(TC/2)), 1 or 2): y = 0 -> the six
+// lines u, omega of TC/2 columns (the state is read and converted once per mode), y = 1 ->
+// density (Boussinesq: one field over 3 TC columns, output field 6).
 // ------------------------------------------------------------------------------------------
 template <typename T, int NX, bool BOUSS>
 __global__ void __launch_bounds__(FftPlan<NX>::G * 3 * p1_cols<T, NX>())
 k_p1(const PassArgs a) {
   using V = v2_t<T>;
   constexpr int TC = p1_cols<T, NX>();
+  constexpr int TC2 = TC / 2;                  // columns of the u, omega blocks (6 lines each)
   constexpr int G = FftPlan<NX>::G;
   constexpr int LD = line_ld<V, NX>();
   constexpr int NTW = twiddle_count_xy(NX);
+  static_assert(TC % 2 == 0, "x-inverse tiles hold an even number of columns");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw = reinterpret_cast<V*>(smem_raw);
   V* lines = tw + NTW;
@@ -182,20 +185,18 @@ k_p1(const PassArgs a) {
   const Geom& g = a.g;
   const double2* __restrict__ Y = resolve_in(a.y, a.ctrl, a.yslot);
   V* __restrict__ out = reinterpret_cast<V*>(a.out);
-  const int half = blockIdx.y;
-  const int col0 = blockIdx.x * TC;
   const int tid = threadIdx.x, nth = blockDim.x;
   constexpr int NTH = G * 3 * TC;
-  T* colk = reinterpret_cast<T*>(lines + 3 * TC * LD);   // ky, kz of each column
+  T* colk = reinterpret_cast<T*>(lines + 6 * TC2 * LD);   // ky, kz of each column
   copy_tw(tw, reinterpret_cast<const V*>(a.tw), NTW);
-  for_rows<NTH>(3 * TC, NX - g.Mx, [&](int l, int q) { lines[l * LD + pidx<V>(g.Kx + 1 + q)] = zero2<V>(); });
   const T s = (T)g.inv_n3;
   const T sx = (T)g.sx, sy = (T)g.sy, sz = (T)g.sz;
   if constexpr (BOUSS) {
-    if (half == 2) {   // density: lines are 3 TC columns of one field
+    if (blockIdx.y == 1) {   // density: lines are 3 TC columns of one field
       constexpr int TC3 = 3 * TC;
       const int c0 = blockIdx.x * TC3;
       if (c0 >= g.MyMz) return;   // uniform over the CTA, before any barrier
+      for_rows<NTH>(TC3, NX - g.Mx, [&](int l, int q) { lines[l * LD + pidx<V>(g.Kx + 1 + q)] = zero2<V>(); });
       __syncthreads();
       for (int i = tid; i < g.Mx * TC3; i += nth) {
         const int ix = i / TC3, c = i - ix * TC3, col = c0 + c;
@@ -215,50 +216,51 @@ k_p1(const PassArgs a) {
       return;
     }
   }
-  if (tid < TC) {
+  const int col0 = blockIdx.x * TC2;
+  for_rows<NTH>(6 * TC2, NX - g.Mx, [&](int l, int q) { lines[l * LD + pidx<V>(g.Kx + 1 + q)] = zero2<V>(); });
+  if (tid < TC2) {
     const int col = min(col0 + tid, g.MyMz - 1);
     const int jy = col / g.Mz, kz = col - jy * g.Mz;
     colk[2 * tid] = sy * (T)signed_mode(jy, g.Ky, g.My);
     colk[2 * tid + 1] = sz * (T)kz;
   }
   __syncthreads();
-  // thread tid owns column c = tid mod TC and rows r0 + k RS: constant strides, no division
-  constexpr int RS = NTH / TC;
-  const int c = tid % TC, r0 = tid / TC, col = col0 + c;
+  // thread tid owns column c = tid mod TC2 and modes r0 + k RS: constant strides, no division
+  constexpr int RS = NTH / TC2;
+  const int c = tid % TC2, r0 = tid / TC2, col = col0 + c;
   const bool ok = col < g.MyMz;
+  const T ky = colk[2 * c], kzz = colk[2 * c + 1];
   for (int ix = r0; ix < g.Mx; ix += RS) {
-    V f0 = zero2<V>(), f1 = f0, f2 = f0;
+    V u0 = zero2<V>(), u1 = u0, u2 = u0, w0 = u0, w1 = u0, w2 = u0;
     if (ok) {
       const size_t off = (size_t)ix * g.MyMz + col;
       const double2 d0 = Y[off], d1 = Y[off + g.M], d2 = Y[off + 2 * g.M];
       const V y0 = mk<V>(from_f64<T>(d0.x), from_f64<T>(d0.y));
       const V y1 = mk<V>(from_f64<T>(d1.x), from_f64<T>(d1.y));
       const V y2 = mk<V>(from_f64<T>(d2.x), from_f64<T>(d2.y));
-      if (half == 0) {
-        f0 = cscale(y0, s); f1 = cscale(y1, s); f2 = cscale(y2, s);
-      } else {
-        const T kx = sx * (T)signed_mode(ix, g.Kx, g.Mx);
-        const T ky = colk[2 * c], kzz = colk[2 * c + 1];
-        // omega = i kappa x Y, scaled by 1/(nx ny nz)
-        const V cx = mk<V>(ky * y2.x - kzz * y1.x, ky * y2.y - kzz * y1.y);
-        const V cy = mk<V>(kzz * y0.x - kx * y2.x, kzz * y0.y - kx * y2.y);
-        const V cz = mk<V>(kx * y1.x - ky * y0.x, kx * y1.y - ky * y0.y);
-        f0 = mk<V>(-cx.y * s, cx.x * s);
-        f1 = mk<V>(-cy.y * s, cy.x * s);
-        f2 = mk<V>(-cz.y * s, cz.x * s);
-      }
+      u0 = cscale(y0, s); u1 = cscale(y1, s); u2 = cscale(y2, s);
+      const T kx = sx * (T)signed_mode(ix, g.Kx, g.Mx);
+      // omega = i kappa x Y, scaled by 1/(nx ny nz): i (kappa x u) with u already scaled
+      const V cx = mk<V>(ky * u2.x - kzz * u1.x, ky * u2.y - kzz * u1.y);
+      const V cy = mk<V>(kzz * u0.x - kx * u2.x, kzz * u0.y - kx * u2.y);
+      const V cz = mk<V>(kx * u1.x - ky * u0.x, kx * u1.y - ky * u0.y);
+      w0 = mk<V>(-cx.y, cx.x);
+      w1 = mk<V>(-cy.y, cy.x);
+      w2 = mk<V>(-cz.y, cz.x);
     }
     const int pos = pidx<V>(ix <= g.Kx ? ix : NX - g.Mx + ix);
-    lines[(0 * TC + c) * LD + pos] = f0;
-    lines[(1 * TC + c) * LD + pos] = f1;
-    lines[(2 * TC + c) * LD + pos] = f2;
+    lines[(0 * TC2 + c) * LD + pos] = u0;
+    lines[(1 * TC2 + c) * LD + pos] = u1;
+    lines[(2 * TC2 + c) * LD + pos] = u2;
+    lines[(3 * TC2 + c) * LD + pos] = w0;
+    lines[(4 * TC2 + c) * LD + pos] = w1;
+    lines[(5 * TC2 + c) * LD + pos] = w2;
   }
   __syncthreads();
   line_fft<V, NX, +1>(lines + (tid / G) * LD, tid % G, tw);
-  for (int i = tid; i < 3 * NX * TC; i += nth) {
-    const int f = i / (NX * TC), r = i - f * (NX * TC), x = r / TC, c = r - x * TC, col = col0 + c;
-    if (col < g.MyMz)
-      out[((size_t)(half * 3 + f) * NX + x) * g.MyMz + col] = lines[(f * TC + c) * LD + pidx<V>(x)];
+  for (int i = tid; i < 6 * NX * TC2; i += nth) {
+    const int f = i / (NX * TC2), r = i - f * (NX * TC2), x = r / TC2, cc = r - x * TC2, cl = col0 + cc;
+    if (cl < g.MyMz) out[((size_t)f * NX + x) * g.MyMz + cl] = lines[(f * TC2 + cc) * LD + pidx<V>(x)];
   }
 }
 

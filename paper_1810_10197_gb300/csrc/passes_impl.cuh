@@ -19,7 +19,7 @@ static cudaError_t launch_p1(const PassArgs& a, cudaStream_t s) {
                       (size_t)2 * TC * sizeof(T);
   cudaError_t e = set_smem(k_p1<T, N, B>, smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((a.g.MyMz + TC - 1) / TC, B ? 3 : 2);
+  dim3 grid((a.g.MyMz + TC / 2 - 1) / (TC / 2), B ? 2 : 1);
   k_p1<T, N, B><<<grid, FftPlan<N>::G * 3 * TC, smem, s>>>(a);
   return cudaGetLastError();
 }
