@@ -313,6 +313,17 @@ def run_ensemble(args):
     return 0
 
 
+def at_error(curve, e, key):
+    """log-log interpolation of `key` on an error-versus-cost curve at error e (None outside
+    the curve's range)."""
+    pts = sorted((c["l2_error"], c[key]) for c in curve if c["l2_error"] > 0)
+    for (e0, v0), (e1, v1) in zip(pts, pts[1:]):
+        if e0 <= e <= e1:
+            w = (math.log(e) - math.log(e0)) / (math.log(e1) - math.log(e0)) if e1 > e0 else 0.0
+            return math.exp(math.log(v0) + w * (math.log(v1) - math.log(v0)))
+    return None
+
+
 def run_accuracy(args):
     """Simulated time per GPU-second at a fixed final-state L2 error (BASELINE configs[1]):
     TG 256^3, nu = 1/1600, t in [0, T].  Error-versus-cost curves (Section 3's comparison) for
@@ -385,15 +396,6 @@ def run_accuracy(args):
         u, i, sec, _ = run("RK4", 0.0, dt)
         curves["rk4_fp64"].append(dict(dt=dt, **rec(u, i, sec)))
         dt /= 2
-
-    def at_error(curve, e, key):
-        """log-log interpolation of `key` on a curve at error e (None outside its range)."""
-        pts = sorted((c["l2_error"], c[key]) for c in curve if c["l2_error"] > 0)
-        for (e0, v0), (e1, v1) in zip(pts, pts[1:]):
-            if e0 <= e <= e1:
-                w = (math.log(e) - math.log(e0)) / (math.log(e1) - math.log(e0)) if e1 > e0 else 0.0
-                return math.exp(math.log(v0) + w * (math.log(v1) - math.log(v0)))
-        return None
 
     cmp = []
     for c in curves["bs5_fp64"]:
@@ -490,11 +492,28 @@ def run_controllers(args):
     u_ref, i_ref, s_ref, _ = run("I", args.ref_tol, "fp64")
     nrm = np.linalg.norm(u_ref)
     rows = {}
+    curves = {"I": [], "PI": [], "MLP": []}
     for kind in ("I", "PI", "MLP"):
-        u, info, sec, st = run(kind, TOL)
-        rows[kind] = {"status": st, "t": info.t, "rhs_evals": int(info.n_rhs), "accepted": int(info.n_acc),
-                      "rejected": int(info.n_rej), "l2_error": float(np.linalg.norm(u - u_ref) / nrm),
-                      "gpu_seconds": sec, "sim_time_per_gpu_s": T_end / sec}
+        for tol in sorted(set(args.ctrl_tols) | {TOL}, reverse=True):
+            u, info, sec, st = run(kind, tol)
+            row = {"tol": tol, "status": st, "t": info.t, "rhs_evals": int(info.n_rhs), "accepted": int(info.n_acc),
+                   "rejected": int(info.n_rej), "l2_error": float(np.linalg.norm(u - u_ref) / nrm),
+                   "gpu_seconds": sec, "sim_time_per_gpu_s": T_end / sec}
+            if st == 0:
+                curves[kind].append(row)
+            if tol == TOL:
+                rows[kind] = row
+    # each controller against the Section 2.2.1 (I) controller at the same final error
+    equal_error = {}
+    for kind in ("PI", "MLP"):
+        equal_error[kind] = []
+        for c in curves[kind]:
+            i_rhs = at_error(curves["I"], c["l2_error"], "rhs_evals")
+            i_sim = at_error(curves["I"], c["l2_error"], "sim_time_per_gpu_s")
+            equal_error[kind].append({"tol": c["tol"], "l2_error": c["l2_error"], "rhs_evals": c["rhs_evals"],
+                                      "I_rhs_evals_at_same_error": i_rhs,
+                                      "rhs_saving_vs_I": (i_rhs / c["rhs_evals"]) if i_rhs else None,
+                                      "sim_time_ratio_vs_I": (c["sim_time_per_gpu_s"] / i_sim) if i_sim else None})
     out = {"metric": METRIC, "value": rows["MLP"]["sim_time_per_gpu_s"], "unit": "sim-time/GPU-s (MLP controller)",
            "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True,
            "dtype": {"fp64": "f64", "fp32_mixed": "f32+f64", "fp32x2": "f32x2+f64"}[args.precision],
@@ -506,6 +525,8 @@ def run_controllers(args):
                       "training_loss_first_last": [float(hist[:20].mean()), float(hist[-200:].mean())],
                       "training_seconds_incl_trajectories": train_s},
            "runs": rows,
+           "curves": curves,
+           "at_equal_error_vs_I": equal_error,
            "mlp_rhs_saving_vs_I": rows["I"]["rhs_evals"] / max(rows["MLP"]["rhs_evals"], 1),
            "wall_seconds": time.perf_counter() - t_start}
     print(json.dumps(out), flush=True)
@@ -717,6 +738,8 @@ def main():
     ap.add_argument("--workload", default="single", choices=["single", "ensemble", "accuracy", "controllers"])
     ap.add_argument("--rt-shape", type=int, nargs=3, default=[128, 128, 256])
     ap.add_argument("--ref-tol", type=float, default=1e-9)
+    ap.add_argument("--ctrl-tols", type=float, nargs="+", default=[1e-5, 1e-6, 1e-7, 1e-8],
+                    help="tolerance sweep of the controllers workload")
     ap.add_argument("--rk4-dt", type=float, default=0.02)
     ap.add_argument("--rk4-levels", type=int, default=4)
     ap.add_argument("--tols", type=float, nargs="+", default=[1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9])
