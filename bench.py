@@ -325,11 +325,12 @@ def at_error(curve, e, key):
 
 
 def run_accuracy(args):
-    """Simulated time per GPU-second at a fixed final-state L2 error (BASELINE configs[1]):
-    TG 256^3, nu = 1/1600, t in [0, T].  Error-versus-cost curves (Section 3's comparison) for
-    BS5 adaptive over tolerances, RK4 over halving steps, DP5 and the FP32-mixed form, all
-    against a time-converged FP64 reference (BS5 at tol 1e-10); comparisons at equal error
-    interpolate each curve in log-log.  Energy and enstrophy are traced every step."""
+    """Simulated time per GPU-second at a fixed final-state L2 error on the Taylor-Green vortex
+    at 256^3, nu = 1/1600, t in [0, T] (or the forced HIT flow with --flow hit).  Error-versus-
+    cost curves (Section 3's comparison) for BS5 adaptive over tolerances, RK4 over halving
+    steps, DP5, the FP32-mixed and the double-word forms, all against a time-converged FP64
+    reference (BS5 at tol 1e-10); comparisons at equal error interpolate each curve in log-log.
+    Energy and enstrophy are traced every step."""
     import torch
 
     from paper_1810_10197_gb300 import Dns, build
@@ -440,12 +441,12 @@ def run_accuracy(args):
 
 
 def run_controllers(args):
-    """BASELINE configs[4]: the learned step-size proposal against the Section 2.2.1 (I) and PI
-    controllers on periodic Boussinesq Rayleigh-Taylor (128 x 128 x 256, Atwood 0.5, tanh
-    interfaces of width 0.05, multimode perturbation 1e-3, nu = kappa = 1e-3, Ri = 1).  The
-    network is trained on the GPU from trajectories of Taylor-Green and forced-HIT flows
-    (configs[0..2] shapes at 32^3, tolerances 1e-5..1e-8); every run is measured against a
-    tol-1e-9 FP64 reference of the same problem."""
+    """The learned step-size proposal against the Section 2.2.1 (I) and PI controllers on
+    periodic Boussinesq Rayleigh-Taylor (128 x 128 x 256, Atwood 0.5, tanh interfaces of width
+    0.05, multimode perturbation 1e-3, nu = kappa = 1e-3, Ri = 1), each over a tolerance
+    sweep and compared at equal final error.  The network is trained on the GPU from
+    trajectories of Taylor-Green and forced-HIT flows (32^3 and 48^3, tolerances 1e-5..1e-8);
+    every run is measured against a tol-1e-9 FP64 reference of the same problem."""
     import torch
 
     import synthetic as syn
