@@ -444,9 +444,10 @@ def run_controllers(args):
     """The learned step-size proposal against the Section 2.2.1 (I) and PI controllers on
     periodic Boussinesq Rayleigh-Taylor (128 x 128 x 256, Atwood 0.5, tanh interfaces of width
     0.05, multimode perturbation 1e-3, nu = kappa = 1e-3, Ri = 1), each over a tolerance
-    sweep and compared at equal final error.  The network is trained on the GPU from
-    trajectories of Taylor-Green and forced-HIT flows (32^3 and 48^3, tolerances 1e-5..1e-8);
-    every run is measured against a tol-1e-9 FP64 reference of the same problem."""
+    sweep and compared at equal final error.  The network corrects the PI factor; it is
+    trained on the GPU from PI-controlled trajectories of Taylor-Green and forced-HIT flows
+    (32^3 and 48^3, tolerances 1e-5..1e-8); every run is measured against a tol-1e-9 FP64
+    reference of the same problem."""
     import torch
 
     import synthetic as syn
@@ -515,6 +516,13 @@ def run_controllers(args):
                                       "I_rhs_evals_at_same_error": i_rhs,
                                       "rhs_saving_vs_I": (i_rhs / c["rhs_evals"]) if i_rhs else None,
                                       "sim_time_ratio_vs_I": (c["sim_time_per_gpu_s"] / i_sim) if i_sim else None})
+    # the learned correction against its own base, the PI controller, at the same final error
+    mlp_vs_pi = []
+    for c in curves["MLP"]:
+        p_rhs = at_error(curves["PI"], c["l2_error"], "rhs_evals")
+        mlp_vs_pi.append({"tol": c["tol"], "l2_error": c["l2_error"], "rhs_evals": c["rhs_evals"],
+                          "PI_rhs_evals_at_same_error": p_rhs,
+                          "rhs_saving_vs_PI": (p_rhs / c["rhs_evals"]) if p_rhs else None})
     out = {"metric": METRIC, "value": rows["MLP"]["sim_time_per_gpu_s"], "unit": "sim-time/GPU-s (MLP controller)",
            "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True,
            "dtype": {"fp64": "f64", "fp32_mixed": "f32+f64", "fp32x2": "f32x2+f64"}[args.precision],
@@ -528,6 +536,7 @@ def run_controllers(args):
            "runs": rows,
            "curves": curves,
            "at_equal_error_vs_I": equal_error,
+           "mlp_at_equal_error_vs_PI": mlp_vs_pi,
            "mlp_rhs_saving_vs_I": rows["I"]["rhs_evals"] / max(rows["MLP"]["rhs_evals"], 1),
            "wall_seconds": time.perf_counter() - t_start}
     print(json.dumps(out), flush=True)

@@ -212,10 +212,11 @@ DNS_API dns_status dns_trace(dns_ctx* ctx, double* out, long long cap, long long
  * DNS_CTRL_PI: after an accepted step h_new = h min(2, max(0.01, 0.8 err^-0.14 err_prev^0.08))
  * (the PI controller the paper names as future work, Section 4, with exponents 0.7/(q+1),
  * 0.4/(q+1)).  DNS_CTRL_MLP: after an accepted step, once 4 accepted steps are known, a
- * learned correction of the Section 2.2.1 factor, h_new = h min(2, max(0.01,
- * 0.8 err^(-1/5) exp(clamp(y, -log 1.5, log 1.5)))) with y from the network below (capped at
- * 1 right after a rejection).  In every variant the embedded error norm still accepts or
- * rejects each step, and rejections (and non-finite proposals) use the Section 2.2.1 factor.
+ * learned correction of the PI factor, h_new = h min(2, max(0.01,
+ * 0.8 err^-0.14 err_prev^0.08 exp(clamp(y, -log 1.5, log 1.5)))) with y from the network
+ * below (capped at 1 right after a rejection); before that, and when y is not finite, the PI
+ * factor.  In every variant the embedded error norm still accepts or rejects each step, and
+ * a rejected attempt takes the Section 2.2.1 factor.
  * mlp_params_dev: DNS_MLP_PARAMS floats on the device (copied in), for DNS_CTRL_MLP only. */
 typedef enum { DNS_CTRL_I = 0, DNS_CTRL_PI = 1, DNS_CTRL_MLP = 2 } dns_controller;
 DNS_API dns_status dns_set_controller(dns_ctx* ctx, int kind, const float* mlp_params_dev);

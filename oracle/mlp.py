@@ -2,11 +2,13 @@
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).  The paper's step-size controller is
 the elementary one of Section 2.2.1 and it names better controllers as future work
-(Section 4); this module is the reference for the learned variant built on top of it.  The
-network proposes a bounded correction of the Section 2.2.1 factor from the recent
-accepted-step history: h_next = h min(2, max(0.01, 0.8 err^(-1/5) exp(clamp(y, +-log 1.5)))).
-An uncertain network (y near 0) behaves like that controller; the embedded error estimate
-still accepts or rejects every step and the Section 2.2.1 controller is the fallback.
+(Section 4); this module is the reference for the learned variant built on the PI controller
+(factor 0.8 err^(-0.7/5) err_prev^(0.4/5), err_prev the error of the previous accepted step).
+The network proposes a bounded correction of the PI factor from the recent accepted-step
+history: h_next = h min(2, max(0.01, 0.8 err^(-0.7/5) err_prev^(0.4/5) exp(clamp(y, +-log 1.5)))).
+An uncertain network (y near 0) behaves like the PI controller, which is also the fallback
+(the first accepted steps, a non-finite output); the embedded error estimate still accepts or
+rejects every step, and a rejected attempt takes the Section 2.2.1 factor.
 
 Parameter vector (float, length N_PARAMS), in this order:
   W1[64][16], b1[64], W2[64][64], b2[64], w3[64], b3[1]
@@ -16,10 +18,11 @@ Loss:     L = mean_b (y_b - t_b)^2
 Features of the history (4 most recent accepted steps, newest first, i = 0..3), each
   [log10 err_i, log(h_i / h_0), rejections just before step i, log(h_i / h_{i+1})]
 with h_0 the newest accepted step (the last feature of i = 3 uses the step before it, or 0).
-Target for training at accepted step n: log(h*_n / h_n) - log(0.8 err_n^(-1/5)), with
+Target for training at accepted step n: log(h*_n / h_n) - log(0.8 err_n^(-0.7/5) e_n^(0.4/5)),
+with e_n the error of the last accepted step before n with a positive error (1 if none),
 h*_n = h_{n+1} (0.8^5/err_{n+1})^(1/5) and n+1 the next accepted step -- the step that, in
-hindsight, would have produced the error 0.8^5 that the Section 2.2.1 controller aims for,
-relative to what that controller proposed.
+hindsight, would have produced the error 0.8^5 that the controllers aim for (error ~ h^5 for
+the 4th-order embedded estimate), relative to what the PI controller proposed.
 """
 from __future__ import annotations
 
@@ -31,6 +34,12 @@ NIN, NH, NOUT = 16, 64, 1
 N_PARAMS = NH * NIN + NH + NH * NH + NH + NH + 1
 LOG_DMIN, LOG_DMAX = math.log(0.01), math.log(2.0)
 LOG_CORR = math.log(1.5)      # bound of the learned correction
+PI_ALPHA, PI_BETA = 0.7 / 5.0, 0.4 / 5.0
+
+
+def log_pi_factor(err, err_prev):
+    """log of the unclamped PI factor 0.8 err^(-alpha) err_prev^beta (err, err_prev > 0)."""
+    return math.log(0.8) - PI_ALPHA * math.log(err) + PI_BETA * math.log(err_prev)
 
 
 def unpack(p):
@@ -108,11 +117,16 @@ def features(hist):
 
 def dataset_from_history(steps):
     """Training pairs from one run's attempt history [(t, h, err, accepted), ...]."""
-    acc = []
+    acc = []            # (err, h, rejections before it)
+    eprev = []          # error of the last earlier accepted step with err > 0 (1 if none)
     rej = 0
+    e_last = 1.0
     for (_, h, err, ok) in steps:
         if ok:
             acc.append((err, h, rej))
+            eprev.append(e_last)
+            if err > 0:
+                e_last = err
             rej = 0
         else:
             rej += 1
@@ -125,17 +139,18 @@ def dataset_from_history(steps):
             continue
         hstar = h1 * (0.8 ** 5 / err1) ** 0.2
         X.append(features(hist))
-        T.append(math.log(hstar / acc[n][1]) - math.log(0.8 * errn ** -0.2))
+        T.append(math.log(hstar / acc[n][1]) - log_pi_factor(errn, eprev[n]))
     return np.array(X).reshape(-1, NIN), np.array(T)
 
 
-def propose_factor(p, hist):
-    """Step factor fac_I exp(clamp(y, +-log 1.5)) clamped to [dmin, dmax] (weights rounded to
-    bf16); hist[0] is the step just accepted.  None if y is not finite."""
+def propose_factor(p, hist, err_prev):
+    """Step factor fac_PI exp(clamp(y, +-log 1.5)) clamped to [dmin, dmax] (weights rounded to
+    bf16); hist[0] is the step just accepted, err_prev the error of the accepted step before
+    it (1 if none).  None if y is not finite."""
     y, _ = forward(round_bf16(p), features(hist)[None, :])
     y = float(y[0])
     err = hist[0][0]
     if not math.isfinite(y) or not err > 0:
         return None
-    lf = math.log(0.8) - 0.2 * math.log(err) + min(LOG_CORR, max(-LOG_CORR, y))
+    lf = log_pi_factor(err, err_prev) + min(LOG_CORR, max(-LOG_CORR, y))
     return math.exp(min(LOG_DMAX, max(LOG_DMIN, lf)))

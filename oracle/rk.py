@@ -212,8 +212,10 @@ def integrate(f: Callable, u0: np.ndarray, t0: float, t_end: float, method: str,
     method: "RK4" (fixed h0), "BS5_FIXED" (fixed h0, error logged), "BS5_ADAPTIVE",
     "DP5_FIXED", "DP5_ADAPTIVE".  The last step is clipped to land on t_end.
     controller (adaptive methods): "I" (Section 2.2.1), "PI", or ("MLP", params): after an
-    accepted step the PI / network proposal replaces the factor; after a rejection, and for
-    the first 4 accepted steps (MLP), the Section 2.2.1 factor is used.
+    accepted step the PI factor, or the network's bounded correction of it, replaces the
+    Section 2.2.1 factor; the MLP controller falls back to the PI factor for its first 3
+    accepted steps and when the network's output is not finite; a rejected attempt always
+    takes the Section 2.2.1 factor.
     post_step(u_old, u_new) -> u, if given, replaces the state after every accepted step (the
     band rescale forcing of Section 3.3.1); when it returns a new array the derivative carried
     over by a first-same-as-last pair no longer belongs to the state and k_1 is evaluated afresh.
@@ -249,12 +251,13 @@ def integrate(f: Callable, u0: np.ndarray, t0: float, t_end: float, method: str,
         if adaptive:
             accepted = math.isfinite(err) and err <= 1.0
             fac = controller_factor(err, after_reject)
-            if accepted and controller == "PI":
+            is_mlp = isinstance(controller, tuple) and controller[0] == "MLP"
+            if accepted and (controller == "PI" or is_mlp):
                 fac = pi_factor(err, err_prev, after_reject)
-            elif accepted and isinstance(controller, tuple) and controller[0] == "MLP":
+            if accepted and is_mlp:
                 hist = [(err, h_step, rej_since)] + hist[:4]
                 if len(hist) >= 4:
-                    prop = _mlp.propose_factor(controller[1], hist)
+                    prop = _mlp.propose_factor(controller[1], hist, err_prev)
                     if prop is not None:
                         fac = min(1.0, prop) if after_reject else prop
             h_new = h_step * fac

@@ -138,9 +138,9 @@ __global__ void k_begin_attempt(DnsCtrl* c, int method) {
 // Section 2.2.1: err = max_j sqrt(S_j / (nx ny (nz/2+1))); accept iff err <= 1;
 // h_new = h min(dmax, max(dmin, 0.8 err^(-1/5))), dmax = 1 right after a rejection.
 // Variants after an accepted step: PI (0.8 err^(-0.7/5) err_prev^(0.4/5)) or the learned
-// correction 0.8 err^(-1/5) exp(clamp(mlp(features), +-log 1.5)) once 4 accepted steps are
-// known; after a rejection and when the proposal is not finite the Section 2.2.1 factor is
-// used.
+// correction of it, PI exp(clamp(mlp(features), +-log 1.5)), once 4 accepted steps are
+// known (before that, and when the network's output is not finite, the PI factor); a
+// rejected attempt takes the Section 2.2.1 factor.
 __global__ void __launch_bounds__(kRedThreads) k_controller(DnsCtrl* c, const double* partials,
                                                             int method, int nstages, int nblk,
                                                             double nmodes, int nc) {
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kRedThreads) k_controller(DnsCtrl* c, const do
       if (!fin) fac = 0.01;
       else if (err == 0.0) fac = dmax;
       else fac = fmin(dmax, fmax(0.01, 0.8 * pow(err, -1.0 / 5.0)));
-      if (accept && c->ctrl_kind == 1 && err > 0.0)
+      if (accept && (c->ctrl_kind == 1 || (c->ctrl_kind == 2 && c->mlp)) && err > 0.0)
         fac = fmin(dmax, fmax(0.01, 0.8 * pow(err, -(0.7 / 5.0)) * pow(c->err_prev, 0.4 / 5.0)));
       if (accept && c->ctrl_kind == 2 && c->mlp) {
         for (int i = 4; i > 0; --i) {
@@ -228,9 +228,10 @@ __global__ void __launch_bounds__(kRedThreads) k_controller(DnsCtrl* c, const do
   const bool accept = s_accept != 0;
   double fac = s_fac;
   if (use_mlp && isfinite(y) && err > 0.0) {
-    // learned correction of the Section 2.2.1 factor, bounded by 1.5x either way
+    // learned correction of the PI factor, bounded by 1.5x either way
     const double corr = fmin(log(1.5), fmax(-log(1.5), (double)y));
-    const double lf = fmin(log(2.0), fmax(log(0.01), log(0.8) - 0.2 * log(err) + corr));
+    const double lpi = log(0.8) - (0.7 / 5.0) * log(err) + (0.4 / 5.0) * log(c->err_prev);
+    const double lf = fmin(log(2.0), fmax(log(0.01), lpi + corr));
     fac = exp(lf);
     if (c->after_reject) fac = fmin(1.0, fac);
   }

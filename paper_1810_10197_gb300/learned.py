@@ -1,14 +1,17 @@
 """Training pipeline for the learned step-size proposal (DNS_CTRL_MLP).
 
 Trajectories come from the device attempt trace (dns_set_trace / dns_trace) of runs with the
-Section 2.2.1 controller; the training pairs are built on the host (a few thousand rows)
-and the network is trained on the GPU by the library's own kernels (dns_mlp_train).
+PI controller, the base the learned proposal corrects; the training pairs are built on the
+host (a few thousand rows) and the network is trained on the GPU by the library's own
+kernels (dns_mlp_train).
 
 Features at accepted step n (newest first, i = 0..3, h_0 = h_n):
     [log10 err_i, log(h_i / h_0), rejections just before step i, log(h_i / h_{i+1})]
-Target: log(h*_n / h_n) - log(0.8 err_n^(-1/5)) with h*_n = h_{n+1} (0.8^5 / err_{n+1})^(1/5),
-n+1 the next accepted step: the step that in hindsight gives the error 0.8^5 the controller
-aims for, relative to the Section 2.2.1 proposal (the network learns a bounded correction).
+Target: log(h*_n / h_n) - log(0.8 err_n^(-0.7/5) e_n^(0.4/5)) with
+h*_n = h_{n+1} (0.8^5 / err_{n+1})^(1/5), n+1 the next accepted step and e_n the error of the
+last earlier accepted step with a positive error (1 if none): the step that in hindsight gives
+the error 0.8^5 the controllers aim for, relative to the PI proposal (the network learns a
+bounded correction of it).
 """
 from __future__ import annotations
 
@@ -31,11 +34,14 @@ def _features(hist):
 
 def pairs_from_trace(trace: np.ndarray):
     """(X[n,16], T[n]) from an attempt trace (columns t, h, err, accepted, ...)."""
-    acc, rej = [], 0
+    acc, eprev, rej, e_last = [], [], 0, 1.0
     for row in trace:
         h, err, ok = float(row[1]), float(row[2]), row[3] > 0.5
         if ok:
             acc.append((err, h, rej))
+            eprev.append(e_last)
+            if err > 0:
+                e_last = err
             rej = 0
         else:
             rej += 1
@@ -47,7 +53,8 @@ def pairs_from_trace(trace: np.ndarray):
             continue
         hist = [acc[n - i] for i in range(min(5, n + 1))]
         X.append(_features(hist))
-        T.append(math.log(h1 * (0.8 ** 5 / err1) ** 0.2 / acc[n][1]) - math.log(0.8 * errn ** -0.2))
+        T.append(math.log(h1 * (0.8 ** 5 / err1) ** 0.2 / acc[n][1])
+                 - math.log(0.8 * errn ** -0.14 * eprev[n] ** 0.08))
     return np.asarray(X, dtype=np.float32).reshape(-1, 16), np.asarray(T, dtype=np.float32)
 
 
@@ -78,10 +85,11 @@ def train(X: np.ndarray, T: np.ndarray, steps=3000, batch=128, lr=2e-3, seed=0):
 
 
 def training_set(flows, make_dns, to_dev):
-    """Pairs from runs of the Section 2.2.1 controller: flows = [(shape, uhat, nu, forcing, tol, T)]."""
+    """Pairs from runs of the PI controller: flows = [(shape, uhat, nu, forcing, tol, T)]."""
     Xs, Ts = [], []
     for (shape, uh, nu, forcing, tol, T) in flows:
         d = make_dns(shape, nu, forcing)
+        d.set_controller("PI")
         d.set_state(to_dev(uh), 0.0)
         d.set_trace(20000)
         d.integrate(T, "BS5_ADAPTIVE", tol, tol, h0=1e-3)
