@@ -83,6 +83,23 @@ def pass_bytes(n, esz=16):
     }
 
 
+# Nonzero stage coefficients of the Bogacki-Shampine 5(4) pair (Appendix A): terms of the
+# stage sums forming the inputs of stages 2..8 (the last one is u_{n+1}), and the terms of
+# the embedded error e = h sum_j (b_j - bhat_j) k_j.
+BS5_STAGE_TERMS = (1, 2, 3, 4, 5, 6, 6)
+BS5_ERR_TERMS = 7
+
+
+def step_kernel_bytes(n, nc=3):
+    """Algorithmic HBM bytes per BS5 attempt of the kernels around the passes: each stage sum
+    reads u and its k_j and writes one field; the error norm reads u_n, u_{n+1} and its k_j.
+    Every field is the FP64 retained box (nc M complex values)."""
+    K = (n - 1) // 3
+    field = nc * (2 * K + 1) ** 2 * (K + 1) * 16
+    return {"stage_sum": sum(t + 2 for t in BS5_STAGE_TERMS) * field,
+            "err_norm_partials": (BS5_ERR_TERMS + 2) * field}
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -664,7 +681,10 @@ def run_gpu(args):
     names = list(flops)
     dom = max(names, key=lambda k: prof.get(k, (0, 0.0))[1])
     nl, tot_ms = prof[dom]
-    avg_s = tot_ms * 1e-3 / nl
+    # in step mode every attempt also launches the passes for k_1, which return at once when
+    # first-same-as-last carries k_1 over: a pass does work n_rhs times, not nl times
+    n_work = n_rhs if args.mode == "step" else nl
+    avg_s = tot_ms * 1e-3 / n_work
     traffic = None
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
@@ -699,6 +719,17 @@ def run_gpu(args):
                       "avg_ms": round(v[1] / max(v[0], 1), 4)}
                   for k, v in prof.items()}
     rhs_bytes = sum(byts.values())
+    # algorithmic bytes moved in the timed region, per kernel and for the whole step
+    attempts = (i1.n_acc - i0.n_acc) + (i1.n_rej - i0.n_rej) if args.mode == "step" else 0
+    moved = {k: byts[k] * n_rhs for k in byts}
+    for k, b in step_kernel_bytes(n).items():
+        moved[k] = b * attempts
+    for k, b in moved.items():
+        if k in prof and prof[k][1] > 0 and b > 0:
+            gbs = b / (prof[k][1] * 1e-3) / 1e9
+            per_kernel[k]["hbm_gbs"] = round(gbs, 1)
+            per_kernel[k]["hbm_frac_of_measured"] = round(gbs / peaks["hbm_gbs"], 4)
+    step_hbm_frac = sum(moved.values()) / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]
     cpu = None
     if ws == 1 and not args.no_cpu:
         v, dt = cpu_sample(2)
@@ -721,6 +752,7 @@ def run_gpu(args):
            "sim_time_advanced": sim, "rhs_evals": n_rhs, "t_end_state": i1.t,
            "accepted": i1.n_acc - i0.n_acc, "rejected": i1.n_rej - i0.n_rej,
            "rhs_hbm_frac_of_measured": rhs_bytes * value / ws / 1e9 / peaks["hbm_gbs"],
+           "step_hbm_frac_of_measured": step_hbm_frac,
            "e2e": e2e,
            "gpu_launches": launches,
            "kernels": per_kernel,

@@ -322,6 +322,15 @@ DNS_API dns_status dns_debug_stall(dns_ctx* ctx);
  * right-hand side; takes effect for work enqueued after the call. */
 DNS_API dns_status dns_debug_poison(dns_ctx* ctx, int on);
 
+/* Test hook for the FP64-to-FP32 conversion the FP32-mixed stage sums and error norm use
+ * (integer instructions on the bits, no FP64 arithmetic): y[i] = x[i] rounded to FP32 with the
+ * significand rounded to nearest (ties away from zero), magnitudes below the smallest normal
+ * float flushed to a signed zero, beyond the largest float an infinity, NaN kept.
+ * x_dev: n doubles, y_dev: n floats, both on the device (caller-owned); enqueued on `stream`
+ * (NULL: the legacy default stream).  DNS_ERR_ARG for n < 0 or a NULL pointer with n > 0;
+ * DNS_ERR_CUDA if the launch fails. */
+DNS_API dns_status dns_debug_f32_from_f64(const double* x_dev, float* y_dev, long long n, void* stream);
+
 /* Grid facts: retained cut-offs K[3] and the number of device bytes the context holds. */
 DNS_API dns_status dns_query(const dns_ctx* ctx, int* K3, size_t* device_bytes);
 

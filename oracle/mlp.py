@@ -20,9 +20,12 @@ Features of the history (4 most recent accepted steps, newest first, i = 0..3), 
 with h_0 the newest accepted step (the last feature of i = 3 uses the step before it, or 0).
 Target for training at accepted step n: log(h*_n / h_n) - log(0.8 err_n^(-0.7/5) e_n^(0.4/5)),
 with e_n the error of the last accepted step before n with a positive error (1 if none),
-h*_n = h_{n+1} (0.8^5/err_{n+1})^(1/5) and n+1 the next accepted step -- the step that, in
-hindsight, would have produced the error 0.8^5 that the controllers aim for (error ~ h^5 for
-the 4th-order embedded estimate), relative to what the PI controller proposed.
+h*_n = h_{n+1} (E_TARGET/err_{n+1})^(1/5) and n+1 the next accepted step -- the step that, in
+hindsight, would have produced the error the PI controller settles at (error ~ h^5 for the
+4th-order embedded estimate), relative to what the PI controller proposed.  That level is the
+fixed point of the PI factor at constant error, 0.8 e^(-0.7/5 + 0.4/5) = 1, so
+E_TARGET = 0.8^(1/0.06) = 0.0243: the network corrects the PI controller's prediction of the
+next error, not the error level it keeps.
 """
 from __future__ import annotations
 
@@ -35,6 +38,7 @@ N_PARAMS = NH * NIN + NH + NH * NH + NH + NH + 1
 LOG_DMIN, LOG_DMAX = math.log(0.01), math.log(2.0)
 LOG_CORR = math.log(1.5)      # bound of the learned correction
 PI_ALPHA, PI_BETA = 0.7 / 5.0, 0.4 / 5.0
+E_TARGET = 0.8 ** (1.0 / (PI_ALPHA - PI_BETA))   # fixed point of the PI factor
 
 
 def log_pi_factor(err, err_prev):
@@ -137,7 +141,7 @@ def dataset_from_history(steps):
         errn = acc[n][0]
         if not (err1 > 0 and math.isfinite(err1) and errn > 0):
             continue
-        hstar = h1 * (0.8 ** 5 / err1) ** 0.2
+        hstar = h1 * (E_TARGET / err1) ** 0.2
         X.append(features(hist))
         T.append(math.log(hstar / acc[n][1]) - log_pi_factor(errn, eprev[n]))
     return np.array(X).reshape(-1, NIN), np.array(T)

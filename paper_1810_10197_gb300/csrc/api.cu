@@ -272,6 +272,7 @@ dns_status enqueue_stage(dns_ctx* c, int nterms, const int* kslots, const double
   s.uslot = SLOT_U;
   s.yslot = yslot;
   s.n2 = (long long)c->g.nc * c->g.M;
+  s.f32 = c->precision == DNS_FP32_MIXED ? 1 : 0;
   CK(timed(c, PR_STAGE, [&] { return launch_stage_sum(s, c->stream); }), "stage sum");
   return DNS_OK;
 }
@@ -328,6 +329,7 @@ dns_status enqueue_attempt(dns_ctx* c, int method) {
   e.M = c->g.M;
   e.nc = c->g.nc;
   e.partials = c->partials;
+  e.f32 = c->precision == DNS_FP32_MIXED ? 1 : 0;
   int n = 0;
   for (int j = 0; j < S; ++j) {
     if (Bw(j).p * Bh(j).q == Bh(j).p * Bw(j).q) continue;
@@ -1132,6 +1134,11 @@ dns_status dns_debug_poison(dns_ctx* c, int on) {
   if (c->poison != (on != 0)) drop_graphs(c);
   c->poison = on != 0;
   return DNS_OK;
+}
+
+dns_status dns_debug_f32_from_f64(const double* x, float* y, long long n, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) return DNS_ERR_ARG;
+  return launch_f32_from_f64(x, y, n, (cudaStream_t)stream) == cudaSuccess ? DNS_OK : DNS_ERR_CUDA;
 }
 
 dns_status dns_set_tiles(dns_ctx* c, int var_py, int var_p3) {

@@ -13,9 +13,33 @@ inline int grid_for(long long n, int threads, int cap) {
   return (int)(b < cap ? b : cap);
 }
 
+// FP32 value of an FP64 number computed from its bits with integer instructions only (the
+// FP64 pipe of this part issues at 1/64 of the FP32 rate, and a hardware conversion would
+// use it): the significand rounded to 24 bits (nearest, ties away from zero), the exponent
+// rebiased from 1023 to 127.  Magnitudes that round below the smallest normal float give a
+// signed zero, above the largest float an infinity; NaN stays NaN.
+__device__ __forceinline__ float f32_from_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
+  const unsigned long long a = mag + (1ull << 28);                  // + half a float ulp
+  const unsigned int ahi = (unsigned int)(a >> 32), alo = (unsigned int)a;
+  const unsigned int e = ahi >> 20;                                  // exponent after rounding
+  // bits 31..23 of (a >> 29) hold e mod 512; subtracting 896 << 23 modulo 2^32 leaves e - 896
+  // in the float's exponent field for 897 <= e <= 1150, the normal float range
+  unsigned int r = __funnelshift_r(alo, ahi, 29) - (896u << 23);
+  r = e < 897u ? 0u : r;
+  r = e > 1150u ? 0x7F800000u : r;
+  r = mag > 0x7FF0000000000000ull ? 0x7FC00000u : r;
+  return __uint_as_float(r | sign);
+}
+
 // Y = u + h * sum_j coef_j k_j, terms added in ascending j (fused multiply-adds: on this part
 // the FP64 pipe, not HBM, bounds this kernel, so the instruction count matters).
-template <int NT>
+// F32 (the FP32-mixed form, whose k_j carry FP32 accuracy): the increment sum_j (h coef_j) k_j
+// is formed in FP32 from FP32 values of the k_j and added to u in FP64; its rounding (~6e-8 of
+// the increment) lies below the error the k_j already carry, and the kernel becomes HBM-bound.
+template <int NT, bool F32>
 __global__ void k_stage_sum(const StageArgs a) {
   const DnsCtrl* c = a.ctrl;
   if (gated_off(c, a.gate_k1)) return;
@@ -26,6 +50,24 @@ __global__ void k_stage_sum(const StageArgs a) {
 #pragma unroll
   for (int j = 0; j < NT; ++j) k[j] = c->slot[a.kslot[j]];
   const long long stride = (long long)gridDim.x * blockDim.x;
+  if (F32) {
+    float hc[NT];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) hc[j] = (float)(h * a.coef[j]);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n2; i += stride) {
+      double2 kv = k[0][i];
+      float ar = hc[0] * f32_from_bits(kv.x), ai = hc[0] * f32_from_bits(kv.y);
+#pragma unroll
+      for (int j = 1; j < NT; ++j) {
+        kv = k[j][i];
+        ar = fmaf(hc[j], f32_from_bits(kv.x), ar);
+        ai = fmaf(hc[j], f32_from_bits(kv.y), ai);
+      }
+      const double2 uv = u[i];
+      y[i] = make_double2(uv.x + (double)ar, uv.y + (double)ai);
+    }
+    return;
+  }
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n2; i += stride) {
     double2 kv = k[0][i];
     double ar = a.coef[0] * kv.x, ai = a.coef[0] * kv.y;
@@ -70,7 +112,10 @@ __device__ __forceinline__ void block_sum3(double v[3], double* sh) { block_sum<
 
 // Per-block partial sums of (|e| / sc)^2 per component, e = h sum_j (b_j - bhat_j) k_j,
 // sc = atol + rtol max(|u_n|, |u_{n+1}|)  (Section 2.2.1).
-template <int NT>
+// F32 (the FP32-mixed form): e, sc and the ratio in FP32 from FP32 values of the inputs, the
+// squares accumulated in FP64; the k_j carry FP32 accuracy, so err keeps all the accuracy
+// they hold.  Nonzero tolerances outside [1e-30, 1e30] take the FP64 arithmetic.
+template <int NT, bool F32>
 __global__ void __launch_bounds__(kRedThreads) k_err_partials(const ErrArgs a) {
   __shared__ double sh[4 * 32];
   const DnsCtrl* c = a.ctrl;
@@ -83,6 +128,36 @@ __global__ void __launch_bounds__(kRedThreads) k_err_partials(const ErrArgs a) {
   for (int j = 0; j < NT; ++j) k[j] = c->slot[a.kslot[j]];
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   const long long stride = (long long)gridDim.x * blockDim.x;
+  const bool rt_ok = rtol == 0.0 || (rtol >= 1e-30 && rtol <= 1e30);
+  const bool at_ok = atol == 0.0 || (atol >= 1e-30 && atol <= 1e30);
+  if (F32 && rt_ok && at_ok) {
+    float hc[NT];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) hc[j] = (float)(h * a.coef[j]);
+    const float rt = (float)rtol, at = (float)atol;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (q >= a.nc) break;
+      for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.M; i += stride) {
+        const long long idx = q * a.M + i;
+        double2 kv = k[0][idx];
+        float er = hc[0] * f32_from_bits(kv.x), ei = hc[0] * f32_from_bits(kv.y);
+#pragma unroll
+        for (int j = 1; j < NT; ++j) {
+          kv = k[j][idx];
+          er = fmaf(hc[j], f32_from_bits(kv.x), er);
+          ei = fmaf(hc[j], f32_from_bits(kv.y), ei);
+        }
+        const double2 a0 = u0[idx], a1 = u1[idx];
+        const float x0 = f32_from_bits(a0.x), y0 = f32_from_bits(a0.y);
+        const float x1 = f32_from_bits(a1.x), y1 = f32_from_bits(a1.y);
+        const float m2 = fmaxf(fmaf(x0, x0, y0 * y0), fmaf(x1, x1, y1 * y1));
+        const float inv = 1.0f / fmaf(rt, sqrtf(m2), at);
+        const double tr = (double)(er * inv), ti = (double)(ei * inv);
+        acc[q] = fma(tr, tr, fma(ti, ti, acc[q]));
+      }
+    }
+  } else {
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     if (q >= a.nc) break;
@@ -103,6 +178,7 @@ __global__ void __launch_bounds__(kRedThreads) k_err_partials(const ErrArgs a) {
       const double sc = fma(rtol, sqrt(m2), atol);
       acc[q] += fma(er, er, ei * ei) / (sc * sc);
     }
+  }
   }
   block_sum<4>(acc, sh);
   if (threadIdx.x == 0) {
@@ -591,30 +667,51 @@ cudaError_t launch_spectrum(const Geom& g, const double2* u, double* partials, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_stage_sum(const StageArgs& a, cudaStream_t s) {
-  const int blocks = grid_for(a.n2, 256, 152 * 16);
+__global__ void k_f32_from_f64(const double* __restrict__ x, float* __restrict__ y, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = f32_from_bits(x[i]);
+}
+
+template <bool F32>
+cudaError_t stage_sum_nt(const StageArgs& a, int blocks, cudaStream_t s) {
   switch (a.nterms) {
-    case 1: k_stage_sum<1><<<blocks, 256, 0, s>>>(a); break;
-    case 2: k_stage_sum<2><<<blocks, 256, 0, s>>>(a); break;
-    case 3: k_stage_sum<3><<<blocks, 256, 0, s>>>(a); break;
-    case 4: k_stage_sum<4><<<blocks, 256, 0, s>>>(a); break;
-    case 5: k_stage_sum<5><<<blocks, 256, 0, s>>>(a); break;
-    case 6: k_stage_sum<6><<<blocks, 256, 0, s>>>(a); break;
-    case 7: k_stage_sum<7><<<blocks, 256, 0, s>>>(a); break;
-    case 8: k_stage_sum<8><<<blocks, 256, 0, s>>>(a); break;
+    case 1: k_stage_sum<1, F32><<<blocks, 256, 0, s>>>(a); break;
+    case 2: k_stage_sum<2, F32><<<blocks, 256, 0, s>>>(a); break;
+    case 3: k_stage_sum<3, F32><<<blocks, 256, 0, s>>>(a); break;
+    case 4: k_stage_sum<4, F32><<<blocks, 256, 0, s>>>(a); break;
+    case 5: k_stage_sum<5, F32><<<blocks, 256, 0, s>>>(a); break;
+    case 6: k_stage_sum<6, F32><<<blocks, 256, 0, s>>>(a); break;
+    case 7: k_stage_sum<7, F32><<<blocks, 256, 0, s>>>(a); break;
+    case 8: k_stage_sum<8, F32><<<blocks, 256, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_err_partials(const ErrArgs& a, cudaStream_t s) {
+template <bool F32>
+cudaError_t err_partials_nt(const ErrArgs& a, cudaStream_t s) {
   switch (a.nterms) {
-    case 6: k_err_partials<6><<<kRedBlocks, kRedThreads, 0, s>>>(a); break;
-    case 7: k_err_partials<7><<<kRedBlocks, kRedThreads, 0, s>>>(a); break;
-    case 5: k_err_partials<5><<<kRedBlocks, kRedThreads, 0, s>>>(a); break;
+    case 6: k_err_partials<6, F32><<<kRedBlocks, kRedThreads, 0, s>>>(a); break;
+    case 7: k_err_partials<7, F32><<<kRedBlocks, kRedThreads, 0, s>>>(a); break;
+    case 5: k_err_partials<5, F32><<<kRedBlocks, kRedThreads, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_stage_sum(const StageArgs& a, cudaStream_t s) {
+  const int blocks = grid_for(a.n2, 256, 152 * 16);
+  return a.f32 ? stage_sum_nt<true>(a, blocks, s) : stage_sum_nt<false>(a, blocks, s);
+}
+
+cudaError_t launch_f32_from_f64(const double* x, float* y, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_f32_from_f64<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(x, y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_err_partials(const ErrArgs& a, cudaStream_t s) {
+  return a.f32 ? err_partials_nt<true>(a, s) : err_partials_nt<false>(a, s);
 }
 
 cudaError_t launch_begin_attempt(DnsCtrl* c, int method, cudaStream_t s) {

@@ -18,6 +18,7 @@ struct StageArgs {
   double coef[kMaxTerms];
   int uslot, yslot;
   long long n2;          // complex elements per field set (3 M)
+  int f32;               // 1: increment formed in FP32 (FP32-mixed form)
 };
 
 struct ErrArgs {
@@ -28,11 +29,13 @@ struct ErrArgs {
   long long M;              // modes per component
   int nc;                   // state components (3 or 4)
   double* partials;         // [kRedBlocks][4]
+  int f32;                  // 1: e, sc and the ratio in FP32 (FP32-mixed form)
 };
 
 // Host launchers (stepper.cu).  All enqueue on stream s and return the launch status.
 cudaError_t launch_stage_sum(const StageArgs& a, cudaStream_t s);
 cudaError_t launch_err_partials(const ErrArgs& a, cudaStream_t s);
+cudaError_t launch_f32_from_f64(const double* x, float* y, long long n, cudaStream_t s);
 cudaError_t launch_begin_attempt(DnsCtrl* c, int method, cudaStream_t s);
 cudaError_t launch_controller(DnsCtrl* c, const double* partials, int method, int nstages,
                               double nmodes, int nc, cudaStream_t s);

@@ -110,6 +110,7 @@ _SIGS.update({
     "dns_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "dns_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "dns_crc32": (C.c_uint, [C.c_void_p, C.c_size_t, C.c_uint]),
+    "dns_debug_f32_from_f64": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]),
 })
 TRACE_COLS = 8
 MLP_PARAMS = 5313
@@ -370,6 +371,15 @@ def dns_crc32(data: bytes, crc: int = 0) -> int:
     """CRC-32 of the checkpoint trailer (host code, no GPU needed)."""
     buf = C.create_string_buffer(bytes(data), len(data))
     return int(load().dns_crc32(buf, len(data), crc))
+
+
+def dns_debug_f32_from_f64(x_dev, y_dev, stream=None):
+    """The integer-bit FP64-to-FP32 conversion of the FP32-mixed stage sums (test hook)."""
+    h = getattr(stream, "cuda_stream", stream)
+    st = load().dns_debug_f32_from_f64(C.c_void_p(_ptr(x_dev)), C.c_void_p(_ptr(y_dev)), int(x_dev.numel()),
+                                       C.c_void_p(h) if h else None)
+    if st != 0:
+        raise DnsError(st, "dns_debug_f32_from_f64")
 
 
 def dns_rhs_noalloc(nx, ny, nz, nu, uhat_dev, f_dev, stream=None):

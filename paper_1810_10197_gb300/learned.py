@@ -8,10 +8,11 @@ kernels (dns_mlp_train).
 Features at accepted step n (newest first, i = 0..3, h_0 = h_n):
     [log10 err_i, log(h_i / h_0), rejections just before step i, log(h_i / h_{i+1})]
 Target: log(h*_n / h_n) - log(0.8 err_n^(-0.7/5) e_n^(0.4/5)) with
-h*_n = h_{n+1} (0.8^5 / err_{n+1})^(1/5), n+1 the next accepted step and e_n the error of the
-last earlier accepted step with a positive error (1 if none): the step that in hindsight gives
-the error 0.8^5 the controllers aim for, relative to the PI proposal (the network learns a
-bounded correction of it).
+h*_n = h_{n+1} (E_TARGET / err_{n+1})^(1/5), n+1 the next accepted step and e_n the error of
+the last earlier accepted step with a positive error (1 if none): the step that in hindsight
+gives the error the PI controller settles at, E_TARGET = 0.8^(1/(0.7/5 - 0.4/5)) (the fixed
+point of its factor at constant error), relative to the PI proposal.  The network learns a
+bounded correction of PI's prediction, not of the error level PI keeps.
 """
 from __future__ import annotations
 
@@ -20,6 +21,8 @@ import math
 import numpy as np
 
 from . import dns as _dns
+
+E_TARGET = 0.8 ** (1.0 / (0.7 / 5.0 - 0.4 / 5.0))
 
 
 def _features(hist):
@@ -53,7 +56,7 @@ def pairs_from_trace(trace: np.ndarray):
             continue
         hist = [acc[n - i] for i in range(min(5, n + 1))]
         X.append(_features(hist))
-        T.append(math.log(h1 * (0.8 ** 5 / err1) ** 0.2 / acc[n][1])
+        T.append(math.log(h1 * (E_TARGET / err1) ** 0.2 / acc[n][1])
                  - math.log(0.8 * errn ** -0.14 * eprev[n] ** 0.08))
     return np.asarray(X, dtype=np.float32).reshape(-1, 16), np.asarray(T, dtype=np.float32)
 

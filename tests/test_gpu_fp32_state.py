@@ -1,0 +1,119 @@
+"""Stage sums and error norm of the FP32-mixed form.
+
+In that form the k_j carry FP32 accuracy, so the stage increments sum_j (h a_ij) k_j and the
+embedded error e = h sum_j (b_j - bhat_j) k_j are formed in FP32 from FP32 values of the FP64
+k_j, produced by an integer-bit conversion.  Checked here:
+* the conversion against IEEE round-to-nearest (numpy float32) with its two stated
+  differences: ties round away from zero, and magnitudes below the smallest normal float
+  flush to a signed zero;
+* the error norm's FP32 arithmetic against its FP64 arithmetic on the same attempt (the FP64
+  arithmetic is taken for tolerances below 1e-30): at rtol 1e-3 the cancellation in e
+  amplifies FP32 rounding (6e-8 of the terms) by h|k|/|e| ~ 1e2, bound 1e-4 relative;
+* ten adaptive FP32-mixed steps against the oracle replaying the same step sizes (decisions
+  need not match the oracle's own: the RHS's FP32 error moves err by a few percent at
+  tolerance 1e-6), state within 1e-6 relative L2, as for fixed steps.
+"""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle import rk
+from oracle import spectral as sp
+from tests.gpu_helpers import lib_ready, rel_l2, require_gpu, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+FLT_MIN = float(np.finfo(np.float32).tiny)
+FLT_MAX = float(np.finfo(np.float32).max)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    require_gpu()
+    lib_ready()
+
+
+def convert(x):
+    from paper_1810_10197_gb300.dns import dns_debug_f32_from_f64
+    xd = to_dev(np.asarray(x, dtype=np.float64))
+    yd = torch.empty(xd.numel(), dtype=torch.float32, device="cuda")
+    dns_debug_f32_from_f64(xd, yd)
+    torch.cuda.synchronize()
+    return yd.cpu().numpy()
+
+
+def test_conversion_matches_ieee_rounding_on_the_normal_range():
+    rng = np.random.default_rng(11)
+    n = 1 << 20
+    x = rng.uniform(1.0, 2.0, n) * np.exp2(rng.integers(-126, 128, n).astype(np.float64))
+    x *= np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    x = x[np.abs(x) <= FLT_MAX]
+    got = convert(x)
+    want = x.astype(np.float32)
+    bits = x.view(np.uint64)
+    tie = (bits & np.uint64(0x1FFFFFFF)) == np.uint64(0x10000000)
+    assert np.array_equal(got[~tie], want[~tie])
+    # a tie rounds away from zero
+    assert np.all(np.abs(got[tie].astype(np.float64)) > np.abs(x[tie]))
+
+
+def test_conversion_special_values():
+    one_tie = 1.0 + 2.0 ** -24                 # halfway between 1 and 1 + 2^-23
+    cases = [
+        (0.0, 0.0), (-0.0, -0.0), (np.inf, np.inf), (-np.inf, -np.inf),
+        (FLT_MIN, FLT_MIN), (-FLT_MIN, -FLT_MIN), (FLT_MIN * (1 - 2.0 ** -30), FLT_MIN),
+        (FLT_MIN / 2, 0.0), (-1e-40, -0.0), (1e-300, 0.0), (5e-324, 0.0),
+        (FLT_MAX, FLT_MAX), (3.5e38, np.inf), (-3.5e38, -np.inf), (1e300, np.inf),
+        (FLT_MAX + 2.0 ** 103, np.inf),         # half an ulp above the largest float
+        (one_tie, 1.0 + 2.0 ** -23), (-one_tie, -(1.0 + 2.0 ** -23)),
+        (1.0 + 3 * 2.0 ** -24, 1.0 + 2.0 ** -22), (1.0 + 2.0 ** -25, 1.0), (np.pi, np.float32(np.pi)),
+    ]
+    x = np.array([c[0] for c in cases])
+    got = convert(np.concatenate([x, [np.nan, -np.nan]]))
+    for (xi, want), g in zip(cases, got):
+        assert float(g) == want and np.signbit(g) == np.signbit(want), (xi, g, want)
+    assert np.all(np.isnan(got[-2:]))
+
+
+def attempt_err(shape, uh, nu, rtol, atol):
+    from paper_1810_10197_gb300 import Dns
+    d = Dns(*shape, nu=nu, precision="fp32_mixed")
+    d.set_state(to_dev(uh), 0.0)
+    info = d.step("BS5_ADAPTIVE", 2e-2, rtol, atol)
+    d.close()
+    return info
+
+
+def test_error_norm_fp32_arithmetic_matches_fp64_arithmetic():
+    shape, nu = (32, 32, 32), 0.01
+    g = sp.Grid(*shape)
+    uh = g.dealias(syn.random_solenoidal_hat(*shape, seed=5, k0=3.0))
+    a = attempt_err(shape, uh, nu, 1e-3, 1e-20)     # FP32 arithmetic
+    b = attempt_err(shape, uh, nu, 1e-3, 1e-31)     # FP64 arithmetic (atol below 1e-30)
+    c = attempt_err(shape, uh, nu, 0.0, 1e-5)       # pure absolute tolerance: FP32 arithmetic
+    d = attempt_err(shape, uh, nu, 1e-31, 1e-5)     # FP64 arithmetic
+    assert 0.0 < a.err < 1e3 and 0.0 < c.err < 1e3
+    assert a.err == pytest.approx(b.err, rel=1e-4)
+    assert c.err == pytest.approx(d.err, rel=1e-4)
+
+
+def test_fp32_mixed_adaptive_steps_against_oracle():
+    # ten adaptive attempts; the oracle replays the accepted step sizes from the attempt trace
+    # in FP64, so the difference is the FP32 arithmetic alone (RHS, stage increments)
+    from paper_1810_10197_gb300 import Dns
+    shape, nu, tol = (64, 64, 64), 1e-3, 1e-6
+    g = sp.Grid(*shape)
+    uh = g.dealias(syn.random_solenoidal_hat(*shape, seed=1, k0=4.0))
+    d = Dns(*shape, nu=nu, precision="fp32_mixed")
+    d.set_state(to_dev(uh), 0.0)
+    d.set_trace(100)
+    d.enqueue_attempts(10, "BS5_ADAPTIVE", tol, tol, t_end=1e9, h0=1e-3)
+    info = d.info()
+    tr = d.trace()
+    assert info.n_acc >= 8 and len(tr) == 10
+    u = uh.copy()
+    for row in tr[tr[:, 3] > 0.5]:
+        u = rk.rk_attempt(lambda y: sp.rhs(g, y, nu), u, float(row[1]), rk.TABLEAUS["BS5"], None)[0]
+    assert float(np.sum(tr[tr[:, 3] > 0.5, 1])) == pytest.approx(info.t, rel=1e-14)
+    assert rel_l2(d.get_state(), u) < 1e-6
+    d.close()

@@ -55,17 +55,25 @@ def test_bf16_rounding():
 
 
 def test_dataset_targets_are_hindsight_steps():
-    # history: accepted steps with known errors; target = log(h_{n+1} (0.8^5/err_{n+1})^(1/5) / h_n)
+    # history: accepted steps with known errors; target = log(h_{n+1} (e*/err_{n+1})^(1/5) / h_n)
+    # with e* the PI factor's fixed point: 0.8 e^(-0.14) e^(0.08) = 1, e* = 0.8^(1/0.06)
+    estar = math.exp(math.log(0.8) / 0.06)
+    assert abs(estar - 0.024257) < 1e-6 and abs(mlp.E_TARGET - estar) < 1e-14
+    assert abs(rk.pi_factor(estar, estar, False) - 1.0) < 1e-13
     steps = [(0, 0.1, 0.5, True), (0.1, 0.1, 0.5, True), (0.2, 0.1, 0.25, True), (0.3, 0.2, 2.0, False),
-             (0.3, 0.12, 0.4, True), (0.42, 0.15, 0.32768, True)]
+             (0.3, 0.12, 0.4, True), (0.42, 0.15, estar, True)]
     X, T = mlp.dataset_from_history(steps)
     assert X.shape == (1, 16)
-    # n = 3 (4th accepted: h=0.12, err 0.4), next accepted h=0.15 with err = 0.8^5 -> h* = 0.15;
+    # n = 3 (4th accepted: h=0.12, err 0.4), next accepted h=0.15 with err = e* -> h* = 0.15;
     # the PI factor at n is 0.8 * 0.4^(-0.14) * 0.25^(0.08): err_prev is the accepted step
     # before it (0.25), not the rejected attempt (2.0).  Worked by hand: 0.4^-0.14 = 1.136872,
     # 0.25^0.08 = 0.895025, factor 0.814023, target log(1.25) - log(0.814023) = 0.428910
     assert abs(T[0] - (math.log(0.15 / 0.12) - math.log(0.8 * 0.4 ** -0.14 * 0.25 ** 0.08))) < 1e-12
     assert abs(T[0] - 0.428910) < 2e-6
+    # a next error 32x the target halves the hindsight step: the target drops by log 2
+    steps[-1] = (0.42, 0.15, 32 * estar, True)
+    X2, T2 = mlp.dataset_from_history(steps)
+    assert abs(T2[0] - (T[0] - math.log(2.0))) < 1e-12
     # features: newest accepted err 0.4 with 1 rejection before it
     assert abs(X[0, 0] - math.log10(0.4)) < 1e-12 and X[0, 2] == 1.0 and X[0, 1] == 0.0
 
