@@ -194,19 +194,23 @@ template <> __device__ __forceinline__ dw2 cmulc<dw2>(dw2 a, dw2 b) {
 // Conversions between FP64 and FP32 with integer bit arithmetic.  On this part FP64<->FP32
 // conversion instructions issue on the FP64 pipe (1/64 of the FP32 rate); the mixed-precision
 // passes convert every mode, so they use these instead.
-//   d2f_bits: round to nearest (ties away from zero), |x| < 2^-126 flushes to signed zero,
-//             overflow gives inf, NaN stays NaN.
+//   d2f_bits: significand rounded to 24 bits (nearest, ties away from zero), exponent
+//             rebiased from 1023 to 127; magnitudes that round below 2^-126 give a signed
+//             zero, above the largest float an infinity; NaN stays NaN.  Branch-free.
 //   f2d_bits: exact; FP32 subnormals flush to signed zero; inf/NaN preserved.
 __device__ __forceinline__ float d2f_bits(double x) {
-  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-  const unsigned s = hi & 0x80000000u, a = hi & 0x7fffffffu;
-  if (a < (897u << 20)) return __uint_as_float(s);
-  if (a >= (1151u << 20)) {
-    const bool nan = a > 0x7ff00000u || (a == 0x7ff00000u && lo != 0u);
-    return __uint_as_float(s | 0x7f800000u | (nan ? 0x400000u : 0u));
-  }
-  unsigned b = ((a - (896u << 20)) << 3) | (lo >> 29);
-  b += (lo >> 28) & 1u;
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const unsigned s = (unsigned)(bits >> 32) & 0x80000000u;
+  const unsigned long long mag = bits & 0x7FFFFFFFFFFFFFFFull;
+  const unsigned long long r = mag + (1ull << 28);                  // + half a float ulp
+  const unsigned rhi = (unsigned)(r >> 32), rlo = (unsigned)r;
+  const unsigned e = rhi >> 20;                                      // exponent after rounding
+  // bits 31..23 of (r >> 29) hold e mod 512; subtracting 896 << 23 modulo 2^32 leaves e - 896
+  // in the float's exponent field for 897 <= e <= 1150, the normal float range
+  unsigned b = __funnelshift_r(rlo, rhi, 29) - (896u << 23);
+  b = e < 897u ? 0u : b;
+  b = e > 1150u ? 0x7F800000u : b;
+  b = mag > 0x7FF0000000000000ull ? 0x7FC00000u : b;
   return __uint_as_float(s | b);
 }
 __device__ __forceinline__ double f2d_bits(float f) {

@@ -488,7 +488,9 @@ k_p3(const PassArgs a) {
 
 // ------------------------------------------------------------------------------------------
 // P5: x-forward + epilogue.  grid ceil(MyMz/TC).  The Leray projection runs in the
-// transform precision T; the viscous term, forcing and the output k are FP64.
+// transform precision T; the viscous term and forcing are FP64 (FP64 and double-word forms)
+// or FP32 (FP32-mixed form, whose k carries FP32 accuracy and is read back as FP32 by its
+// stage sums and error norm: the epilogue then has no FP64 instruction); k is stored FP64.
 // Boussinesq (Section 3.2): fields 0..2 hold (u x omega)^, 3..5 (rho u)^; the buoyancy
 // -Ri rho e_z (kappa != 0) enters before the projection, and the density equation is
 // -i kappa . (rho u)^ - kappa_d |kappa|^2 rho.
@@ -496,8 +498,14 @@ k_p3(const PassArgs a) {
 template <typename T, int NX> __host__ __device__ constexpr int p5_cols(bool bouss) {
   return bouss ? p1_cols<T, NX>() / 2 : p1_cols<T, NX>();
 }
+// FP32 lines up to 256 points: two CTAs per SM (the register budget of two 768-thread
+// blocks, which these fit without spilling; the shared-memory tile fits twice), so that one
+// CTA's loads overlap the other's transform and epilogue.  Longer lines would spill.
+template <typename T, int NX> __host__ __device__ constexpr int p5_min_blocks() {
+  return std::is_same<T, float>::value && NX <= 256 ? 2 : 1;
+}
 template <typename T, int NX, bool BOUSS>
-__global__ void __launch_bounds__(FftPlan<NX>::G * 3 * p1_cols<T, NX>())
+__global__ void __launch_bounds__(FftPlan<NX>::G * 3 * p1_cols<T, NX>(), p5_min_blocks<T, NX>())
 k_p5(const PassArgs a) {
   using V = v2_t<T>;
   constexpr int TC = p5_cols<T, NX>(BOUSS);
@@ -579,12 +587,21 @@ k_p5(const PassArgs a) {
       n2 = mk<V>(n2.x - kzz * dr, n2.y - kzz * di);
     }
     const double2 y0 = Y[off], y1 = Y[off + g.M], y2 = Y[off + 2 * g.M];
-    const double k2d = k2x[ix] + k2yz[c];
-    double vis = -a.nu * k2d;
-    if (fc != 0.0 && k2 > (T)0 && k2 <= kf2) vis += fc;
-    K[off] = make_double2(fma(vis, y0.x, to_f64(n0.x)), fma(vis, y0.y, to_f64(n0.y)));
-    K[off + g.M] = make_double2(fma(vis, y1.x, to_f64(n1.x)), fma(vis, y1.y, to_f64(n1.y)));
-    K[off + 2 * g.M] = make_double2(fma(vis, y2.x, to_f64(n2.x)), fma(vis, y2.y, to_f64(n2.y)));
+    double k2d = 0.0;
+    if constexpr (std::is_same<T, float>::value) {
+      T vis = -(T)a.nu * k2;
+      if (fc != 0.0 && k2 > (T)0 && k2 <= kf2) vis += (T)fc;
+      K[off] = make_double2(to_f64(fmaf(vis, d2f_bits(y0.x), n0.x)), to_f64(fmaf(vis, d2f_bits(y0.y), n0.y)));
+      K[off + g.M] = make_double2(to_f64(fmaf(vis, d2f_bits(y1.x), n1.x)), to_f64(fmaf(vis, d2f_bits(y1.y), n1.y)));
+      K[off + 2 * g.M] = make_double2(to_f64(fmaf(vis, d2f_bits(y2.x), n2.x)), to_f64(fmaf(vis, d2f_bits(y2.y), n2.y)));
+    } else {
+      k2d = k2x[ix] + k2yz[c];
+      double vis = -a.nu * k2d;
+      if (fc != 0.0 && k2 > (T)0 && k2 <= kf2) vis += fc;
+      K[off] = make_double2(fma(vis, y0.x, to_f64(n0.x)), fma(vis, y0.y, to_f64(n0.y)));
+      K[off + g.M] = make_double2(fma(vis, y1.x, to_f64(n1.x)), fma(vis, y1.y, to_f64(n1.y)));
+      K[off + 2 * g.M] = make_double2(fma(vis, y2.x, to_f64(n2.x)), fma(vis, y2.y, to_f64(n2.y)));
+    }
     if (off == 0 && a.ctrl && a.kslot >= SLOT_K1 && a.ctrl->inject_rhs >= 0) {
       // debug fault injection (dns_debug_inject): this evaluation's running index is the count
       // before the attempt plus its position in the attempt (k_1 first when it is evaluated)
@@ -599,9 +616,14 @@ k_p5(const PassArgs a) {
       const V f0 = lines[(3 * TC + c) * LD + pos], f1 = lines[(4 * TC + c) * LD + pos], f2 = lines[(5 * TC + c) * LD + pos];
       V kd = mk<V>(kx * f0.x + ky * f1.x + kzz * f2.x, kx * f0.y + ky * f1.y + kzz * f2.y);
       if (fsc != (T)1) kd = cscale(kd, fsc);
-      const double visr = -a.kappa_d * k2d;
       // -i (kappa . F) = (Im, -Re)
-      K[off + 3 * g.M] = make_double2(fma(visr, rho.x, to_f64(kd.y)), fma(visr, rho.y, -to_f64(kd.x)));
+      if constexpr (std::is_same<T, float>::value) {
+        const T visr = -(T)a.kappa_d * k2;
+        K[off + 3 * g.M] = make_double2(to_f64(fmaf(visr, d2f_bits(rho.x), kd.y)), to_f64(fmaf(visr, d2f_bits(rho.y), -kd.x)));
+      } else {
+        const double visr = -a.kappa_d * k2d;
+        K[off + 3 * g.M] = make_double2(fma(visr, rho.x, to_f64(kd.y)), fma(visr, rho.y, -to_f64(kd.x)));
+      }
     }
   }
 }

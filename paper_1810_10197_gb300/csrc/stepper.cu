@@ -13,32 +13,13 @@ inline int grid_for(long long n, int threads, int cap) {
   return (int)(b < cap ? b : cap);
 }
 
-// FP32 value of an FP64 number computed from its bits with integer instructions only (the
-// FP64 pipe of this part issues at 1/64 of the FP32 rate, and a hardware conversion would
-// use it): the significand rounded to 24 bits (nearest, ties away from zero), the exponent
-// rebiased from 1023 to 127.  Magnitudes that round below the smallest normal float give a
-// signed zero, above the largest float an infinity; NaN stays NaN.
-__device__ __forceinline__ float f32_from_bits(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
-  const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
-  const unsigned long long a = mag + (1ull << 28);                  // + half a float ulp
-  const unsigned int ahi = (unsigned int)(a >> 32), alo = (unsigned int)a;
-  const unsigned int e = ahi >> 20;                                  // exponent after rounding
-  // bits 31..23 of (a >> 29) hold e mod 512; subtracting 896 << 23 modulo 2^32 leaves e - 896
-  // in the float's exponent field for 897 <= e <= 1150, the normal float range
-  unsigned int r = __funnelshift_r(alo, ahi, 29) - (896u << 23);
-  r = e < 897u ? 0u : r;
-  r = e > 1150u ? 0x7F800000u : r;
-  r = mag > 0x7FF0000000000000ull ? 0x7FC00000u : r;
-  return __uint_as_float(r | sign);
-}
-
 // Y = u + h * sum_j coef_j k_j, terms added in ascending j (fused multiply-adds: on this part
 // the FP64 pipe, not HBM, bounds this kernel, so the instruction count matters).
 // F32 (the FP32-mixed form, whose k_j carry FP32 accuracy): the increment sum_j (h coef_j) k_j
-// is formed in FP32 from FP32 values of the k_j and added to u in FP64; its rounding (~6e-8 of
-// the increment) lies below the error the k_j already carry, and the kernel becomes HBM-bound.
+// is formed in FP32 from FP32 values of the k_j (d2f_bits: integer instructions, since a
+// hardware conversion would use the FP64 pipe, which issues at 1/64 of the FP32 rate) and
+// added to u in FP64; its rounding (~6e-8 of the increment) lies below the error the k_j
+// already carry, and the kernel becomes HBM-bound.
 template <int NT, bool F32>
 __global__ void k_stage_sum(const StageArgs a) {
   const DnsCtrl* c = a.ctrl;
@@ -56,12 +37,12 @@ __global__ void k_stage_sum(const StageArgs a) {
     for (int j = 0; j < NT; ++j) hc[j] = (float)(h * a.coef[j]);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n2; i += stride) {
       double2 kv = k[0][i];
-      float ar = hc[0] * f32_from_bits(kv.x), ai = hc[0] * f32_from_bits(kv.y);
+      float ar = hc[0] * d2f_bits(kv.x), ai = hc[0] * d2f_bits(kv.y);
 #pragma unroll
       for (int j = 1; j < NT; ++j) {
         kv = k[j][i];
-        ar = fmaf(hc[j], f32_from_bits(kv.x), ar);
-        ai = fmaf(hc[j], f32_from_bits(kv.y), ai);
+        ar = fmaf(hc[j], d2f_bits(kv.x), ar);
+        ai = fmaf(hc[j], d2f_bits(kv.y), ai);
       }
       const double2 uv = u[i];
       y[i] = make_double2(uv.x + (double)ar, uv.y + (double)ai);
@@ -141,16 +122,16 @@ __global__ void __launch_bounds__(kRedThreads) k_err_partials(const ErrArgs a) {
       for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.M; i += stride) {
         const long long idx = q * a.M + i;
         double2 kv = k[0][idx];
-        float er = hc[0] * f32_from_bits(kv.x), ei = hc[0] * f32_from_bits(kv.y);
+        float er = hc[0] * d2f_bits(kv.x), ei = hc[0] * d2f_bits(kv.y);
 #pragma unroll
         for (int j = 1; j < NT; ++j) {
           kv = k[j][idx];
-          er = fmaf(hc[j], f32_from_bits(kv.x), er);
-          ei = fmaf(hc[j], f32_from_bits(kv.y), ei);
+          er = fmaf(hc[j], d2f_bits(kv.x), er);
+          ei = fmaf(hc[j], d2f_bits(kv.y), ei);
         }
         const double2 a0 = u0[idx], a1 = u1[idx];
-        const float x0 = f32_from_bits(a0.x), y0 = f32_from_bits(a0.y);
-        const float x1 = f32_from_bits(a1.x), y1 = f32_from_bits(a1.y);
+        const float x0 = d2f_bits(a0.x), y0 = d2f_bits(a0.y);
+        const float x1 = d2f_bits(a1.x), y1 = d2f_bits(a1.y);
         const float m2 = fmaxf(fmaf(x0, x0, y0 * y0), fmaf(x1, x1, y1 * y1));
         const float inv = 1.0f / fmaf(rt, sqrtf(m2), at);
         const double tr = (double)(er * inv), ti = (double)(ei * inv);
@@ -669,7 +650,7 @@ cudaError_t launch_spectrum(const Geom& g, const double2* u, double* partials, i
 
 __global__ void k_f32_from_f64(const double* __restrict__ x, float* __restrict__ y, long long n) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[i] = f32_from_bits(x[i]);
+    y[i] = d2f_bits(x[i]);
 }
 
 template <bool F32>
