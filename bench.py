@@ -68,8 +68,10 @@ def pass_flops(n):
     }
 
 
-def pass_bytes(n, esz=16):
-    """Algorithmic HBM bytes per launch (each pass reads its input and writes its output once)."""
+def pass_bytes(n, esz=16, ksz=16):
+    """Algorithmic HBM bytes per launch (each pass reads its input and writes its output once).
+    esz: bytes per complex value of the intermediate fields; ksz: of the output k (FP32 k slots
+    of the FP32-mixed form in a step: 8)."""
     K = (n - 1) // 3
     M = (2 * K + 1) ** 2 * (K + 1)
     L1 = n * (2 * K + 1) * (K + 1)
@@ -79,7 +81,7 @@ def pass_bytes(n, esz=16):
         "p2_y_inverse": 6 * L1 * esz + 6 * L2 * esz,
         "p3_z_c2r_cross_r2c": 6 * L2 * esz + 3 * L2 * esz,
         "p4_y_forward": 3 * L2 * esz + 3 * L1 * esz,
-        "p5_x_forward_project": 3 * L1 * esz + 3 * M * 16 * 2,
+        "p5_x_forward_project": 3 * L1 * esz + 3 * M * 16 + 3 * M * ksz,
     }
 
 
@@ -90,14 +92,15 @@ BS5_STAGE_TERMS = (1, 2, 3, 4, 5, 6, 6)
 BS5_ERR_TERMS = 7
 
 
-def step_kernel_bytes(n, nc=3):
+def step_kernel_bytes(n, nc=3, ksz=16):
     """Algorithmic HBM bytes per BS5 attempt of the kernels around the passes: each stage sum
     reads u and its k_j and writes one field; the error norm reads u_n, u_{n+1} and its k_j.
-    Every field is the FP64 retained box (nc M complex values)."""
+    Fields are the retained box (nc M complex values): the state FP64 (16 bytes), the k_j ksz
+    bytes per complex value (8 in the FP32-mixed form)."""
     K = (n - 1) // 3
-    field = nc * (2 * K + 1) ** 2 * (K + 1) * 16
-    return {"stage_sum": sum(t + 2 for t in BS5_STAGE_TERMS) * field,
-            "err_norm_partials": (BS5_ERR_TERMS + 2) * field}
+    cells = nc * (2 * K + 1) ** 2 * (K + 1)
+    return {"stage_sum": sum(2 * 16 + t * ksz for t in BS5_STAGE_TERMS) * cells,
+            "err_norm_partials": (2 * 16 + BS5_ERR_TERMS * ksz) * cells}
 
 
 def load_peaks():
@@ -677,7 +680,8 @@ def run_gpu(args):
     fp32 = args.precision == "fp32_mixed"
     dwp = args.precision == "fp32x2"
     flops = pass_flops(n)
-    byts = pass_bytes(n, esz=8 if fp32 else 16)
+    ksz = 8 if (fp32 and args.mode == "step") else 16
+    byts = pass_bytes(n, esz=8 if fp32 else 16, ksz=ksz)
     names = list(flops)
     dom = max(names, key=lambda k: prof.get(k, (0, 0.0))[1])
     nl, tot_ms = prof[dom]
@@ -722,7 +726,7 @@ def run_gpu(args):
     # algorithmic bytes moved in the timed region, per kernel and for the whole step
     attempts = (i1.n_acc - i0.n_acc) + (i1.n_rej - i0.n_rej) if args.mode == "step" else 0
     moved = {k: byts[k] * n_rhs for k in byts}
-    for k, b in step_kernel_bytes(n).items():
+    for k, b in step_kernel_bytes(n, ksz=ksz).items():
         moved[k] = b * attempts
     for k, b in moved.items():
         if k in prof and prof[k][1] > 0 and b > 0:

@@ -559,6 +559,9 @@ static dns_status create_impl(const dns_config* cfg, int bouss, double kappa, do
     for (int i = 2; i <= 7; ++i) h.slot[SLOT_K1 + i - 1] = c->kfix[i];
     h.slot[SLOT_K1 + 7] = c->kk[1];
     h.done = 1; h.max_rejects = 30; h.method = DNS_BS5_ADAPTIVE; h.inject_rhs = -1;
+    // FP32-mixed: k_1..k_8 are FP32 (their readers, the stage sums and the error norm, use
+    // FP32 values of them); dns_rhs and the diagnostics keep FP64 outputs (ctrl_rhs)
+    h.k_f32 = c->precision == DNS_FP32_MIXED ? 1 : 0;
     DnsCtrl r{};
     r.slot[SLOT_Y] = c->rhs_in;
     r.slot[SLOT_K1] = c->rhs_out;
@@ -933,7 +936,13 @@ dns_status dns_save(dns_ctx* c, const char* path) {
   CK(cudaMemcpy(u.data(), c->uu[h.parity], n * sizeof(double2), cudaMemcpyDeviceToHost), "state download");
   if (h.k1_valid) {
     k1.resize(n);
-    CK(cudaMemcpy(k1.data(), c->kk[h.parity], n * sizeof(double2), cudaMemcpyDeviceToHost), "k1 download");
+    if (h.k_f32) {   // FP32 k slots: widen (exact) so that the file layout is the same in every form
+      std::vector<float2> k32(n);
+      CK(cudaMemcpy(k32.data(), c->kk[h.parity], n * sizeof(float2), cudaMemcpyDeviceToHost), "k1 download");
+      for (size_t i = 0; i < n; ++i) k1[i] = make_double2(k32[i].x, k32[i].y);
+    } else {
+      CK(cudaMemcpy(k1.data(), c->kk[h.parity], n * sizeof(double2), cudaMemcpyDeviceToHost), "k1 download");
+    }
   }
   FILE* f = std::fopen(path, "wb");
   if (!f) return fail(c, DNS_ERR_ARG, std::string("dns_save: cannot open ") + path);
@@ -1002,7 +1011,15 @@ dns_status dns_load(dns_ctx* c, const char* path) {
   if (h.ctrl_kind == 2 && !d.mlp)
     return fail(c, DNS_ERR_STATE, "dns_load: the checkpoint uses the learned controller; set its parameters first");
   CK(cudaMemcpy(c->uu[0], u.data(), n * sizeof(double2), cudaMemcpyHostToDevice), "state upload");
-  if (h.k1_valid) CK(cudaMemcpy(c->kk[0], k1.data(), n * sizeof(double2), cudaMemcpyHostToDevice), "k1 upload");
+  if (h.k1_valid) {
+    if (d.k_f32) {
+      std::vector<float2> k32(n);
+      for (size_t i = 0; i < n; ++i) k32[i] = make_float2((float)k1[i].x, (float)k1[i].y);
+      CK(cudaMemcpy(c->kk[0], k32.data(), n * sizeof(float2), cudaMemcpyHostToDevice), "k1 upload");
+    } else {
+      CK(cudaMemcpy(c->kk[0], k1.data(), n * sizeof(double2), cudaMemcpyHostToDevice), "k1 upload");
+    }
+  }
   d.t = h.t; d.h = h.h; d.h_try = h.h_try; d.err = h.err; d.err_prev = h.err_prev; d.rtol = h.rtol; d.atol = h.atol;
   for (int q = 0; q < 4; ++q) d.errc[q] = h.errc[q];
   d.method = h.method; d.k1_valid = h.k1_valid ? 1 : 0; d.after_reject = h.after_reject; d.accepted = h.accepted;

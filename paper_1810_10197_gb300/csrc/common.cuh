@@ -282,7 +282,7 @@ struct DnsCtrl {
   int after_reject;
   int accepted;
   int max_rejects;
-  int pad_;
+  int k_f32;            // the k slots hold FP32 complex values (FP32-mixed form)
   long long n_rhs, n_acc, n_rej, n_attempts, rejects_in_row;
   // controller variant: 0 = Section 2.2.1, 1 = PI, 2 = learned proposal (MLP)
   int ctrl_kind;
@@ -307,6 +307,10 @@ __device__ __forceinline__ const double2* resolve_in(const double2* p, const Dns
 }
 __device__ __forceinline__ double2* resolve_out(double2* p, const DnsCtrl* c, int slot) {
   return (c && slot >= 0) ? c->slot[slot] : p;
+}
+// whether a pass output resolved through a controller slot is stored as FP32 complex
+__device__ __forceinline__ bool out_is_f32(const DnsCtrl* c, int slot) {
+  return c && slot >= 0 && c->k_f32 != 0;
 }
 // gate: skip flags a launch may check (the k_1 evaluation runs only when needed)
 __device__ __forceinline__ bool gated_off(const DnsCtrl* c, int only_if_need_k1) {

@@ -489,8 +489,9 @@ k_p3(const PassArgs a) {
 // ------------------------------------------------------------------------------------------
 // P5: x-forward + epilogue.  grid ceil(MyMz/TC).  The Leray projection runs in the
 // transform precision T; the viscous term and forcing are FP64 (FP64 and double-word forms)
-// or FP32 (FP32-mixed form, whose k carries FP32 accuracy and is read back as FP32 by its
-// stage sums and error norm: the epilogue then has no FP64 instruction); k is stored FP64.
+// or FP32 (FP32-mixed form, whose k carries FP32 accuracy: the epilogue then has no FP64
+// instruction).  k is stored FP64, except into the FP32 k slots of an FP32-mixed context
+// (stored FP32 and read as FP32 by its stage sums and error norm).
 // Boussinesq (Section 3.2): fields 0..2 hold (u x omega)^, 3..5 (rho u)^; the buoyancy
 // -Ri rho e_z (kappa != 0) enters before the projection, and the density equation is
 // -i kappa . (rho u)^ - kappa_d |kappa|^2 rho.
@@ -520,6 +521,7 @@ k_p5(const PassArgs a) {
   const Geom& g = a.g;
   const double2* __restrict__ Y = resolve_in(a.y, a.ctrl, a.yslot);
   double2* __restrict__ K = resolve_out(a.kout, a.ctrl, a.kslot);
+  const bool k32 = out_is_f32(a.ctrl, a.kslot);   // FP32 k slots (FP32-mixed form only)
   const V* __restrict__ in = reinterpret_cast<const V*>(a.in);
   const int col0 = blockIdx.x * TC;
   const int tid = threadIdx.x, nth = blockDim.x;
@@ -591,9 +593,17 @@ k_p5(const PassArgs a) {
     if constexpr (std::is_same<T, float>::value) {
       T vis = -(T)a.nu * k2;
       if (fc != 0.0 && k2 > (T)0 && k2 <= kf2) vis += (T)fc;
-      K[off] = make_double2(to_f64(fmaf(vis, d2f_bits(y0.x), n0.x)), to_f64(fmaf(vis, d2f_bits(y0.y), n0.y)));
-      K[off + g.M] = make_double2(to_f64(fmaf(vis, d2f_bits(y1.x), n1.x)), to_f64(fmaf(vis, d2f_bits(y1.y), n1.y)));
-      K[off + 2 * g.M] = make_double2(to_f64(fmaf(vis, d2f_bits(y2.x), n2.x)), to_f64(fmaf(vis, d2f_bits(y2.y), n2.y)));
+      const float2 r0 = make_float2(fmaf(vis, d2f_bits(y0.x), n0.x), fmaf(vis, d2f_bits(y0.y), n0.y));
+      const float2 r1 = make_float2(fmaf(vis, d2f_bits(y1.x), n1.x), fmaf(vis, d2f_bits(y1.y), n1.y));
+      const float2 r2 = make_float2(fmaf(vis, d2f_bits(y2.x), n2.x), fmaf(vis, d2f_bits(y2.y), n2.y));
+      if (k32) {
+        float2* K32 = reinterpret_cast<float2*>(K);
+        K32[off] = r0; K32[off + g.M] = r1; K32[off + 2 * g.M] = r2;
+      } else {
+        K[off] = make_double2(to_f64(r0.x), to_f64(r0.y));
+        K[off + g.M] = make_double2(to_f64(r1.x), to_f64(r1.y));
+        K[off + 2 * g.M] = make_double2(to_f64(r2.x), to_f64(r2.y));
+      }
     } else {
       k2d = k2x[ix] + k2yz[c];
       double vis = -a.nu * k2d;
@@ -608,7 +618,8 @@ k_p5(const PassArgs a) {
       DnsCtrl* cw = const_cast<DnsCtrl*>(a.ctrl);
       const long long idx = cw->n_rhs + (a.kslot - SLOT_K1) - (cw->need_k1 ? 0 : 1);
       if (idx == cw->inject_rhs) {
-        K[0] = make_double2(__longlong_as_double(0x7ff8000000000000ULL), 0.0);
+        if (k32) reinterpret_cast<float2*>(K)[0] = make_float2(__uint_as_float(0x7fc00000u), 0.f);
+        else K[0] = make_double2(__longlong_as_double(0x7ff8000000000000ULL), 0.0);
         cw->inject_rhs = -1;
       }
     }
@@ -619,7 +630,9 @@ k_p5(const PassArgs a) {
       // -i (kappa . F) = (Im, -Re)
       if constexpr (std::is_same<T, float>::value) {
         const T visr = -(T)a.kappa_d * k2;
-        K[off + 3 * g.M] = make_double2(to_f64(fmaf(visr, d2f_bits(rho.x), kd.y)), to_f64(fmaf(visr, d2f_bits(rho.y), -kd.x)));
+        const float2 rr = make_float2(fmaf(visr, d2f_bits(rho.x), kd.y), fmaf(visr, d2f_bits(rho.y), -kd.x));
+        if (k32) reinterpret_cast<float2*>(K)[off + 3 * g.M] = rr;
+        else K[off + 3 * g.M] = make_double2(to_f64(rr.x), to_f64(rr.y));
       } else {
         const double visr = -a.kappa_d * k2d;
         K[off + 3 * g.M] = make_double2(fma(visr, rho.x, to_f64(kd.y)), fma(visr, rho.y, -to_f64(kd.x)));

@@ -15,11 +15,10 @@ inline int grid_for(long long n, int threads, int cap) {
 
 // Y = u + h * sum_j coef_j k_j, terms added in ascending j (fused multiply-adds: on this part
 // the FP64 pipe, not HBM, bounds this kernel, so the instruction count matters).
-// F32 (the FP32-mixed form, whose k_j carry FP32 accuracy): the increment sum_j (h coef_j) k_j
-// is formed in FP32 from FP32 values of the k_j (d2f_bits: integer instructions, since a
-// hardware conversion would use the FP64 pipe, which issues at 1/64 of the FP32 rate) and
-// added to u in FP64; its rounding (~6e-8 of the increment) lies below the error the k_j
-// already carry, and the kernel becomes HBM-bound.
+// F32 (the FP32-mixed form, whose k_j carry FP32 accuracy and are stored as FP32 complex
+// values): the increment sum_j (h coef_j) k_j is formed in FP32 and added to u in FP64; its
+// rounding (~6e-8 of the increment) lies below the error the k_j already carry, and the
+// kernel is HBM-bound (the FP64 pipe issues at 1/64 of the FP32 rate).
 template <int NT, bool F32>
 __global__ void k_stage_sum(const StageArgs a) {
   const DnsCtrl* c = a.ctrl;
@@ -32,17 +31,20 @@ __global__ void k_stage_sum(const StageArgs a) {
   for (int j = 0; j < NT; ++j) k[j] = c->slot[a.kslot[j]];
   const long long stride = (long long)gridDim.x * blockDim.x;
   if (F32) {
+    const float2* k32[NT];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) k32[j] = reinterpret_cast<const float2*>(k[j]);
     float hc[NT];
 #pragma unroll
     for (int j = 0; j < NT; ++j) hc[j] = (float)(h * a.coef[j]);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n2; i += stride) {
-      double2 kv = k[0][i];
-      float ar = hc[0] * d2f_bits(kv.x), ai = hc[0] * d2f_bits(kv.y);
+      float2 kv = k32[0][i];
+      float ar = hc[0] * kv.x, ai = hc[0] * kv.y;
 #pragma unroll
       for (int j = 1; j < NT; ++j) {
-        kv = k[j][i];
-        ar = fmaf(hc[j], d2f_bits(kv.x), ar);
-        ai = fmaf(hc[j], d2f_bits(kv.y), ai);
+        kv = k32[j][i];
+        ar = fmaf(hc[j], kv.x, ar);
+        ai = fmaf(hc[j], kv.y, ai);
       }
       const double2 uv = u[i];
       y[i] = make_double2(uv.x + (double)ar, uv.y + (double)ai);
@@ -93,9 +95,10 @@ __device__ __forceinline__ void block_sum3(double v[3], double* sh) { block_sum<
 
 // Per-block partial sums of (|e| / sc)^2 per component, e = h sum_j (b_j - bhat_j) k_j,
 // sc = atol + rtol max(|u_n|, |u_{n+1}|)  (Section 2.2.1).
-// F32 (the FP32-mixed form): e, sc and the ratio in FP32 from FP32 values of the inputs, the
-// squares accumulated in FP64; the k_j carry FP32 accuracy, so err keeps all the accuracy
-// they hold.  Nonzero tolerances outside [1e-30, 1e30] take the FP64 arithmetic.
+// F32 (the FP32-mixed form, k_j stored as FP32 complex values): e, sc and the ratio in FP32
+// (u_n, u_{n+1} converted by d2f_bits, integer instructions), the squares accumulated in
+// FP64; the k_j carry FP32 accuracy, so err keeps all the accuracy they hold.  Nonzero
+// tolerances outside [1e-30, 1e30] take FP64 arithmetic (the FP32 k_j widened exactly).
 template <int NT, bool F32>
 __global__ void __launch_bounds__(kRedThreads) k_err_partials(const ErrArgs a) {
   __shared__ double sh[4 * 32];
@@ -112,6 +115,9 @@ __global__ void __launch_bounds__(kRedThreads) k_err_partials(const ErrArgs a) {
   const bool rt_ok = rtol == 0.0 || (rtol >= 1e-30 && rtol <= 1e30);
   const bool at_ok = atol == 0.0 || (atol >= 1e-30 && atol <= 1e30);
   if (F32 && rt_ok && at_ok) {
+    const float2* k32[NT];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) k32[j] = reinterpret_cast<const float2*>(k[j]);
     float hc[NT];
 #pragma unroll
     for (int j = 0; j < NT; ++j) hc[j] = (float)(h * a.coef[j]);
@@ -121,13 +127,13 @@ __global__ void __launch_bounds__(kRedThreads) k_err_partials(const ErrArgs a) {
       if (q >= a.nc) break;
       for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.M; i += stride) {
         const long long idx = q * a.M + i;
-        double2 kv = k[0][idx];
-        float er = hc[0] * d2f_bits(kv.x), ei = hc[0] * d2f_bits(kv.y);
+        float2 kv = k32[0][idx];
+        float er = hc[0] * kv.x, ei = hc[0] * kv.y;
 #pragma unroll
         for (int j = 1; j < NT; ++j) {
-          kv = k[j][idx];
-          er = fmaf(hc[j], d2f_bits(kv.x), er);
-          ei = fmaf(hc[j], d2f_bits(kv.y), ei);
+          kv = k32[j][idx];
+          er = fmaf(hc[j], kv.x, er);
+          ei = fmaf(hc[j], kv.y, ei);
         }
         const double2 a0 = u0[idx], a1 = u1[idx];
         const float x0 = d2f_bits(a0.x), y0 = d2f_bits(a0.y);
@@ -144,11 +150,19 @@ __global__ void __launch_bounds__(kRedThreads) k_err_partials(const ErrArgs a) {
     if (q >= a.nc) break;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.M; i += stride) {
       const long long idx = q * a.M + i;
-      double2 kv = k[0][idx];
+      // F32 here: FP32 k slots, widened exactly (tolerances outside the FP32 range)
+      const auto kval = [&](int j) {
+        if (F32) {
+          const float2 v = reinterpret_cast<const float2*>(k[j])[idx];
+          return make_double2(f2d_bits(v.x), f2d_bits(v.y));
+        }
+        return k[j][idx];
+      };
+      double2 kv = kval(0);
       double er = a.coef[0] * kv.x, ei = a.coef[0] * kv.y;
 #pragma unroll
       for (int j = 1; j < NT; ++j) {
-        kv = k[j][idx];
+        kv = kval(j);
         er = fma(a.coef[j], kv.x, er);
         ei = fma(a.coef[j], kv.y, ei);
       }
@@ -335,6 +349,7 @@ __global__ void __launch_bounds__(kRedThreads) k_trace_partials(const Geom g, co
   if (c->skip || !c->trace_diag || !c->trace) return;
   const double2* __restrict__ u = c->uu[c->parity];
   const double2* __restrict__ f = c->kk[c->parity];
+  const float2* __restrict__ f32 = reinterpret_cast<const float2*>(f);   // FP32 k slots
   double v[3] = {0.0, 0.0, 0.0};
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < g.M; r += stride) {
@@ -346,7 +361,14 @@ __global__ void __launch_bounds__(kRedThreads) k_trace_partials(const Geom g, co
     const double w = kz == 0 ? 1.0 : 2.0;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      const double2 a = u[q * g.M + r], b = f[q * g.M + r];
+      const double2 a = u[q * g.M + r];
+      double2 b;
+      if (c->k_f32) {
+        const float2 b32 = f32[q * g.M + r];
+        b = make_double2(f2d_bits(b32.x), f2d_bits(b32.y));
+      } else {
+        b = f[q * g.M + r];
+      }
       const double m2 = a.x * a.x + a.y * a.y;
       v[0] += w * m2;
       v[1] += w * k2 * m2;

@@ -28,9 +28,9 @@ def _lib():
     lib_ready()
 
 
-def make(shape, uh, nu, forcing=None, t0=0.0):
+def make(shape, uh, nu, forcing=None, t0=0.0, precision="fp64"):
     from paper_1810_10197_gb300 import Dns
-    d = Dns(*shape, nu=nu, forcing=forcing)
+    d = Dns(*shape, nu=nu, forcing=forcing, precision=precision)
     d.set_state(to_dev(uh), t0)
     return d
 
@@ -44,24 +44,27 @@ def _same(a, b):
     return a.tobytes() == b.tobytes()
 
 
-@pytest.mark.parametrize("method,ctrl,h0", [("BS5_ADAPTIVE", "I", 0.5), ("DP5_ADAPTIVE", "PI", 0.5),
-                                            ("BS5_FIXED", "I", 2e-3), ("RK4", "I", 2e-3)])
-def test_resume_is_bit_for_bit(tmp_path, method, ctrl, h0):
+@pytest.mark.parametrize("method,ctrl,h0,prec", [("BS5_ADAPTIVE", "I", 0.5, "fp64"), ("DP5_ADAPTIVE", "PI", 0.5, "fp64"),
+                                                 ("BS5_FIXED", "I", 2e-3, "fp64"), ("RK4", "I", 2e-3, "fp64"),
+                                                 ("BS5_ADAPTIVE", "I", 0.5, "fp32_mixed")])
+def test_resume_is_bit_for_bit(tmp_path, method, ctrl, h0, prec):
     # 10 attempts in one context == 5 attempts, save, load into a fresh context, 5 attempts.
     # The large h0 of the adaptive runs forces rejections inside the first five attempts.
+    # FP32-mixed: the carried k_1 is held in FP32 on the device and written widened (exactly)
+    # to the file, so the resumed run is bit-identical as well.
     shape, nu, tol = (32, 32, 32), 0.01, 1e-7
     g, uh = _hit(shape)
-    a = make(shape, uh, nu)
+    a = make(shape, uh, nu, precision=prec)
     a.set_controller(ctrl)
     a.enqueue_attempts(10, method, tol, tol, h0=h0)
     ia, ua = a.info(), a.get_state()
-    b = make(shape, uh, nu)
+    b = make(shape, uh, nu, precision=prec)
     b.set_controller(ctrl)
     b.enqueue_attempts(5, method, tol, tol, h0=h0)
     mid = b.info()
     path = str(tmp_path / "mid.ckpt")
     b.save(path)
-    c = make(shape, np.zeros_like(uh), nu)     # a different state, overwritten by the load
+    c = make(shape, np.zeros_like(uh), nu, precision=prec)     # a different state, overwritten by the load
     c.load(path)
     ic0 = c.info()
     assert (ic0.t, ic0.h_next, ic0.n_rhs, ic0.n_acc, ic0.n_rej) == \

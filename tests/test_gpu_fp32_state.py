@@ -11,7 +11,9 @@ k_j, produced by an integer-bit conversion.  Checked here:
   amplifies FP32 rounding (6e-8 of the terms) by h|k|/|e| ~ 1e2, bound 1e-4 relative;
 * ten adaptive FP32-mixed steps against the oracle replaying the same step sizes (decisions
   need not match the oracle's own: the RHS's FP32 error moves err by a few percent at
-  tolerance 1e-6), state within 1e-6 relative L2, as for fixed steps.
+  tolerance 1e-6), state within 1e-6 relative L2, as for fixed steps;
+* the trace's dissipation rate, read from the carried k_1 (FP32 in this form), against the
+  oracle within 1e-5.
 """
 import numpy as np
 import pytest
@@ -116,4 +118,22 @@ def test_fp32_mixed_adaptive_steps_against_oracle():
         u = rk.rk_attempt(lambda y: sp.rhs(g, y, nu), u, float(row[1]), rk.TABLEAUS["BS5"], None)[0]
     assert float(np.sum(tr[tr[:, 3] > 0.5, 1])) == pytest.approx(info.t, rel=1e-14)
     assert rel_l2(d.get_state(), u) < 1e-6
+    d.close()
+
+
+def test_trace_dissipation_from_fp32_k_slots():
+    # the attempt trace's dissipation rate reads the carried k_1, held in FP32 in this form
+    from paper_1810_10197_gb300 import Dns
+    from oracle import diag
+    shape, nu = (32, 32, 32), 0.01
+    g = sp.Grid(*shape)
+    uh = g.dealias(syn.taylor_green_3d_hat(*shape) + 0.1 * syn.random_solenoidal_hat(*shape, seed=2, k0=3.0))
+    d = Dns(*shape, nu=nu, precision="fp32_mixed")
+    d.set_state(to_dev(uh), 0.0)
+    d.set_trace(100, diagnostics=True)
+    d.integrate(0.2, "BS5_ADAPTIVE", 1e-6, 1e-6, h0=0.01)
+    tr = d.trace()
+    u = d.get_state()
+    assert tr[-1, 5] == pytest.approx(diag.energy(g, u), rel=1e-12)
+    assert tr[-1, 7] == pytest.approx(diag.dissipation(g, u, sp.rhs(g, u, nu)), rel=1e-5)
     d.close()

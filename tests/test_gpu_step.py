@@ -261,13 +261,15 @@ def test_injected_nan_is_rejected_and_the_run_recovers(index):
     assert rel_l2(d.get_state(), ref.u) < 1e-12
 
 
-def test_injected_nan_in_a_carried_k1_ends_nonfinite():
+@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
+def test_injected_nan_in_a_carried_k1_ends_nonfinite(precision):
     # the very first evaluation is k_1 of u_0; a first-same-as-last pair reuses it after the
     # rejection, so every retry fails: DNS_ERR_NONFINITE after max_rejects, as in the oracle
+    # (FP32-mixed: the NaN lands in the FP32 k slot)
     shape, nu = (16, 16, 16), 0.01
     g = sp.Grid(*shape)
     uh = g.dealias(syn.random_solenoidal_hat(*shape, seed=9, k0=3.0))
-    d = make(shape, uh, nu)
+    d = make(shape, uh, nu, precision=precision)
     d.debug_inject(0)
     st, info = d.integrate(1.0, "BS5_ADAPTIVE", 1e-6, 1e-6, h0=0.05, max_rejects=3, check=False)
     assert st == 4 and info.n_rej == 4 and info.t == 0.0 and info.n_rhs == 8 + 3 * 7
