@@ -68,20 +68,21 @@ def pass_flops(n):
     }
 
 
-def pass_bytes(n, esz=16, ksz=16):
+def pass_bytes(n, esz=16, ksz=16, ysz=16):
     """Algorithmic HBM bytes per launch (each pass reads its input and writes its output once).
-    esz: bytes per complex value of the intermediate fields; ksz: of the output k (FP32 k slots
-    of the FP32-mixed form in a step: 8)."""
+    esz: bytes per complex value of the intermediate fields; ksz: of the output k; ysz: of the
+    stage input the x passes read (the FP32-mixed step keeps k and the intermediate stage
+    inputs in FP32: 8 bytes, and 6 of the 7 stage inputs of an attempt are intermediate)."""
     K = (n - 1) // 3
     M = (2 * K + 1) ** 2 * (K + 1)
     L1 = n * (2 * K + 1) * (K + 1)
     L2 = n * n * (K + 1)
     return {
-        "p1_x_inverse_curl": 3 * M * 16 + 6 * L1 * esz,
+        "p1_x_inverse_curl": 3 * M * ysz + 6 * L1 * esz,
         "p2_y_inverse": 6 * L1 * esz + 6 * L2 * esz,
         "p3_z_c2r_cross_r2c": 6 * L2 * esz + 3 * L2 * esz,
         "p4_y_forward": 3 * L2 * esz + 3 * L1 * esz,
-        "p5_x_forward_project": 3 * L1 * esz + 3 * M * 16 + 3 * M * ksz,
+        "p5_x_forward_project": 3 * L1 * esz + 3 * M * ysz + 3 * M * ksz,
     }
 
 
@@ -95,11 +96,14 @@ BS5_ERR_TERMS = 7
 def step_kernel_bytes(n, nc=3, ksz=16):
     """Algorithmic HBM bytes per BS5 attempt of the kernels around the passes: each stage sum
     reads u and its k_j and writes one field; the error norm reads u_n, u_{n+1} and its k_j.
-    Fields are the retained box (nc M complex values): the state FP64 (16 bytes), the k_j ksz
-    bytes per complex value (8 in the FP32-mixed form)."""
+    Fields are the retained box (nc M complex values): the state FP64 (16 bytes); the k_j and
+    the intermediate stage inputs ksz bytes per complex value (8 in the FP32-mixed form);
+    u_{n+1}, the last stage sum's output, FP64."""
     K = (n - 1) // 3
     cells = nc * (2 * K + 1) ** 2 * (K + 1)
-    return {"stage_sum": sum(2 * 16 + t * ksz for t in BS5_STAGE_TERMS) * cells,
+    last = len(BS5_STAGE_TERMS) - 1
+    return {"stage_sum": sum(16 + t * ksz + (16 if i == last else ksz)
+                             for i, t in enumerate(BS5_STAGE_TERMS)) * cells,
             "err_norm_partials": (2 * 16 + BS5_ERR_TERMS * ksz) * cells}
 
 
@@ -681,7 +685,8 @@ def run_gpu(args):
     dwp = args.precision == "fp32x2"
     flops = pass_flops(n)
     ksz = 8 if (fp32 and args.mode == "step") else 16
-    byts = pass_bytes(n, esz=8 if fp32 else 16, ksz=ksz)
+    ysz = (6 * 8 + 16) / 7 if (fp32 and args.mode == "step") else 16
+    byts = pass_bytes(n, esz=8 if fp32 else 16, ksz=ksz, ysz=ysz)
     names = list(flops)
     dom = max(names, key=lambda k: prof.get(k, (0, 0.0))[1])
     nl, tot_ms = prof[dom]

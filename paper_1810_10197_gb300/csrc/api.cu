@@ -559,9 +559,10 @@ static dns_status create_impl(const dns_config* cfg, int bouss, double kappa, do
     for (int i = 2; i <= 7; ++i) h.slot[SLOT_K1 + i - 1] = c->kfix[i];
     h.slot[SLOT_K1 + 7] = c->kk[1];
     h.done = 1; h.max_rejects = 30; h.method = DNS_BS5_ADAPTIVE; h.inject_rhs = -1;
-    // FP32-mixed: k_1..k_8 are FP32 (their readers, the stage sums and the error norm, use
-    // FP32 values of them); dns_rhs and the diagnostics keep FP64 outputs (ctrl_rhs)
-    h.k_f32 = c->precision == DNS_FP32_MIXED ? 1 : 0;
+    // FP32-mixed: k_1..k_8 and the stage-input scratch are FP32 (their readers -- stage sums,
+    // error norm, the x passes -- use FP32 values of them); dns_rhs and the diagnostics keep
+    // FP64 inputs and outputs (ctrl_rhs)
+    h.f32_slots = c->precision == DNS_FP32_MIXED ? 1 : 0;
     DnsCtrl r{};
     r.slot[SLOT_Y] = c->rhs_in;
     r.slot[SLOT_K1] = c->rhs_out;
@@ -936,7 +937,7 @@ dns_status dns_save(dns_ctx* c, const char* path) {
   CK(cudaMemcpy(u.data(), c->uu[h.parity], n * sizeof(double2), cudaMemcpyDeviceToHost), "state download");
   if (h.k1_valid) {
     k1.resize(n);
-    if (h.k_f32) {   // FP32 k slots: widen (exact) so that the file layout is the same in every form
+    if (h.f32_slots) {   // FP32 k slots: widen (exact) so that the file layout is the same in every form
       std::vector<float2> k32(n);
       CK(cudaMemcpy(k32.data(), c->kk[h.parity], n * sizeof(float2), cudaMemcpyDeviceToHost), "k1 download");
       for (size_t i = 0; i < n; ++i) k1[i] = make_double2(k32[i].x, k32[i].y);
@@ -1012,7 +1013,7 @@ dns_status dns_load(dns_ctx* c, const char* path) {
     return fail(c, DNS_ERR_STATE, "dns_load: the checkpoint uses the learned controller; set its parameters first");
   CK(cudaMemcpy(c->uu[0], u.data(), n * sizeof(double2), cudaMemcpyHostToDevice), "state upload");
   if (h.k1_valid) {
-    if (d.k_f32) {
+    if (d.f32_slots) {
       std::vector<float2> k32(n);
       for (size_t i = 0; i < n; ++i) k32[i] = make_float2((float)k1[i].x, (float)k1[i].y);
       CK(cudaMemcpy(c->kk[0], k32.data(), n * sizeof(float2), cudaMemcpyHostToDevice), "k1 upload");

@@ -282,7 +282,8 @@ struct DnsCtrl {
   int after_reject;
   int accepted;
   int max_rejects;
-  int k_f32;            // the k slots hold FP32 complex values (FP32-mixed form)
+  int f32_slots;        // k_1..k_8 and the stage-input scratch hold FP32 complex values
+                        // (FP32-mixed form); u_n and u_{n+1} are FP64 in every form
   long long n_rhs, n_acc, n_rej, n_attempts, rejects_in_row;
   // controller variant: 0 = Section 2.2.1, 1 = PI, 2 = learned proposal (MLP)
   int ctrl_kind;
@@ -308,9 +309,19 @@ __device__ __forceinline__ const double2* resolve_in(const double2* p, const Dns
 __device__ __forceinline__ double2* resolve_out(double2* p, const DnsCtrl* c, int slot) {
   return (c && slot >= 0) ? c->slot[slot] : p;
 }
-// whether a pass output resolved through a controller slot is stored as FP32 complex
+// whether a pass output (a k slot) resolved through a controller slot is stored as FP32 complex
 __device__ __forceinline__ bool out_is_f32(const DnsCtrl* c, int slot) {
-  return c && slot >= 0 && c->k_f32 != 0;
+  return c && slot >= 0 && c->f32_slots != 0;
+}
+// whether a pass input resolved through a controller slot is the FP32 stage-input scratch
+__device__ __forceinline__ bool in_is_f32(const DnsCtrl* c, int slot) {
+  return c && slot == SLOT_Y && c->f32_slots != 0;
+}
+// a stage-input value as FP32: read from the FP32 scratch, or rounded from FP64 (d2f_bits)
+__device__ __forceinline__ float2 y_as_f32(const double2* Y, size_t i, bool y32) {
+  if (y32) return reinterpret_cast<const float2*>(Y)[i];
+  const double2 d = Y[i];
+  return make_float2(d2f_bits(d.x), d2f_bits(d.y));
 }
 // gate: skip flags a launch may check (the k_1 evaluation runs only when needed)
 __device__ __forceinline__ bool gated_off(const DnsCtrl* c, int only_if_need_k1) {

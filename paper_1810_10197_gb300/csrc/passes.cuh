@@ -184,6 +184,7 @@ k_p1(const PassArgs a) {
   if (gated_off(a.ctrl, a.gate_k1)) return;
   const Geom& g = a.g;
   const double2* __restrict__ Y = resolve_in(a.y, a.ctrl, a.yslot);
+  const bool y32 = in_is_f32(a.ctrl, a.yslot);   // FP32 stage-input scratch (FP32-mixed form)
   V* __restrict__ out = reinterpret_cast<V*>(a.out);
   const int tid = threadIdx.x, nth = blockDim.x;
   constexpr int NTH = G * 3 * TC;
@@ -202,8 +203,13 @@ k_p1(const PassArgs a) {
         const int ix = i / TC3, c = i - ix * TC3, col = c0 + c;
         V f = zero2<V>();
         if (col < g.MyMz) {
-          const double2 d = Y[3 * g.M + (size_t)ix * g.MyMz + col];
-          f = cscale(mk<V>(from_f64<T>(d.x), from_f64<T>(d.y)), s);
+          const size_t yi = 3 * g.M + (size_t)ix * g.MyMz + col;
+          if constexpr (std::is_same<T, float>::value) {
+            f = cscale(y_as_f32(Y, yi, y32), s);
+          } else {
+            const double2 d = Y[yi];
+            f = cscale(mk<V>(from_f64<T>(d.x), from_f64<T>(d.y)), s);
+          }
         }
         lines[c * LD + pidx<V>(ix <= g.Kx ? ix : NX - g.Mx + ix)] = f;
       }
@@ -234,10 +240,15 @@ k_p1(const PassArgs a) {
     V u0 = zero2<V>(), u1 = u0, u2 = u0, w0 = u0, w1 = u0, w2 = u0;
     if (ok) {
       const size_t off = (size_t)ix * g.MyMz + col;
-      const double2 d0 = Y[off], d1 = Y[off + g.M], d2 = Y[off + 2 * g.M];
-      const V y0 = mk<V>(from_f64<T>(d0.x), from_f64<T>(d0.y));
-      const V y1 = mk<V>(from_f64<T>(d1.x), from_f64<T>(d1.y));
-      const V y2 = mk<V>(from_f64<T>(d2.x), from_f64<T>(d2.y));
+      V y0, y1, y2;
+      if constexpr (std::is_same<T, float>::value) {
+        y0 = y_as_f32(Y, off, y32); y1 = y_as_f32(Y, off + g.M, y32); y2 = y_as_f32(Y, off + 2 * g.M, y32);
+      } else {
+        const double2 d0 = Y[off], d1 = Y[off + g.M], d2 = Y[off + 2 * g.M];
+        y0 = mk<V>(from_f64<T>(d0.x), from_f64<T>(d0.y));
+        y1 = mk<V>(from_f64<T>(d1.x), from_f64<T>(d1.y));
+        y2 = mk<V>(from_f64<T>(d2.x), from_f64<T>(d2.y));
+      }
       u0 = cscale(y0, s); u1 = cscale(y1, s); u2 = cscale(y2, s);
       const T kx = sx * (T)signed_mode(ix, g.Kx, g.Mx);
       // omega = i kappa x Y, scaled by 1/(nx ny nz): i (kappa x u) with u already scaled
@@ -522,6 +533,7 @@ k_p5(const PassArgs a) {
   const double2* __restrict__ Y = resolve_in(a.y, a.ctrl, a.yslot);
   double2* __restrict__ K = resolve_out(a.kout, a.ctrl, a.kslot);
   const bool k32 = out_is_f32(a.ctrl, a.kslot);   // FP32 k slots (FP32-mixed form only)
+  const bool y32 = in_is_f32(a.ctrl, a.yslot);    // FP32 stage-input scratch (same)
   const V* __restrict__ in = reinterpret_cast<const V*>(a.in);
   const int col0 = blockIdx.x * TC;
   const int tid = threadIdx.x, nth = blockDim.x;
@@ -573,11 +585,17 @@ k_p5(const PassArgs a) {
     const T k2 = kx * kx + ky * ky + kzz * kzz;
     const size_t off = (size_t)ix * g.MyMz + col;
     double2 rho = make_double2(0.0, 0.0);
+    float2 rho32 = make_float2(0.f, 0.f);
     if constexpr (BOUSS) {
-      rho = Y[off + 3 * g.M];
-      if (k2 > (T)0) {
-        const T ri = (T)a.ri;
-        n2 = mk<V>(n2.x - ri * from_f64<T>(rho.x), n2.y - ri * from_f64<T>(rho.y));
+      if constexpr (std::is_same<T, float>::value) {
+        rho32 = y_as_f32(Y, off + 3 * g.M, y32);
+        if (k2 > (T)0) n2 = mk<V>(n2.x - (T)a.ri * rho32.x, n2.y - (T)a.ri * rho32.y);
+      } else {
+        rho = Y[off + 3 * g.M];
+        if (k2 > (T)0) {
+          const T ri = (T)a.ri;
+          n2 = mk<V>(n2.x - ri * from_f64<T>(rho.x), n2.y - ri * from_f64<T>(rho.y));
+        }
       }
     }
     if (k2 > (T)0) {
@@ -588,14 +606,14 @@ k_p5(const PassArgs a) {
       n1 = mk<V>(n1.x - ky * dr, n1.y - ky * di);
       n2 = mk<V>(n2.x - kzz * dr, n2.y - kzz * di);
     }
-    const double2 y0 = Y[off], y1 = Y[off + g.M], y2 = Y[off + 2 * g.M];
     double k2d = 0.0;
     if constexpr (std::is_same<T, float>::value) {
       T vis = -(T)a.nu * k2;
       if (fc != 0.0 && k2 > (T)0 && k2 <= kf2) vis += (T)fc;
-      const float2 r0 = make_float2(fmaf(vis, d2f_bits(y0.x), n0.x), fmaf(vis, d2f_bits(y0.y), n0.y));
-      const float2 r1 = make_float2(fmaf(vis, d2f_bits(y1.x), n1.x), fmaf(vis, d2f_bits(y1.y), n1.y));
-      const float2 r2 = make_float2(fmaf(vis, d2f_bits(y2.x), n2.x), fmaf(vis, d2f_bits(y2.y), n2.y));
+      const float2 y0 = y_as_f32(Y, off, y32), y1 = y_as_f32(Y, off + g.M, y32), y2 = y_as_f32(Y, off + 2 * g.M, y32);
+      const float2 r0 = make_float2(fmaf(vis, y0.x, n0.x), fmaf(vis, y0.y, n0.y));
+      const float2 r1 = make_float2(fmaf(vis, y1.x, n1.x), fmaf(vis, y1.y, n1.y));
+      const float2 r2 = make_float2(fmaf(vis, y2.x, n2.x), fmaf(vis, y2.y, n2.y));
       if (k32) {
         float2* K32 = reinterpret_cast<float2*>(K);
         K32[off] = r0; K32[off + g.M] = r1; K32[off + 2 * g.M] = r2;
@@ -605,6 +623,7 @@ k_p5(const PassArgs a) {
         K[off + 2 * g.M] = make_double2(to_f64(r2.x), to_f64(r2.y));
       }
     } else {
+      const double2 y0 = Y[off], y1 = Y[off + g.M], y2 = Y[off + 2 * g.M];
       k2d = k2x[ix] + k2yz[c];
       double vis = -a.nu * k2d;
       if (fc != 0.0 && k2 > (T)0 && k2 <= kf2) vis += fc;
@@ -630,7 +649,7 @@ k_p5(const PassArgs a) {
       // -i (kappa . F) = (Im, -Re)
       if constexpr (std::is_same<T, float>::value) {
         const T visr = -(T)a.kappa_d * k2;
-        const float2 rr = make_float2(fmaf(visr, d2f_bits(rho.x), kd.y), fmaf(visr, d2f_bits(rho.y), -kd.x));
+        const float2 rr = make_float2(fmaf(visr, rho32.x, kd.y), fmaf(visr, rho32.y, -kd.x));
         if (k32) reinterpret_cast<float2*>(K)[off + 3 * g.M] = rr;
         else K[off + 3 * g.M] = make_double2(to_f64(rr.x), to_f64(rr.y));
       } else {

@@ -31,6 +31,9 @@ __global__ void k_stage_sum(const StageArgs a) {
   for (int j = 0; j < NT; ++j) k[j] = c->slot[a.kslot[j]];
   const long long stride = (long long)gridDim.x * blockDim.x;
   if (F32) {
+    // an intermediate stage input goes to the FP32 scratch (the x passes read it as FP32);
+    // u_{n+1} stays FP64
+    const bool y32 = a.yslot == SLOT_Y && c->f32_slots;
     const float2* k32[NT];
 #pragma unroll
     for (int j = 0; j < NT; ++j) k32[j] = reinterpret_cast<const float2*>(k[j]);
@@ -47,7 +50,8 @@ __global__ void k_stage_sum(const StageArgs a) {
         ai = fmaf(hc[j], kv.y, ai);
       }
       const double2 uv = u[i];
-      y[i] = make_double2(uv.x + (double)ar, uv.y + (double)ai);
+      if (y32) reinterpret_cast<float2*>(y)[i] = make_float2(d2f_bits(uv.x) + ar, d2f_bits(uv.y) + ai);
+      else y[i] = make_double2(uv.x + (double)ar, uv.y + (double)ai);
     }
     return;
   }
@@ -363,7 +367,7 @@ __global__ void __launch_bounds__(kRedThreads) k_trace_partials(const Geom g, co
     for (int q = 0; q < 3; ++q) {
       const double2 a = u[q * g.M + r];
       double2 b;
-      if (c->k_f32) {
+      if (c->f32_slots) {
         const float2 b32 = f32[q * g.M + r];
         b = make_double2(f2d_bits(b32.x), f2d_bits(b32.y));
       } else {
@@ -475,6 +479,7 @@ __global__ void __launch_bounds__(kRedThreads) k_forcing_coef(const Geom g, DnsC
   __shared__ double sh[3 * 32];
   if (gated_off(c, gate_k1)) return;
   const double2* __restrict__ Y = c->slot[yslot];
+  const bool y32 = in_is_f32(c, yslot);   // FP32 stage-input scratch (FP32-mixed form)
   const int bx = min(g.Kx, (int)floor(kf / g.sx)), by = min(g.Ky, (int)floor(kf / g.sy));
   const int bz = min(g.Kz, (int)floor(kf / g.sz));
   const int nxb = 2 * bx + 1, nyb = 2 * by + 1, nzb = bz + 1;
@@ -490,7 +495,13 @@ __global__ void __launch_bounds__(kRedThreads) k_forcing_coef(const Geom g, DnsC
     const double w = mz == 0 ? 1.0 : 2.0;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      const double2 y = Y[q * g.M + off];
+      double2 y;
+      if (y32) {
+        const float2 y2 = reinterpret_cast<const float2*>(Y)[q * g.M + off];
+        y = make_double2(f2d_bits(y2.x), f2d_bits(y2.y));
+      } else {
+        y = Y[q * g.M + off];
+      }
       v[q] += w * (y.x * y.x + y.y * y.y);
     }
   }
@@ -670,7 +681,7 @@ cudaError_t launch_spectrum(const Geom& g, const double2* u, double* partials, i
   return cudaGetLastError();
 }
 
-__global__ void k_f32_from_f64(const double* __restrict__ x, float* __restrict__ y, long long n) {
+__global__ void f32_slots_from_f64(const double* __restrict__ x, float* __restrict__ y, long long n) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     y[i] = d2f_bits(x[i]);
 }
@@ -709,7 +720,7 @@ cudaError_t launch_stage_sum(const StageArgs& a, cudaStream_t s) {
 
 cudaError_t launch_f32_from_f64(const double* x, float* y, long long n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_f32_from_f64<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(x, y, n);
+  f32_slots_from_f64<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(x, y, n);
   return cudaGetLastError();
 }
 
