@@ -99,9 +99,10 @@ __device__ __forceinline__ void block_sum3(double v[3], double* sh) { block_sum<
 
 // Per-block partial sums of (|e| / sc)^2 per component, e = h sum_j (b_j - bhat_j) k_j,
 // sc = atol + rtol max(|u_n|, |u_{n+1}|)  (Section 2.2.1).
-// F32 (the FP32-mixed form, k_j stored as FP32 complex values): e, sc and the ratio in FP32
-// (u_n, u_{n+1} converted by d2f_bits, integer instructions), the squares accumulated in
-// FP64; the k_j carry FP32 accuracy, so err keeps all the accuracy they hold.  Nonzero
+// F32 (the FP32-mixed form, k_j stored as FP32 complex values): e, sc, the ratio and each
+// thread's sum of squares in FP32 (u_n, u_{n+1} converted by d2f_bits, integer
+// instructions), the block and grid sums in FP64; the k_j carry FP32 accuracy, so err keeps
+// all the accuracy they hold.  Nonzero
 // tolerances outside [1e-30, 1e30] take FP64 arithmetic (the FP32 k_j widened exactly).
 template <int NT, bool F32>
 __global__ void __launch_bounds__(kRedThreads) k_err_partials(const ErrArgs a) {
@@ -129,6 +130,9 @@ __global__ void __launch_bounds__(kRedThreads) k_err_partials(const ErrArgs a) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (q >= a.nc) break;
+      // a thread's terms (M / (blocks x threads), about 8 at 256^3) are summed in FP32 and
+      // added to the FP64 partial once: no FP64 instruction per mode
+      float accf = 0.f;
       for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.M; i += stride) {
         const long long idx = q * a.M + i;
         float2 kv = k32[0][idx];
@@ -144,9 +148,10 @@ __global__ void __launch_bounds__(kRedThreads) k_err_partials(const ErrArgs a) {
         const float x1 = d2f_bits(a1.x), y1 = d2f_bits(a1.y);
         const float m2 = fmaxf(fmaf(x0, x0, y0 * y0), fmaf(x1, x1, y1 * y1));
         const float inv = 1.0f / fmaf(rt, sqrtf(m2), at);
-        const double tr = (double)(er * inv), ti = (double)(ei * inv);
-        acc[q] = fma(tr, tr, fma(ti, ti, acc[q]));
+        const float tr = er * inv, ti = ei * inv;
+        accf = fmaf(tr, tr, fmaf(ti, ti, accf));
       }
+      acc[q] = f2d_bits(accf);
     }
   } else {
 #pragma unroll
