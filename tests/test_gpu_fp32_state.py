@@ -137,3 +137,27 @@ def test_trace_dissipation_from_fp32_k_slots():
     assert tr[-1, 5] == pytest.approx(diag.energy(g, u), rel=1e-12)
     assert tr[-1, 7] == pytest.approx(diag.dissipation(g, u, sp.rhs(g, u, nu)), rel=1e-5)
     d.close()
+
+
+@pytest.mark.parametrize("method,h0", [("RK4", 4e-3), ("DP5_ADAPTIVE", 1e-3)])
+def test_fp32_mixed_rk4_and_dp5_against_oracle(method, h0):
+    # the other stage structures through the FP32 slots: RK4 (one-term stage sums, four k
+    # slots, no error norm) and DP5 (seven stages, six error terms); the oracle replays the
+    # accepted step sizes in FP64
+    from paper_1810_10197_gb300 import Dns
+    shape, nu, tol = (48, 48, 48), 2e-3, 1e-6
+    g = sp.Grid(*shape)
+    uh = g.dealias(syn.random_solenoidal_hat(*shape, seed=4, k0=3.0))
+    d = Dns(*shape, nu=nu, precision="fp32_mixed")
+    d.set_state(to_dev(uh), 0.0)
+    d.set_trace(100)
+    d.enqueue_attempts(8, method, tol, tol, t_end=1e9, h0=h0)
+    tr = d.trace()
+    acc = tr[tr[:, 3] > 0.5]
+    assert len(acc) >= 6
+    tab = rk.TABLEAUS["RK4" if method == "RK4" else "DP5"]
+    u = uh.copy()
+    for row in acc:
+        u = rk.rk_attempt(lambda y: sp.rhs(g, y, nu), u, float(row[1]), tab, None)[0]
+    assert rel_l2(d.get_state(), u) < 1e-6
+    d.close()
