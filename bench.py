@@ -71,7 +71,7 @@ def pass_flops(n):
 def pass_bytes(n, esz=16, ksz=16, ysz=16):
     """Algorithmic HBM bytes per launch (each pass reads its input and writes its output once).
     esz: bytes per complex value of the intermediate fields; ksz: of the output k; ysz: of the
-    stage input the x passes read (the FP32-mixed step keeps k and the intermediate stage
+    stage input the x passes read (the fp32 form's step keeps k and the intermediate stage
     inputs in FP32: 8 bytes, and 6 of the 7 stage inputs of an attempt are intermediate)."""
     K = (n - 1) // 3
     M = (2 * K + 1) ** 2 * (K + 1)
@@ -86,6 +86,10 @@ def pass_bytes(n, esz=16, ksz=16, ysz=16):
     }
 
 
+# arithmetic of each form: fp32_mixed transforms in FP32 with FP64 k, stage sums and error
+# norm; fp32 also keeps k, the intermediate stage inputs and the increments in FP32
+DTYPES = {"fp64": "f64", "fp32_mixed": "f32+f64", "fp32x2": "f32x2+f64", "fp32": "f32+f64state"}
+
 # Nonzero stage coefficients of the Bogacki-Shampine 5(4) pair (Appendix A): terms of the
 # stage sums forming the inputs of stages 2..8 (the last one is u_{n+1}), and the terms of
 # the embedded error e = h sum_j (b_j - bhat_j) k_j.
@@ -97,7 +101,7 @@ def step_kernel_bytes(n, nc=3, ksz=16):
     """Algorithmic HBM bytes per BS5 attempt of the kernels around the passes: each stage sum
     reads u and its k_j and writes one field; the error norm reads u_n, u_{n+1} and its k_j.
     Fields are the retained box (nc M complex values): the state FP64 (16 bytes); the k_j and
-    the intermediate stage inputs ksz bytes per complex value (8 in the FP32-mixed form);
+    the intermediate stage inputs ksz bytes per complex value (8 in the fp32 form);
     u_{n+1}, the last stage sum's output, FP64."""
     K = (n - 1) // 3
     cells = nc * (2 * K + 1) ** 2 * (K + 1)
@@ -321,7 +325,7 @@ def run_ensemble(args):
     sim = len(all_specs) * t_end
     out = {"metric": METRIC, "value": n_rhs / batched_s, "unit": UNIT, "n_gpus": ws, "steps": 1,
            "warmup": 1, "ms_per_step": batched_s * 1e3, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": {"fp64": "f64", "fp32_mixed": "f32+f64", "fp32x2": "f32x2+f64"}[prec],
+           "vs_baseline": None, "dtype": DTYPES[prec],
            "data": "synthetic",
            "config": {"workload": f"ensemble_{len(all_specs)}x(24x64^3,24x96^3,16x128^3)_bs5_tol1e-6_to_t{t_end:g}",
                       "precision": prec, "tiles": tiles, "parallelism": f"instances sharded over {ws} rank(s)"},
@@ -352,7 +356,7 @@ def run_accuracy(args):
     """Simulated time per GPU-second at a fixed final-state L2 error on the Taylor-Green vortex
     at 256^3, nu = 1/1600, t in [0, T] (or the forced HIT flow with --flow hit).  Error-versus-
     cost curves (Section 3's comparison) for BS5 adaptive over tolerances, RK4 over halving
-    steps, DP5, the FP32-mixed and the double-word forms, all against a time-converged FP64
+    steps, DP5, the FP32-mixed, fp32 and double-word forms, all against a time-converged FP64
     reference (BS5 at tol 1e-10); comparisons at equal error interpolate each curve in log-log.
     Energy and enstrophy are traced every step."""
     import torch
@@ -398,7 +402,8 @@ def run_accuracy(args):
                 "accepted": int(i.n_acc), "rejected": int(i.n_rej), "gpu_seconds": sec,
                 "sim_time_per_gpu_s": T / sec}
 
-    curves = {"bs5_fp64": [], "rk4_fp64": [], "dp5_fp64": [], "bs5_fp32mixed": [], "bs5_fp32x2": []}
+    curves = {"bs5_fp64": [], "rk4_fp64": [], "dp5_fp64": [], "bs5_fp32mixed": [], "bs5_fp32": [],
+              "bs5_fp32x2": []}
     trace = None
     for tol in args.tols:
         u, i, sec, tr = run("BS5_ADAPTIVE", tol, H0, trace=(tol == TOL))
@@ -410,6 +415,8 @@ def run_accuracy(args):
     for tol in args.tols[:4]:
         u, i, sec, _ = run("BS5_ADAPTIVE", tol, H0, precision="fp32_mixed")
         curves["bs5_fp32mixed"].append(dict(tol=tol, **rec(u, i, sec)))
+        u, i, sec, _ = run("BS5_ADAPTIVE", tol, H0, precision="fp32")
+        curves["bs5_fp32"].append(dict(tol=tol, **rec(u, i, sec)))
     for tol in args.tols:
         u, i, sec, _ = run("BS5_ADAPTIVE", tol, H0, precision="fp32x2")
         curves["bs5_fp32x2"].append(dict(tol=tol, **rec(u, i, sec)))
@@ -430,13 +437,17 @@ def run_accuracy(args):
         cmp.append({"l2_error": e, "bs5_rhs": c["rhs_evals"], "rk4_rhs_at_same_error": rk_rhs,
                     "rhs_ratio_rk4_over_bs5": (rk_rhs / c["rhs_evals"]) if rk_rhs else None,
                     "bs5_sim_time_per_gpu_s": c["sim_time_per_gpu_s"], "rk4_sim_time_per_gpu_s": rk_sim})
-    fp32_vs_fp64 = []
-    for c in curves["bs5_fp32mixed"]:
-        e = c["l2_error"]
-        fp64_sim = at_error(curves["bs5_fp64"], e, "sim_time_per_gpu_s")
-        fp32_vs_fp64.append({"l2_error": e, "fp32_sim_time_per_gpu_s": c["sim_time_per_gpu_s"],
-                             "fp64_sim_time_per_gpu_s_at_same_error": fp64_sim,
-                             "speedup": (c["sim_time_per_gpu_s"] / fp64_sim) if fp64_sim else None})
+    def vs_fp64(curve):
+        out = []
+        for c in curve:
+            e = c["l2_error"]
+            fp64_sim = at_error(curves["bs5_fp64"], e, "sim_time_per_gpu_s")
+            out.append({"l2_error": e, "fp32_sim_time_per_gpu_s": c["sim_time_per_gpu_s"],
+                        "fp64_sim_time_per_gpu_s_at_same_error": fp64_sim,
+                        "speedup": (c["sim_time_per_gpu_s"] / fp64_sim) if fp64_sim else None})
+        return out
+    fp32_vs_fp64 = vs_fp64(curves["bs5_fp32mixed"])
+    fp32lean_vs_fp64 = vs_fp64(curves["bs5_fp32"])
     dw_vs_fp64 = []
     for c in curves["bs5_fp32x2"]:
         e = c["l2_error"]
@@ -458,6 +469,7 @@ def run_accuracy(args):
                       "reference": "BS5 adaptive tol 1e-10, FP64", "reference_rhs_evals": int(i_ref.n_rhs),
                       "reference_gpu_seconds": s_ref},
            "curves": curves, "bs5_vs_rk4_at_equal_error": cmp, "fp32mixed_vs_fp64_at_equal_error": fp32_vs_fp64,
+           "fp32_vs_fp64_at_equal_error": fp32lean_vs_fp64,
            "fp32x2_vs_fp64_at_equal_error": dw_vs_fp64,
            "trace_bs5_fp64_tol1e-6": trace, "wall_seconds": time.perf_counter() - t_start}
     print(json.dumps(out), flush=True)
@@ -549,7 +561,7 @@ def run_controllers(args):
                           "rhs_saving_vs_PI": (p_rhs / c["rhs_evals"]) if p_rhs else None})
     out = {"metric": METRIC, "value": rows["MLP"]["sim_time_per_gpu_s"], "unit": "sim-time/GPU-s (MLP controller)",
            "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True,
-           "dtype": {"fp64": "f64", "fp32_mixed": "f32+f64", "fp32x2": "f32x2+f64"}[args.precision],
+           "dtype": DTYPES[args.precision],
            "data": "synthetic",
            "config": {"workload": f"rayleigh_taylor_{nx}x{ny}x{nz}_atwood0.5_t0-{T_end:g}_bs5_tol1e-6",
                       "precision": args.precision,
@@ -681,11 +693,12 @@ def run_gpu(args):
 
     # ---- roofline of the dominant kernel -------------------------------------------------
     peaks, peak_src = load_peaks()
-    fp32 = args.precision == "fp32_mixed"
+    fp32 = args.precision in ("fp32_mixed", "fp32")
+    lean = args.precision == "fp32"
     dwp = args.precision == "fp32x2"
     flops = pass_flops(n)
-    ksz = 8 if (fp32 and args.mode == "step") else 16
-    ysz = (6 * 8 + 16) / 7 if (fp32 and args.mode == "step") else 16
+    ksz = 8 if (lean and args.mode == "step") else 16
+    ysz = (6 * 8 + 16) / 7 if (lean and args.mode == "step") else 16
     byts = pass_bytes(n, esz=8 if fp32 else 16, ksz=ksz, ysz=ysz)
     names = list(flops)
     dom = max(names, key=lambda k: prof.get(k, (0, 0.0))[1])
@@ -783,7 +796,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--grid", type=int, default=N_GRID)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_mixed", "fp32x2"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_mixed", "fp32x2", "fp32"])
     ap.add_argument("--flow", default="tg", choices=["tg", "hit"])
     ap.add_argument("--mode", default="step", choices=["step", "rhs"])
     ap.add_argument("--workload", default="single", choices=["single", "ensemble", "accuracy", "controllers"])

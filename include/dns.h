@@ -71,14 +71,20 @@ typedef enum { DNS_RK4 = 0, DNS_BS5_FIXED = 1, DNS_BS5_ADAPTIVE = 2, DNS_DP5_FIX
                DNS_DP5_ADAPTIVE = 4 } dns_method;
 
 /* DNS_FP64: every step in double precision.  DNS_FP32_MIXED: the transforms and the
- * nonlinear term in single precision; state, stage sums, projection, viscous term, error
- * norm and step control in double precision.  DNS_FP32X2: the transforms, the nonlinear term
+ * nonlinear term in single precision; state, stage sums, viscous term, error norm and step
+ * control in double precision (the projection in single precision, on the transformed
+ * product).  DNS_FP32: as DNS_FP32_MIXED, and further the derivatives k_i, the intermediate
+ * stage inputs, the stage increments, the projection epilogue (viscous term, forcing) and
+ * the embedded error combination in single precision: the k_i carry single-precision
+ * accuracy in both forms, so this form keeps the same error floor and moves about half the
+ * bytes outside the transforms; the state u_n, the update u_{n+1} = u_n + increment, the
+ * error norm's sums and step control stay double.  DNS_FP32X2: the transforms, the nonlinear term
  * and the projection in double-word arithmetic -- each number an unevaluated sum of two FP32
  * values, about 48 significant bits (rounding near 2^-47 per operation instead of FP64's
  * 2^-53) at the FP32 instruction rate; state, stage sums, viscous term, error norm and step
  * control in double precision.  DNS_FP32X2 needs transform lengths of 32 or more on every
  * axis (else DNS_ERR_UNSUPPORTED).  The paper fixes no precision; its runs were FP64. */
-typedef enum { DNS_FP64 = 0, DNS_FP32_MIXED = 1, DNS_FP32X2 = 2 } dns_precision;
+typedef enum { DNS_FP64 = 0, DNS_FP32_MIXED = 1, DNS_FP32X2 = 2, DNS_FP32 = 3 } dns_precision;
 
 /* Forcing (Section 3.3.1 injects energy into 0 < |kappa| <= kf).  kind 0: none.  kind 1:
  * constant power as a right-hand-side term F_k = power/(2 E_f) uhat_k on 0 < |kappa| <= kf,

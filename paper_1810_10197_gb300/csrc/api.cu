@@ -186,9 +186,12 @@ dns_status alloc(dns_ctx* c, void** p, size_t bytes) {
 }
 
 // twiddle table of one axis (layout: axis_twiddle_turns), each entry rounded once from
+// the transforms run in FP32 (both single-precision forms share their kernels and tiles)
+static bool fp32_transforms(int p) { return p == DNS_FP32_MIXED || p == DNS_FP32; }
+
 // long double
 dns_status make_twiddles(dns_ctx* c, int n, bool zaxis, void** out) {
-  const bool f32 = c->precision == DNS_FP32_MIXED, dwp = c->precision == DNS_FP32X2;
+  const bool f32 = fp32_transforms(c->precision), dwp = c->precision == DNS_FP32X2;
   const size_t esz = f32 ? sizeof(float2) : sizeof(double2);
   const int cnt = std::max(1, axis_twiddle_count(n, zaxis));
   std::vector<unsigned char> host(cnt * esz, 0);
@@ -216,7 +219,8 @@ dns_status make_twiddles(dns_ctx* c, int n, bool zaxis, void** out) {
 
 cudaError_t pass(dns_ctx* c, int which, const PassArgs& a) {
   switch (c->precision) {
-    case DNS_FP32_MIXED: return launch_pass<float>(which, a, c->stream);
+    case DNS_FP32_MIXED:
+    case DNS_FP32: return launch_pass<float>(which, a, c->stream);
     case DNS_FP32X2: return launch_pass<dw>(which, a, c->stream);
     default: return launch_pass<double>(which, a, c->stream);
   }
@@ -240,6 +244,7 @@ dns_status enqueue_rhs(dns_ctx* c, DnsCtrl* ctrl, int yslot, int kslot, int gate
   a.yslot = yslot;
   a.kslot = kslot;
   a.nu = c->nu;
+  a.epi32 = c->precision == DNS_FP32 ? 1 : 0;
   a.kf2 = c->forcing.kind == 1 ? c->forcing.kf * c->forcing.kf : 0.0;
   a.kappa_d = c->kappa_d;
   a.ri = c->ri;
@@ -272,7 +277,7 @@ dns_status enqueue_stage(dns_ctx* c, int nterms, const int* kslots, const double
   s.uslot = SLOT_U;
   s.yslot = yslot;
   s.n2 = (long long)c->g.nc * c->g.M;
-  s.f32 = c->precision == DNS_FP32_MIXED ? 1 : 0;
+  s.f32 = c->precision == DNS_FP32 ? 1 : 0;
   CK(timed(c, PR_STAGE, [&] { return launch_stage_sum(s, c->stream); }), "stage sum");
   return DNS_OK;
 }
@@ -329,7 +334,7 @@ dns_status enqueue_attempt(dns_ctx* c, int method) {
   e.M = c->g.M;
   e.nc = c->g.nc;
   e.partials = c->partials;
-  e.f32 = c->precision == DNS_FP32_MIXED ? 1 : 0;
+  e.f32 = c->precision == DNS_FP32 ? 1 : 0;
   int n = 0;
   for (int j = 0; j < S; ++j) {
     if (Bw(j).p * Bh(j).q == Bh(j).p * Bw(j).q) continue;
@@ -489,7 +494,8 @@ static dns_status create_impl(const dns_config* cfg, int bouss, double kappa, do
   // 3/2 rule: the state has N frequencies per axis, the transforms run on 3N/2 points
   auto phys = [&](int n) { return pad ? ((n % 4 == 0) ? 3 * n / 2 : -1) : n; };
   if (!supported(phys(cfg->nx)) || !supported(phys(cfg->ny)) || !supported(phys(cfg->nz))) return DNS_ERR_UNSUPPORTED;
-  if (cfg->precision != DNS_FP64 && cfg->precision != DNS_FP32_MIXED && cfg->precision != DNS_FP32X2)
+  if (cfg->precision != DNS_FP64 && cfg->precision != DNS_FP32_MIXED && cfg->precision != DNS_FP32X2 &&
+      cfg->precision != DNS_FP32)
     return DNS_ERR_ARG;
   // the double-word form: transform lengths of 32 and more
   if (cfg->precision == DNS_FP32X2 && (phys(cfg->nx) < 32 || phys(cfg->ny) < 32 || phys(cfg->nz) < 32))
@@ -524,7 +530,7 @@ static dns_status create_impl(const dns_config* cfg, int bouss, double kappa, do
   g.bouss = bouss;
 
   const size_t vbytes = (size_t)g.nc * g.M * sizeof(double2);
-  const size_t esz = c->precision == DNS_FP32_MIXED ? sizeof(float2) : sizeof(double2);
+  const size_t esz = fp32_transforms(c->precision) ? sizeof(float2) : sizeof(double2);
   // physical-side field counts: inverse (u, omega [, rho]), forward (u x omega [, rho u])
   const size_t fin = g.bouss ? 7 : 6, fout = g.bouss ? 6 : 3;
   const size_t nA = std::max(fin * g.nx * g.My * g.Mz, fout * g.nx * g.ny * g.Mz);
@@ -559,10 +565,10 @@ static dns_status create_impl(const dns_config* cfg, int bouss, double kappa, do
     for (int i = 2; i <= 7; ++i) h.slot[SLOT_K1 + i - 1] = c->kfix[i];
     h.slot[SLOT_K1 + 7] = c->kk[1];
     h.done = 1; h.max_rejects = 30; h.method = DNS_BS5_ADAPTIVE; h.inject_rhs = -1;
-    // FP32-mixed: k_1..k_8 and the stage-input scratch are FP32 (their readers -- stage sums,
+    // DNS_FP32: k_1..k_8 and the stage-input scratch are FP32 (their readers -- stage sums,
     // error norm, the x passes -- use FP32 values of them); dns_rhs and the diagnostics keep
     // FP64 inputs and outputs (ctrl_rhs)
-    h.f32_slots = c->precision == DNS_FP32_MIXED ? 1 : 0;
+    h.f32_slots = c->precision == DNS_FP32 ? 1 : 0;
     DnsCtrl r{};
     r.slot[SLOT_Y] = c->rhs_in;
     r.slot[SLOT_K1] = c->rhs_out;

@@ -41,6 +41,7 @@ struct PassArgs {
   int var_p3;            // tile variant of the z pass (0: full, 1: half the lines), autotuned
   int p3_bulk;           // z pass: stage input rows with bulk copies (rows a multiple of 16 B)
   int p3_stall;          // debug: block 0's bulk-copy barrier expects this many extra bytes
+  int epi32;             // P5 epilogue (viscous term, forcing) in FP32 (DNS_FP32 form)
 };
 
 // ---- bulk copies (TMA engine) completing on a CTA-local mbarrier ---------------------------
@@ -589,6 +590,7 @@ k_p5(const PassArgs a) {
     if constexpr (BOUSS) {
       if constexpr (std::is_same<T, float>::value) {
         rho32 = y_as_f32(Y, off + 3 * g.M, y32);
+        if (!y32) rho = Y[off + 3 * g.M];   // an FP64 stage input keeps its FP64 value
         if (k2 > (T)0) n2 = mk<V>(n2.x - (T)a.ri * rho32.x, n2.y - (T)a.ri * rho32.y);
       } else {
         rho = Y[off + 3 * g.M];
@@ -607,22 +609,27 @@ k_p5(const PassArgs a) {
       n2 = mk<V>(n2.x - kzz * dr, n2.y - kzz * di);
     }
     double k2d = 0.0;
+    bool fp32_epi = false;
+    if constexpr (std::is_same<T, float>::value) fp32_epi = a.epi32 != 0;
     if constexpr (std::is_same<T, float>::value) {
-      T vis = -(T)a.nu * k2;
-      if (fc != 0.0 && k2 > (T)0 && k2 <= kf2) vis += (T)fc;
-      const float2 y0 = y_as_f32(Y, off, y32), y1 = y_as_f32(Y, off + g.M, y32), y2 = y_as_f32(Y, off + 2 * g.M, y32);
-      const float2 r0 = make_float2(fmaf(vis, y0.x, n0.x), fmaf(vis, y0.y, n0.y));
-      const float2 r1 = make_float2(fmaf(vis, y1.x, n1.x), fmaf(vis, y1.y, n1.y));
-      const float2 r2 = make_float2(fmaf(vis, y2.x, n2.x), fmaf(vis, y2.y, n2.y));
-      if (k32) {
-        float2* K32 = reinterpret_cast<float2*>(K);
-        K32[off] = r0; K32[off + g.M] = r1; K32[off + 2 * g.M] = r2;
-      } else {
-        K[off] = make_double2(to_f64(r0.x), to_f64(r0.y));
-        K[off + g.M] = make_double2(to_f64(r1.x), to_f64(r1.y));
-        K[off + 2 * g.M] = make_double2(to_f64(r2.x), to_f64(r2.y));
+      if (fp32_epi) {
+        T vis = -(T)a.nu * k2;
+        if (fc != 0.0 && k2 > (T)0 && k2 <= kf2) vis += (T)fc;
+        const float2 y0 = y_as_f32(Y, off, y32), y1 = y_as_f32(Y, off + g.M, y32), y2 = y_as_f32(Y, off + 2 * g.M, y32);
+        const float2 r0 = make_float2(fmaf(vis, y0.x, n0.x), fmaf(vis, y0.y, n0.y));
+        const float2 r1 = make_float2(fmaf(vis, y1.x, n1.x), fmaf(vis, y1.y, n1.y));
+        const float2 r2 = make_float2(fmaf(vis, y2.x, n2.x), fmaf(vis, y2.y, n2.y));
+        if (k32) {
+          float2* K32 = reinterpret_cast<float2*>(K);
+          K32[off] = r0; K32[off + g.M] = r1; K32[off + 2 * g.M] = r2;
+        } else {
+          K[off] = make_double2(to_f64(r0.x), to_f64(r0.y));
+          K[off + g.M] = make_double2(to_f64(r1.x), to_f64(r1.y));
+          K[off + 2 * g.M] = make_double2(to_f64(r2.x), to_f64(r2.y));
+        }
       }
-    } else {
+    }
+    if (!fp32_epi) {
       const double2 y0 = Y[off], y1 = Y[off + g.M], y2 = Y[off + 2 * g.M];
       k2d = k2x[ix] + k2yz[c];
       double vis = -a.nu * k2d;
@@ -647,12 +654,17 @@ k_p5(const PassArgs a) {
       V kd = mk<V>(kx * f0.x + ky * f1.x + kzz * f2.x, kx * f0.y + ky * f1.y + kzz * f2.y);
       if (fsc != (T)1) kd = cscale(kd, fsc);
       // -i (kappa . F) = (Im, -Re)
+      bool dens_done = false;
       if constexpr (std::is_same<T, float>::value) {
-        const T visr = -(T)a.kappa_d * k2;
-        const float2 rr = make_float2(fmaf(visr, rho32.x, kd.y), fmaf(visr, rho32.y, -kd.x));
-        if (k32) reinterpret_cast<float2*>(K)[off + 3 * g.M] = rr;
-        else K[off + 3 * g.M] = make_double2(to_f64(rr.x), to_f64(rr.y));
-      } else {
+        if (fp32_epi) {
+          const float visr = -(float)a.kappa_d * k2;
+          const float2 rr = make_float2(fmaf(visr, rho32.x, kd.y), fmaf(visr, rho32.y, -kd.x));
+          if (k32) reinterpret_cast<float2*>(K)[off + 3 * g.M] = rr;
+          else K[off + 3 * g.M] = make_double2(to_f64(rr.x), to_f64(rr.y));
+          dens_done = true;
+        }
+      }
+      if (!dens_done) {
         const double visr = -a.kappa_d * k2d;
         K[off + 3 * g.M] = make_double2(fma(visr, rho.x, to_f64(kd.y)), fma(visr, rho.y, -to_f64(kd.x)));
       }

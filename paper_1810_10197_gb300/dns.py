@@ -24,8 +24,8 @@ STATUS_NAMES = {0: "DNS_OK", 1: "DNS_ERR_ARG", 2: "DNS_ERR_CUDA", 3: "DNS_ERR_OO
 DNS_RK4, DNS_BS5_FIXED, DNS_BS5_ADAPTIVE, DNS_DP5_FIXED, DNS_DP5_ADAPTIVE = 0, 1, 2, 3, 4
 METHODS = {"RK4": DNS_RK4, "BS5_FIXED": DNS_BS5_FIXED, "BS5_ADAPTIVE": DNS_BS5_ADAPTIVE,
            "DP5_FIXED": DNS_DP5_FIXED, "DP5_ADAPTIVE": DNS_DP5_ADAPTIVE}
-DNS_FP64, DNS_FP32_MIXED, DNS_FP32X2 = 0, 1, 2
-PRECISIONS = {"fp64": DNS_FP64, "fp32_mixed": DNS_FP32_MIXED, "fp32x2": DNS_FP32X2}
+DNS_FP64, DNS_FP32_MIXED, DNS_FP32X2, DNS_FP32 = 0, 1, 2, 3
+PRECISIONS = {"fp64": DNS_FP64, "fp32_mixed": DNS_FP32_MIXED, "fp32x2": DNS_FP32X2, "fp32": DNS_FP32}
 SUPPORTED_N = (8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768)
 
 

@@ -48,7 +48,7 @@ def gpu_rhs(shape, L, Y, nu, kappa, ri, precision="fp64"):
 @pytest.mark.parametrize("shape,L", [((8, 8, 8), None), ((16, 16, 32), (2 * np.pi, 2 * np.pi, 4 * np.pi)),
                                      ((24, 32, 48), (2 * np.pi, 8 * np.pi / 3, 4 * np.pi)),
                                      ((64, 64, 128), (2 * np.pi, 2 * np.pi, 4 * np.pi))])
-@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed", "fp32"])
 def test_boussinesq_rhs(shape, L, precision):
     Lr = L or (2 * np.pi,) * 3
     g, Y = state(shape, Lr, 40 + shape[0])

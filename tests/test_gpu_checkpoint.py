@@ -46,12 +46,13 @@ def _same(a, b):
 
 @pytest.mark.parametrize("method,ctrl,h0,prec", [("BS5_ADAPTIVE", "I", 0.5, "fp64"), ("DP5_ADAPTIVE", "PI", 0.5, "fp64"),
                                                  ("BS5_FIXED", "I", 2e-3, "fp64"), ("RK4", "I", 2e-3, "fp64"),
-                                                 ("BS5_ADAPTIVE", "I", 0.5, "fp32_mixed")])
+                                                 ("BS5_ADAPTIVE", "I", 0.5, "fp32_mixed"),
+                                                 ("BS5_ADAPTIVE", "PI", 0.5, "fp32")])
 def test_resume_is_bit_for_bit(tmp_path, method, ctrl, h0, prec):
     # 10 attempts in one context == 5 attempts, save, load into a fresh context, 5 attempts.
     # The large h0 of the adaptive runs forces rejections inside the first five attempts.
-    # FP32-mixed: the carried k_1 is held in FP32 on the device and written widened (exactly)
-    # to the file, so the resumed run is bit-identical as well.
+    # fp32: the carried k_1 is held in FP32 on the device and written widened (exactly) to the
+    # file, so the resumed run is bit-identical as well.
     shape, nu, tol = (32, 32, 32), 0.01, 1e-7
     g, uh = _hit(shape)
     a = make(shape, uh, nu, precision=prec)

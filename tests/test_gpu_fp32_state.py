@@ -1,8 +1,10 @@
-"""Stage sums and error norm of the FP32-mixed form.
+"""Stage sums, error norm and FP32 slots of the single-precision forms.
 
-In that form the k_j carry FP32 accuracy, so the stage increments sum_j (h a_ij) k_j and the
-embedded error e = h sum_j (b_j - bhat_j) k_j are formed in FP32 from FP32 values of the FP64
-k_j, produced by an integer-bit conversion.  Checked here:
+In both single-precision forms the k_j carry FP32 accuracy.  The fp32 form (DNS_FP32)
+therefore stores k_j and the intermediate stage inputs in FP32 and forms the stage
+increments sum_j (h a_ij) k_j and the embedded error e = h sum_j (b_j - bhat_j) k_j in FP32;
+FP32-mixed keeps them FP64.  Both convert FP64 values to FP32 by an integer-bit conversion.
+Checked here:
 * the conversion against IEEE round-to-nearest (numpy float32) with its two stated
   differences: ties round away from zero, and magnitudes below the smallest normal float
   flush to a signed zero;
@@ -12,8 +14,10 @@ k_j, produced by an integer-bit conversion.  Checked here:
 * ten adaptive FP32-mixed steps against the oracle replaying the same step sizes (decisions
   need not match the oracle's own: the RHS's FP32 error moves err by a few percent at
   tolerance 1e-6), state within 1e-6 relative L2, as for fixed steps;
-* the trace's dissipation rate, read from the carried k_1 (FP32 in this form), against the
-  oracle within 1e-5.
+* the trace's dissipation rate, read from the carried k_1 (FP32 in the fp32 form), against
+  the oracle within 1e-5;
+* RK4 and DP5 in both forms (the other stage structures) against the oracle replaying the
+  same steps.
 """
 import numpy as np
 import pytest
@@ -79,7 +83,7 @@ def test_conversion_special_values():
 
 def attempt_err(shape, uh, nu, rtol, atol):
     from paper_1810_10197_gb300 import Dns
-    d = Dns(*shape, nu=nu, precision="fp32_mixed")
+    d = Dns(*shape, nu=nu, precision="fp32")
     d.set_state(to_dev(uh), 0.0)
     info = d.step("BS5_ADAPTIVE", 2e-2, rtol, atol)
     d.close()
@@ -99,14 +103,15 @@ def test_error_norm_fp32_arithmetic_matches_fp64_arithmetic():
     assert c.err == pytest.approx(d.err, rel=1e-4)
 
 
-def test_fp32_mixed_adaptive_steps_against_oracle():
+@pytest.mark.parametrize("precision", ["fp32_mixed", "fp32"])
+def test_single_precision_adaptive_steps_against_oracle(precision):
     # ten adaptive attempts; the oracle replays the accepted step sizes from the attempt trace
     # in FP64, so the difference is the FP32 arithmetic alone (RHS, stage increments)
     from paper_1810_10197_gb300 import Dns
     shape, nu, tol = (64, 64, 64), 1e-3, 1e-6
     g = sp.Grid(*shape)
     uh = g.dealias(syn.random_solenoidal_hat(*shape, seed=1, k0=4.0))
-    d = Dns(*shape, nu=nu, precision="fp32_mixed")
+    d = Dns(*shape, nu=nu, precision=precision)
     d.set_state(to_dev(uh), 0.0)
     d.set_trace(100)
     d.enqueue_attempts(10, "BS5_ADAPTIVE", tol, tol, t_end=1e9, h0=1e-3)
@@ -128,7 +133,7 @@ def test_trace_dissipation_from_fp32_k_slots():
     shape, nu = (32, 32, 32), 0.01
     g = sp.Grid(*shape)
     uh = g.dealias(syn.taylor_green_3d_hat(*shape) + 0.1 * syn.random_solenoidal_hat(*shape, seed=2, k0=3.0))
-    d = Dns(*shape, nu=nu, precision="fp32_mixed")
+    d = Dns(*shape, nu=nu, precision="fp32")
     d.set_state(to_dev(uh), 0.0)
     d.set_trace(100, diagnostics=True)
     d.integrate(0.2, "BS5_ADAPTIVE", 1e-6, 1e-6, h0=0.01)
@@ -139,8 +144,9 @@ def test_trace_dissipation_from_fp32_k_slots():
     d.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32_mixed", "fp32"])
 @pytest.mark.parametrize("method,h0", [("RK4", 4e-3), ("DP5_ADAPTIVE", 1e-3)])
-def test_fp32_mixed_rk4_and_dp5_against_oracle(method, h0):
+def test_single_precision_rk4_and_dp5_against_oracle(method, h0, precision):
     # the other stage structures through the FP32 slots: RK4 (one-term stage sums, four k
     # slots, no error norm) and DP5 (seven stages, six error terms); the oracle replays the
     # accepted step sizes in FP64
@@ -148,7 +154,7 @@ def test_fp32_mixed_rk4_and_dp5_against_oracle(method, h0):
     shape, nu, tol = (48, 48, 48), 2e-3, 1e-6
     g = sp.Grid(*shape)
     uh = g.dealias(syn.random_solenoidal_hat(*shape, seed=4, k0=3.0))
-    d = Dns(*shape, nu=nu, precision="fp32_mixed")
+    d = Dns(*shape, nu=nu, precision=precision)
     d.set_state(to_dev(uh), 0.0)
     d.set_trace(100)
     d.enqueue_attempts(8, method, tol, tol, t_end=1e9, h0=h0)
@@ -160,4 +166,34 @@ def test_fp32_mixed_rk4_and_dp5_against_oracle(method, h0):
     for row in acc:
         u = rk.rk_attempt(lambda y: sp.rhs(g, y, nu), u, float(row[1]), tab, None)[0]
     assert rel_l2(d.get_state(), u) < 1e-6
+    d.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32_mixed", "fp32"])
+def test_single_precision_boussinesq_steps_against_oracle(precision):
+    # the density component through the FP32 slots (fp32) or the FP64 ones (FP32-mixed): eight
+    # adaptive attempts of a periodic Rayleigh-Taylor field, replayed by the oracle
+    from paper_1810_10197_gb300 import Dns
+    shape, nu, kap, ri, tol = (32, 32, 64), 1e-2, 1e-2, 1.0, 1e-6
+    rho, L = syn.rayleigh_taylor_fields(*shape, seed=7, width=0.2, amplitude=1e-2)
+    g = sp.Grid(*shape, lengths=L)
+    Y = np.zeros((4, 32, 32, 33), complex)
+    Y[3] = g.dealias(g.to_spectral(rho))
+    Y[:3] = g.dealias(1e-3 * syn.random_solenoidal_hat(*shape, seed=5, k0=3.0))
+
+    def fb(y):
+        a, b = sp.rhs_boussinesq(g, y[:3], y[3], nu, kap, ri)
+        return np.concatenate([a, b[None]])
+    d = Dns(*shape, nu=nu, precision=precision, boussinesq=(kap, ri), lengths=L)
+    d.set_state(to_dev(Y), 0.0)
+    d.set_trace(100)
+    d.enqueue_attempts(8, "BS5_ADAPTIVE", tol, tol, t_end=1e9, h0=1e-2)
+    tr = d.trace()
+    acc = tr[tr[:, 3] > 0.5]
+    assert len(acc) >= 6
+    u = Y.copy()
+    for row in acc:
+        u = rk.rk_attempt(fb, u, float(row[1]), rk.TABLEAUS["BS5"], None)[0]
+    got = d.get_state()
+    assert rel_l2(got[:3], u[:3]) < 1e-5 and rel_l2(got[3], u[3]) < 1e-6
     d.close()

@@ -41,7 +41,7 @@ def _lib():
 @pytest.mark.parametrize("shape", [(8, 8, 8), (12, 12, 12), (16, 16, 16), (24, 24, 24), (32, 32, 32),
                                    (48, 48, 48), (64, 64, 64), (96, 96, 96), (128, 128, 128),
                                    (16, 24, 32), (32, 16, 8), (24, 48, 12)])
-@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed", "fp32"])
 def test_rhs_random_field(shape, precision):
     g = sp.Grid(*shape)
     uh = syn.random_solenoidal_hat(*shape, seed=sum(shape), k0=max(2.0, shape[0] / 8))

@@ -261,11 +261,11 @@ def test_injected_nan_is_rejected_and_the_run_recovers(index):
     assert rel_l2(d.get_state(), ref.u) < 1e-12
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed", "fp32"])
 def test_injected_nan_in_a_carried_k1_ends_nonfinite(precision):
     # the very first evaluation is k_1 of u_0; a first-same-as-last pair reuses it after the
     # rejection, so every retry fails: DNS_ERR_NONFINITE after max_rejects, as in the oracle
-    # (FP32-mixed: the NaN lands in the FP32 k slot)
+    # (fp32: the NaN lands in the FP32 k slot)
     shape, nu = (16, 16, 16), 0.01
     g = sp.Grid(*shape)
     uh = g.dealias(syn.random_solenoidal_hat(*shape, seed=9, k0=3.0))
