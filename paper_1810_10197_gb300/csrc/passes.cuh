@@ -185,7 +185,8 @@ k_p1(const PassArgs a) {
   if (gated_off(a.ctrl, a.gate_k1)) return;
   const Geom& g = a.g;
   const double2* __restrict__ Y = resolve_in(a.y, a.ctrl, a.yslot);
-  const bool y32 = in_is_f32(a.ctrl, a.yslot);   // FP32 stage-input scratch (FP32-mixed form)
+  // FP32 stage-input scratch (fp32 form; compile-time false for the other element types)
+  const bool y32 = std::is_same<T, float>::value && in_is_f32(a.ctrl, a.yslot);
   V* __restrict__ out = reinterpret_cast<V*>(a.out);
   const int tid = threadIdx.x, nth = blockDim.x;
   constexpr int NTH = G * 3 * TC;
@@ -514,8 +515,11 @@ template <typename T, int NX> __host__ __device__ constexpr int p5_cols(bool bou
 // FP32 lines up to 256 points: two CTAs per SM (the register budget of two 768-thread
 // blocks, which these fit without spilling; the shared-memory tile fits twice), so that one
 // CTA's loads overlap the other's transform and epilogue.  Longer lines would spill.
+// Other element types: 0, no bound (an explicit minimum of one CTA lets the allocator take
+// more registers than it does without a minimum: 225 instead of 160 for the 256-point
+// double-word kernel, one CTA per SM instead of two).
 template <typename T, int NX> __host__ __device__ constexpr int p5_min_blocks() {
-  return std::is_same<T, float>::value && NX <= 256 ? 2 : 1;
+  return std::is_same<T, float>::value && NX <= 256 ? 2 : 0;
 }
 template <typename T, int NX, bool BOUSS>
 __global__ void __launch_bounds__(FftPlan<NX>::G * 3 * p1_cols<T, NX>(), p5_min_blocks<T, NX>())
@@ -533,8 +537,9 @@ k_p5(const PassArgs a) {
   const Geom& g = a.g;
   const double2* __restrict__ Y = resolve_in(a.y, a.ctrl, a.yslot);
   double2* __restrict__ K = resolve_out(a.kout, a.ctrl, a.kslot);
-  const bool k32 = out_is_f32(a.ctrl, a.kslot);   // FP32 k slots (FP32-mixed form only)
-  const bool y32 = in_is_f32(a.ctrl, a.yslot);    // FP32 stage-input scratch (same)
+  // FP32 k slots and stage-input scratch (fp32 form; compile-time false for the other types)
+  const bool k32 = std::is_same<T, float>::value && out_is_f32(a.ctrl, a.kslot);
+  const bool y32 = std::is_same<T, float>::value && in_is_f32(a.ctrl, a.yslot);
   const V* __restrict__ in = reinterpret_cast<const V*>(a.in);
   const int col0 = blockIdx.x * TC;
   const int tid = threadIdx.x, nth = blockDim.x;
@@ -610,8 +615,18 @@ k_p5(const PassArgs a) {
     }
     double k2d = 0.0;
     bool fp32_epi = false;
-    if constexpr (std::is_same<T, float>::value) fp32_epi = a.epi32 != 0;
+    // FP64 epilogue: k = N + (-nu |kappa|^2 + forcing) Y in FP64
+    const auto epi64 = [&]() {
+      const double2 y0 = Y[off], y1 = Y[off + g.M], y2 = Y[off + 2 * g.M];
+      k2d = k2x[ix] + k2yz[c];
+      double vis = -a.nu * k2d;
+      if (fc != 0.0 && k2 > (T)0 && k2 <= kf2) vis += fc;
+      K[off] = make_double2(fma(vis, y0.x, to_f64(n0.x)), fma(vis, y0.y, to_f64(n0.y)));
+      K[off + g.M] = make_double2(fma(vis, y1.x, to_f64(n1.x)), fma(vis, y1.y, to_f64(n1.y)));
+      K[off + 2 * g.M] = make_double2(fma(vis, y2.x, to_f64(n2.x)), fma(vis, y2.y, to_f64(n2.y)));
+    };
     if constexpr (std::is_same<T, float>::value) {
+      fp32_epi = a.epi32 != 0;
       if (fp32_epi) {
         T vis = -(T)a.nu * k2;
         if (fc != 0.0 && k2 > (T)0 && k2 <= kf2) vis += (T)fc;
@@ -627,16 +642,11 @@ k_p5(const PassArgs a) {
           K[off + g.M] = make_double2(to_f64(r1.x), to_f64(r1.y));
           K[off + 2 * g.M] = make_double2(to_f64(r2.x), to_f64(r2.y));
         }
+      } else {
+        epi64();
       }
-    }
-    if (!fp32_epi) {
-      const double2 y0 = Y[off], y1 = Y[off + g.M], y2 = Y[off + 2 * g.M];
-      k2d = k2x[ix] + k2yz[c];
-      double vis = -a.nu * k2d;
-      if (fc != 0.0 && k2 > (T)0 && k2 <= kf2) vis += fc;
-      K[off] = make_double2(fma(vis, y0.x, to_f64(n0.x)), fma(vis, y0.y, to_f64(n0.y)));
-      K[off + g.M] = make_double2(fma(vis, y1.x, to_f64(n1.x)), fma(vis, y1.y, to_f64(n1.y)));
-      K[off + 2 * g.M] = make_double2(fma(vis, y2.x, to_f64(n2.x)), fma(vis, y2.y, to_f64(n2.y)));
+    } else {
+      epi64();
     }
     if (off == 0 && a.ctrl && a.kslot >= SLOT_K1 && a.ctrl->inject_rhs >= 0) {
       // debug fault injection (dns_debug_inject): this evaluation's running index is the count

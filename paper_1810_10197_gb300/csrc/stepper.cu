@@ -97,6 +97,38 @@ __device__ __forceinline__ void block_sum(double v[NV], double* sh /* NV*32 */) 
 }
 __device__ __forceinline__ void block_sum3(double v[3], double* sh) { block_sum<3>(v, sh); }
 
+// FP64 square root and reciprocal for the error norm: an FP32 seed (the approximate
+// reciprocal square root / reciprocal instructions) refined by one Newton-Raphson step in
+// FP64, y <- y (3 - x y^2) / 2 and r <- r + r (1 - x r), which squares the seed's relative
+// error (~2^-22 -> ~1e-13).  The norm needs FP64 accuracy, not correct rounding, and the
+// FP64 pipe issues at 1/64 of the FP32 rate.  Arguments outside [2^-120, 2^120] (and zero)
+// take the library operations.
+__device__ __forceinline__ bool in_seed_range(double x) {
+  const unsigned e = ((unsigned)__double2hiint(x) >> 20) & 0x7FFu;   // x >= 0 here
+  return e > 903u && e < 1143u;
+}
+__device__ __forceinline__ float rsqrt_seed(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_seed(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ double sqrt_nr(double x) {
+  if (!in_seed_range(x)) return sqrt(x);
+  const double y0 = f2d_bits(rsqrt_seed(d2f_bits(x)));
+  const double y1 = y0 * fma(-0.5 * x, y0 * y0, 1.5);
+  return x * y1;
+}
+__device__ __forceinline__ double rcp_nr(double x) {
+  if (!in_seed_range(x)) return 1.0 / x;
+  const double r0 = f2d_bits(rcp_seed(d2f_bits(x)));
+  return fma(r0, fma(-x, r0, 1.0), r0);
+}
+
 // Per-block partial sums of (|e| / sc)^2 per component, e = h sum_j (b_j - bhat_j) k_j,
 // sc = atol + rtol max(|u_n|, |u_{n+1}|)  (Section 2.2.1).
 // F32 (the FP32-mixed form, k_j stored as FP32 complex values): e, sc, the ratio and each
@@ -154,6 +186,9 @@ __global__ void __launch_bounds__(kRedThreads) k_err_partials(const ErrArgs a) {
       acc[q] = f2d_bits(accf);
     }
   } else {
+  double hc[NT];                        // h (b_j - bhat_j)
+#pragma unroll
+  for (int j = 0; j < NT; ++j) hc[j] = h * a.coef[j];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     if (q >= a.nc) break;
@@ -168,19 +203,17 @@ __global__ void __launch_bounds__(kRedThreads) k_err_partials(const ErrArgs a) {
         return k[j][idx];
       };
       double2 kv = kval(0);
-      double er = a.coef[0] * kv.x, ei = a.coef[0] * kv.y;
+      double er = hc[0] * kv.x, ei = hc[0] * kv.y;
 #pragma unroll
       for (int j = 1; j < NT; ++j) {
         kv = kval(j);
-        er = fma(a.coef[j], kv.x, er);
-        ei = fma(a.coef[j], kv.y, ei);
+        er = fma(hc[j], kv.x, er);
+        ei = fma(hc[j], kv.y, ei);
       }
-      er *= h;
-      ei *= h;
       const double2 a0 = u0[idx], a1 = u1[idx];
       const double m2 = fmax(fma(a0.x, a0.x, a0.y * a0.y), fma(a1.x, a1.x, a1.y * a1.y));
-      const double sc = fma(rtol, sqrt(m2), atol);
-      acc[q] += fma(er, er, ei * ei) / (sc * sc);
+      const double sc = fma(rtol, sqrt_nr(m2), atol);
+      acc[q] = fma(fma(er, er, ei * ei), rcp_nr(sc * sc), acc[q]);
     }
   }
   }
