@@ -78,3 +78,29 @@ def test_tile_variants_give_identical_results_and_autotune_picks_one(shape, prec
     vpy, vp3 = d.autotune(reps=2)
     assert vpy in (0, 1) and vp3 in (0, 1, 2, 3)   # z pass: bit 0 tile, bit 1 element copies
     d.close()
+
+
+def test_mixed_precision_batch_matches_single_contexts_bitwise():
+    # instances of different forms (FP64, FP32-mixed, fp32 with its FP32 k and stage-input
+    # slots) in one graph launch: each runs the same kernels in the same order as a single
+    # context of its form, so the states agree bit for bit
+    from paper_1810_10197_gb300 import Dns
+    from paper_1810_10197_gb300.dns import DnsBatch
+    specs = [(32, "fp32", 0.01, 0.2), (24, "fp32_mixed", 0.005, 0.15), (16, "fp64", 0.02, 0.25)]
+    b = DnsBatch([dict(nx=n, nu=nu, precision=p) for (n, p, nu, _) in specs])
+    fields = []
+    for i, (n, p, nu, _) in enumerate(specs):
+        g = sp.Grid(n, n, n)
+        uh = g.dealias(syn.random_solenoidal_hat(n, n, n, seed=200 + i, k0=3.0))
+        fields.append(uh)
+        b.instances[i].set_state(to_dev(uh), 0.0)
+    tols = [1e-6, 1e-6, 1e-7]
+    infos = b.integrate("BS5_ADAPTIVE", [s[3] for s in specs], tols, tols, [0.01] * 3)
+    for i, (n, p, nu, T) in enumerate(specs):
+        d = Dns(n, nu=nu, precision=p)
+        d.set_state(to_dev(fields[i]), 0.0)
+        info = d.integrate(T, "BS5_ADAPTIVE", tols[i], tols[i], h0=0.01)
+        assert (infos[i].t, infos[i].n_acc, infos[i].n_rej, infos[i].n_rhs) == (info.t, info.n_acc, info.n_rej, info.n_rhs)
+        assert b.instances[i].get_state().tobytes() == d.get_state().tobytes()
+        d.close()
+    b.close()
