@@ -149,7 +149,9 @@ DNS_API dns_status dns_set_stream(dns_ctx* ctx, void* stream);
 
 /* Load the state uhat (layout above) at time t; where = 0: device pointer, 1: host pointer.
  * Truncates to the 2/3 box, resets the step counters and the controller (next h comes from
- * dns_integrate's h0).  Asynchronous for device input, synchronous for host input. */
+ * dns_integrate's h0).  Asynchronous for device input, synchronous for host input.  A host
+ * input has only its retained modes copied (about 0.3 of the array at the 2/3 rule; pinned
+ * memory transfers by DMA at full speed, pageable memory through the driver's staging). */
 DNS_API dns_status dns_set_state(dns_ctx* ctx, const void* uhat, int where, double t);
 /* Write the current state (zero outside the 2/3 box); where as above.  Synchronous. */
 DNS_API dns_status dns_get_state(dns_ctx* ctx, void* uhat, int where);
