@@ -30,7 +30,7 @@ __global__ void k_stage_sum(const StageArgs a) {
 #pragma unroll
   for (int j = 0; j < NT; ++j) k[j] = c->slot[a.kslot[j]];
   const long long stride = (long long)gridDim.x * blockDim.x;
-  if (F32) {
+  if constexpr (F32) {
     // an intermediate stage input goes to the FP32 scratch (the x passes read it as FP32);
     // u_{n+1} stays FP64
     const bool y32 = a.yslot == SLOT_Y && c->f32_slots;
@@ -53,19 +53,19 @@ __global__ void k_stage_sum(const StageArgs a) {
       if (y32) reinterpret_cast<float2*>(y)[i] = make_float2(d2f_bits(uv.x) + ar, d2f_bits(uv.y) + ai);
       else y[i] = make_double2(uv.x + (double)ar, uv.y + (double)ai);
     }
-    return;
-  }
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n2; i += stride) {
-    double2 kv = k[0][i];
-    double ar = a.coef[0] * kv.x, ai = a.coef[0] * kv.y;
+  } else {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n2; i += stride) {
+      double2 kv = k[0][i];
+      double ar = a.coef[0] * kv.x, ai = a.coef[0] * kv.y;
 #pragma unroll
-    for (int j = 1; j < NT; ++j) {
-      kv = k[j][i];
-      ar = fma(a.coef[j], kv.x, ar);
-      ai = fma(a.coef[j], kv.y, ai);
+      for (int j = 1; j < NT; ++j) {
+        kv = k[j][i];
+        ar = fma(a.coef[j], kv.x, ar);
+        ai = fma(a.coef[j], kv.y, ai);
+      }
+      const double2 uv = u[i];
+      y[i] = make_double2(fma(h, ar, uv.x), fma(h, ai, uv.y));
     }
-    const double2 uv = u[i];
-    y[i] = make_double2(fma(h, ar, uv.x), fma(h, ai, uv.y));
   }
 }
 
