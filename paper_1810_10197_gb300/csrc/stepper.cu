@@ -14,7 +14,7 @@ inline int grid_for(long long n, int threads, int cap) {
 }
 
 // Y = u + h * sum_j coef_j k_j, terms added in ascending j (fused multiply-adds: on this part
-// the FP64 pipe, not HBM, bounds this kernel, so the instruction count matters).
+// the FP64 pipe, not HBM, bounds the FP64 version, so the instruction count matters).
 // F32 (the FP32-mixed form, whose k_j carry FP32 accuracy and are stored as FP32 complex
 // values): the increment sum_j (h coef_j) k_j is formed in FP32 and added to u in FP64; its
 // rounding (~6e-8 of the increment) lies below the error the k_j already carry, and the
@@ -54,17 +54,22 @@ __global__ void k_stage_sum(const StageArgs a) {
       else y[i] = make_double2(uv.x + (double)ar, uv.y + (double)ai);
     }
   } else {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n2; i += stride) {
-      double2 kv = k[0][i];
-      double ar = a.coef[0] * kv.x, ai = a.coef[0] * kv.y;
+    // the terms (h a_ij) k_j accumulate onto u by fused multiply-adds: NT FP64 instructions a
+    // real value (the FP64 pipe bounds this kernel); rounding at most NT/2 units in the last
+    // place of u
+    double hc[NT];
 #pragma unroll
-      for (int j = 1; j < NT; ++j) {
-        kv = k[j][i];
-        ar = fma(a.coef[j], kv.x, ar);
-        ai = fma(a.coef[j], kv.y, ai);
-      }
+    for (int j = 0; j < NT; ++j) hc[j] = h * a.coef[j];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n2; i += stride) {
       const double2 uv = u[i];
-      y[i] = make_double2(fma(h, ar, uv.x), fma(h, ai, uv.y));
+      double ar = uv.x, ai = uv.y;
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        const double2 kv = k[j][i];
+        ar = fma(hc[j], kv.x, ar);
+        ai = fma(hc[j], kv.y, ai);
+      }
+      y[i] = make_double2(ar, ai);
     }
   }
 }
