@@ -331,7 +331,7 @@ DNS_API dns_status dns_debug_stall(dns_ctx* ctx);
 DNS_API dns_status dns_debug_poison(dns_ctx* ctx, int on);
 
 /* Test hook for the FP64-to-FP32 conversion every FP32 kernel uses (the state entering the
- * x-inverse pass, the FP32-mixed stage sums, error norm and projection epilogue; integer
+ * x-inverse pass, the fp32 form's stage sums, error norm and projection epilogue; integer
  * instructions on the bits, no FP64 arithmetic): y[i] = x[i] rounded to FP32 with the
  * significand rounded to nearest (ties away from zero), magnitudes below the smallest normal
  * float flushed to a signed zero, beyond the largest float an infinity, NaN kept.

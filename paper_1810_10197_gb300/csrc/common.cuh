@@ -283,7 +283,7 @@ struct DnsCtrl {
   int accepted;
   int max_rejects;
   int f32_slots;        // k_1..k_8 and the stage-input scratch hold FP32 complex values
-                        // (FP32-mixed form); u_n and u_{n+1} are FP64 in every form
+                        // (fp32 form, DNS_FP32); u_n and u_{n+1} are FP64 in every form
   long long n_rhs, n_acc, n_rej, n_attempts, rejects_in_row;
   // controller variant: 0 = Section 2.2.1, 1 = PI, 2 = learned proposal (MLP)
   int ctrl_kind;

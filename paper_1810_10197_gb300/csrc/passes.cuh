@@ -502,8 +502,8 @@ k_p3(const PassArgs a) {
 // ------------------------------------------------------------------------------------------
 // P5: x-forward + epilogue.  grid ceil(MyMz/TC).  The Leray projection runs in the
 // transform precision T; the viscous term and forcing are FP64 (FP64 and double-word forms)
-// or FP32 (FP32-mixed form, whose k carries FP32 accuracy: the epilogue then has no FP64
-// instruction).  k is stored FP64, except into the FP32 k slots of an FP32-mixed context
+// or FP32 (fp32 form, DNS_FP32, whose k carries FP32 accuracy: the epilogue then has no FP64
+// instruction).  k is stored FP64, except into the FP32 k slots of an fp32 context
 // (stored FP32 and read as FP32 by its stage sums and error norm).
 // Boussinesq (Section 3.2): fields 0..2 hold (u x omega)^, 3..5 (rho u)^; the buoyancy
 // -Ri rho e_z (kappa != 0) enters before the projection, and the density equation is

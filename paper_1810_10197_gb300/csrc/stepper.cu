@@ -15,7 +15,7 @@ inline int grid_for(long long n, int threads, int cap) {
 
 // Y = u + h * sum_j coef_j k_j, terms added in ascending j (fused multiply-adds: on this part
 // the FP64 pipe, not HBM, bounds the FP64 version, so the instruction count matters).
-// F32 (the FP32-mixed form, whose k_j carry FP32 accuracy and are stored as FP32 complex
+// F32 (the fp32 form, DNS_FP32, whose k_j carry FP32 accuracy and are stored as FP32 complex
 // values): the increment sum_j (h coef_j) k_j is formed in FP32 and added to u in FP64; its
 // rounding (~6e-8 of the increment) lies below the error the k_j already carry, and the
 // kernel is HBM-bound (the FP64 pipe issues at 1/64 of the FP32 rate).
@@ -136,7 +136,7 @@ __device__ __forceinline__ double rcp_nr(double x) {
 
 // Per-block partial sums of (|e| / sc)^2 per component, e = h sum_j (b_j - bhat_j) k_j,
 // sc = atol + rtol max(|u_n|, |u_{n+1}|)  (Section 2.2.1).
-// F32 (the FP32-mixed form, k_j stored as FP32 complex values): e, sc, the ratio and each
+// F32 (the fp32 form, DNS_FP32, k_j stored as FP32 complex values): e, sc, the ratio and each
 // thread's sum of squares in FP32 (u_n, u_{n+1} converted by d2f_bits, integer
 // instructions), the block and grid sums in FP64; the k_j carry FP32 accuracy, so err keeps
 // all the accuracy they hold.  Nonzero
@@ -522,7 +522,7 @@ __global__ void __launch_bounds__(kRedThreads) k_forcing_coef(const Geom g, DnsC
   __shared__ double sh[3 * 32];
   if (gated_off(c, gate_k1)) return;
   const double2* __restrict__ Y = c->slot[yslot];
-  const bool y32 = in_is_f32(c, yslot);   // FP32 stage-input scratch (FP32-mixed form)
+  const bool y32 = in_is_f32(c, yslot);   // FP32 stage-input scratch (fp32 form)
   const int bx = min(g.Kx, (int)floor(kf / g.sx)), by = min(g.Ky, (int)floor(kf / g.sy));
   const int bz = min(g.Kz, (int)floor(kf / g.sz));
   const int nxb = 2 * bx + 1, nyb = 2 * by + 1, nzb = bz + 1;

@@ -18,7 +18,7 @@ struct StageArgs {
   double coef[kMaxTerms];
   int uslot, yslot;
   long long n2;          // complex elements per field set (3 M)
-  int f32;               // 1: increment formed in FP32 (FP32-mixed form)
+  int f32;               // 1: increment formed in FP32, k read as FP32 (fp32 form)
 };
 
 struct ErrArgs {
@@ -29,7 +29,7 @@ struct ErrArgs {
   long long M;              // modes per component
   int nc;                   // state components (3 or 4)
   double* partials;         // [kRedBlocks][4]
-  int f32;                  // 1: e, sc and the ratio in FP32 (FP32-mixed form)
+  int f32;                  // 1: e, sc and the ratio in FP32, k read as FP32 (fp32 form)
 };
 
 // Host launchers (stepper.cu).  All enqueue on stream s and return the launch status.

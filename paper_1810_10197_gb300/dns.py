@@ -374,7 +374,7 @@ def dns_crc32(data: bytes, crc: int = 0) -> int:
 
 
 def dns_debug_f32_from_f64(x_dev, y_dev, stream=None):
-    """The integer-bit FP64-to-FP32 conversion of the FP32-mixed stage sums (test hook)."""
+    """The integer-bit FP64-to-FP32 conversion of the single-precision kernels (test hook)."""
     h = getattr(stream, "cuda_stream", stream)
     st = load().dns_debug_f32_from_f64(C.c_void_p(_ptr(x_dev)), C.c_void_p(_ptr(y_dev)), int(x_dev.numel()),
                                        C.c_void_p(h) if h else None)
