@@ -23,7 +23,7 @@ def keep32(g):
 
 
 @pytest.mark.parametrize("shape", [(16, 16, 16), (32, 32, 32), (64, 32, 64), (128, 128, 128)])
-@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed", "fp32"])
 def test_pad32_rhs(shape, precision):
     from paper_1810_10197_gb300 import Dns
     g = sp.Grid(*shape)

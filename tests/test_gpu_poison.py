@@ -22,7 +22,8 @@ CASES = [((16, 16, 16), "fp64", {}), ((12, 24, 48), "fp64", {}), ((24, 12, 8), "
          ((32, 48, 64), "fp32_mixed", {}), ((32, 64, 48), "fp32x2", {}), ((48, 32, 32), "fp32x2", {}),
          ((32, 32, 32), "fp64", {"dealias": "3/2"}), ((32, 32, 32), "fp32x2", {"dealias": "3/2"}),
          ((16, 16, 32), "fp64", {"boussinesq": (0.01, 1.0)}),
-         ((16, 16, 32), "fp32_mixed", {"boussinesq": (0.01, 1.0)})]
+         ((16, 16, 32), "fp32_mixed", {"boussinesq": (0.01, 1.0)}),
+         ((32, 32, 32), "fp32", {"dealias": "3/2"}), ((16, 16, 32), "fp32", {"boussinesq": (0.01, 1.0)})]
 
 
 @pytest.mark.parametrize("shape,precision,kw", CASES)
@@ -45,7 +46,7 @@ def test_rhs_identical_with_poisoned_scratch(shape, precision, kw):
     d.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32x2"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32x2", "fp32"])
 def test_integrate_identical_with_poisoned_scratch(precision):
     from paper_1810_10197_gb300 import Dns
     shape = (32, 32, 32)
