@@ -184,7 +184,11 @@ class Dns:
 
     def __init__(self, nx, ny=None, nz=None, nu=0.0, precision="fp64", forcing=None,
                  lengths=None, stream=None, boussinesq=None, dealias="2/3"):
-        """boussinesq=(kappa, ri) selects the Boussinesq form (state of 4 components);
+        """precision: "fp64", "fp32_mixed" (FP32 transforms; k, stage sums and error norm in
+        FP64), "fp32" (also k, the stage inputs and the increments in FP32) or "fp32x2"
+        (double-word transforms); the state is FP64 in every form (see dns.h dns_precision).
+        forcing: (kf, power) constant-power term, or ("rescale", kf) for the post-step band
+        rescale.  boussinesq=(kappa, ri) selects the Boussinesq form (state of 4 components);
         dealias="3/2" selects the padding rule (state of nx x ny x nz frequencies)."""
         lib = load()
         ny = nx if ny is None else ny
