@@ -163,7 +163,10 @@ DNS_API dns_status dns_rhs(dns_ctx* ctx, const void* uhat_dev, void* f_dev);
 
 /* One attempted step from the current state with step size h (clipped to t_end if t_end >
  * t), embedded error norm with (rtol, atol) and the controller of Section 2.2.1 (adaptive
- * methods accept iff err <= 1 and propose h_new).  Synchronous; fills info if non-NULL. */
+ * methods accept iff err <= 1 and propose h_new).  Synchronous; fills info if non-NULL.
+ * Tolerances: rtol, atol >= 0, not both 0; the adaptive methods need atol > 0 (else
+ * DNS_ERR_ARG): modes that are zero up to rounding make a purely relative norm arbitrary.
+ * A mode with e = 0 adds nothing to the norm, also where its scale is 0. */
 DNS_API dns_status dns_step(dns_ctx* ctx, int method, double h, double rtol, double atol,
                     double t_end, dns_step_info* info);
 
@@ -359,7 +362,9 @@ DNS_API dns_status dns_query(const dns_ctx* ctx, int* K3, size_t* device_bytes);
  * address (cudaGetSymbolAddress, with that device current); make that first call before any
  * stream capture.  All calls on a device share the array and each call rewrites every part
  * it reads, so no state carries over; calls that overlap on the GPU (different streams, or
- * different host threads) race on it and must be serialised by the caller.
+ * different host threads) race on it and must be serialised by the caller.  The looked-up
+ * address is cached per device for the life of the process: after cudaDeviceReset on a
+ * device the cached address is stale, and this entry point must not be called there again.
  * Returns DNS_ERR_ARG for bad pointers or nu, DNS_ERR_CUDA if a launch fails. */
 DNS_API dns_status dns_rhs_noalloc(int nx, int ny, int nz, double nu, const void* uhat_dev, void* f_dev,
                            void* stream);

@@ -5,9 +5,11 @@ TEST INFRASTRUCTURE ONLY.  This package is a plain, slow, FP64 restatement of wh
 method computes, written from the paper for checking the CUDA implementation.  Only the
 test-suite, the smoke check and the benchmark's CPU-baseline leg may import it; the product
 (the ``paper_1810_10197_gb300`` package and its C-ABI library) never does, and the two share
-no code.  numpy's FFT is used as a library primitive for the discrete Fourier transform.
+no code.  The discrete Fourier transform is the oracle's own (``fft``), checked against the
+brute-force DFT sum.
 
 Modules
+  fft       -- the oracle's own mixed-radix Cooley-Tukey DFT and the real 3D transforms
   spectral  -- grid, wavenumbers, 2/3 dealiasing, curl, Leray projection, the right-hand
                side of Eq. (ufdef) (Section 2.1) and the Boussinesq form (Section 3.2)
   rk        -- Butcher tableaus (Appendix A), one Runge-Kutta attempt, the embedded error

@@ -157,10 +157,16 @@ def error_norm(u_old: np.ndarray, u_new: np.ndarray, e: np.ndarray, atol: float,
                nmodes: int) -> float:
     """err = max_j sqrt( (1/nmodes) sum_k (|e_jk| / sc_jk)^2 ), sc = atol + rtol max(|u_old|,|u_new|).
 
-    Axis 0 indexes the components j; the sum runs over every other axis.
+    Axis 0 indexes the components j; the sum runs over every other axis.  A mode whose
+    embedded error is exactly zero contributes zero, whatever its scale: with a purely
+    relative tolerance (atol = 0) a mode that is zero in both solutions has sc = 0, and the
+    quotient 0/0 is read as 0 (Section 2.2.1 scales the error; it does not define 0/0).  A
+    nonzero error over sc = 0 stays infinite.
     """
     sc = atol + rtol * np.maximum(np.abs(u_old), np.abs(u_new))
-    r = np.abs(e) / sc
+    ae = np.abs(e)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        r = np.where(ae == 0.0, 0.0, ae / sc)
     ncomp = e.shape[0]
     errs = [math.sqrt(float(np.sum(r[j] ** 2)) / nmodes) for j in range(ncomp)]
     return max(errs)

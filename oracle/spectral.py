@@ -1,7 +1,7 @@
 """Pseudo-spectral right-hand side, written from Section 2 of arXiv:1810.10197.
 
-TEST INFRASTRUCTURE ONLY (see the package docstring).  Plain FP64 numpy; numpy.fft is the
-DFT primitive.
+TEST INFRASTRUCTURE ONLY (see the package docstring).  Plain FP64 numpy; the DFT is the
+oracle's own Cooley-Tukey transform (oracle/fft.py), pinned against the brute-force DFT sum.
 
 Conventions (readings of the paper, each listed in the design notes):
   * Domain [0, L_x) x [0, L_y) x [0, L_z), default L = 2 pi; wavenumber kappa_a = 2 pi m / L_a
@@ -21,6 +21,8 @@ Conventions (readings of the paper, each listed in the design notes):
 from __future__ import annotations
 
 import numpy as np
+
+from . import fft as _fft
 
 
 class Grid:
@@ -58,11 +60,11 @@ class Grid:
     # ---- transforms -------------------------------------------------------------------
     def to_physical(self, fhat: np.ndarray) -> np.ndarray:
         """Inverse real DFT over the last three axes (carries 1/(nx ny nz))."""
-        return np.fft.irfftn(fhat, s=self.shape, axes=(-3, -2, -1))
+        return _fft.irfftn3(fhat, self.shape)
 
     def to_spectral(self, f: np.ndarray) -> np.ndarray:
         """Unnormalised forward real DFT over the last three axes."""
-        return np.fft.rfftn(f, axes=(-3, -2, -1))
+        return _fft.rfftn3(f)
 
     def dealias(self, fhat: np.ndarray) -> np.ndarray:
         """2/3 rule: zero every mode outside the retained box."""
@@ -216,7 +218,7 @@ def rhs_pad32(grid: Grid, uhat: np.ndarray, nu: float) -> np.ndarray:
         return out
 
     r = (P[0] * P[1] * P[2]) / float(nx * ny * nz)
-    u = np.fft.irfftn(pad(y), s=P, axes=(-3, -2, -1)) * r
-    w = np.fft.irfftn(pad(curl_hat(grid, y)), s=P, axes=(-3, -2, -1)) * r
-    nl = unpad(np.fft.rfftn(cross(u, w), axes=(-3, -2, -1))) / r * keep
+    u = _fft.irfftn3(pad(y), P) * r
+    w = _fft.irfftn3(pad(curl_hat(grid, y)), P) * r
+    nl = unpad(_fft.rfftn3(cross(u, w))) / r * keep
     return (leray(grid, nl) - nu * grid.k2 * y) * keep

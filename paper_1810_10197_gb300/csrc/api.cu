@@ -686,6 +686,13 @@ static dns_status config(dns_ctx* c, double t_end, int method, double rtol, doub
   if (!(t_end == t_end)) return fail(c, DNS_ERR_ARG, "t_end is NaN");
   if (method != DNS_RK4 && (!(rtol >= 0) || !(atol >= 0) || (rtol == 0 && atol == 0)))
     return fail(c, DNS_ERR_ARG, "tolerances must be >= 0 and not both 0");
+  // A purely relative tolerance has no usable norm on these fields: the divergence-free
+  // constraint makes some components of some modes zero up to rounding (u_x at kappa =
+  // (kx, 0, 0), for one), so their error and scale are both rounding noise and their ratio
+  // is arbitrary.  Adaptive control needs an absolute part.
+  if ((method == DNS_BS5_ADAPTIVE || method == DNS_DP5_ADAPTIVE) && !(atol > 0))
+    return fail(c, DNS_ERR_ARG, "adaptive methods need atol > 0 (a purely relative error norm is "
+                                "undefined on modes that are zero up to rounding)");
   if (!(h0 == h0)) return fail(c, DNS_ERR_ARG, "h0 is NaN");
   CK(launch_ctrl_config(c->ctrl, t_end, method, rtol, atol, h0, max_rejects > 0 ? max_rejects : 30,
                         c->stream), "controller config");

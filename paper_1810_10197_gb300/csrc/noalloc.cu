@@ -41,12 +41,17 @@ bool na_size(int n) {
   return n == 8 || n == 12 || n == 16 || n == 24 || n == 32;
 }
 
-// Per call: point the work-space controller at the work-space fields and write the
-// twiddle tables exp(-2 pi i m / n) for the three axes.
+// Per call: clear the work-space controller record, point it at the work-space fields and
+// write the twiddle tables exp(-2 pi i m / n) for the three axes.  The whole record is
+// zeroed first, so that every field the passes read (f32_slots among them) is defined by
+// this call and not by an earlier one or the array's initial contents.
 __global__ void k_na_setup(double2* base, int nx, int ny, int nz) {
   DnsCtrl* c = reinterpret_cast<DnsCtrl*>(base + kOffCtrl);
+  static_assert(sizeof(DnsCtrl) % sizeof(unsigned long long) == 0, "controller record size");
+  unsigned long long* words = reinterpret_cast<unsigned long long*>(c);
+  for (int i = threadIdx.x; i < (int)(sizeof(DnsCtrl) / sizeof(unsigned long long)); i += blockDim.x) words[i] = 0ull;
+  __syncthreads();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    for (int i = 0; i < SLOT_COUNT; ++i) c->slot[i] = nullptr;
     c->slot[SLOT_Y] = base + kOffIn;
     c->slot[SLOT_K1] = base + kOffOut;
     c->skip = 0;

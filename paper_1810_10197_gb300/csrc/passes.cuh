@@ -58,6 +58,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
+// count `bytes` of the barrier's expected transaction bytes as arrived (no data moves)
+__device__ __forceinline__ void mbar_complete_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.complete_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
   unsigned ok;
   asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
@@ -379,10 +383,10 @@ k_p3(const PassArgs a) {
   copy_tw(tw, reinterpret_cast<const V*>(a.tw), NTW);
   if (bulk) {
     __syncthreads();
+    const unsigned extra = blockIdx.x == 0 ? (unsigned)a.p3_stall : 0u;
     if (tid == 0) {
       const unsigned row_bytes = (unsigned)(Mz * sizeof(V));
       const long long rows_here = (nxy - xy0) < TL ? (nxy - xy0) : TL;
-      const unsigned extra = blockIdx.x == 0 ? (unsigned)a.p3_stall : 0u;
       mbar_expect_tx(bar, (unsigned)(NIN * rows_here) * row_bytes + extra);
       for (int f = 0; f < NIN; ++f)
         for (int l = 0; l < rows_here; ++l)
@@ -397,7 +401,11 @@ k_p3(const PassArgs a) {
           cw->status = ST_TIMEOUT;
           cw->done = 1;
         }
-        mbar_wait_bounded(bar, 0);   // let copies still in flight land before the block exits
+        // let copies still in flight land before the block exits: the bytes of the debug
+        // stall never arrive, so count them as arrived; the phase then completes exactly
+        // when every real copy has landed (the wait stays bounded for any other cause)
+        if (extra) mbar_complete_tx(bar, extra);
+        mbar_wait_bounded(bar, 0);
       }
       return;
     }

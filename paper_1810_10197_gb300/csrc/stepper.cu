@@ -186,7 +186,9 @@ __global__ void __launch_bounds__(kRedThreads) k_err_partials(const ErrArgs a) {
         const float m2 = fmaxf(fmaf(x0, x0, y0 * y0), fmaf(x1, x1, y1 * y1));
         const float inv = 1.0f / fmaf(rt, sqrtf(m2), at);
         const float tr = er * inv, ti = ei * inv;
-        accf = fmaf(tr, tr, fmaf(ti, ti, accf));
+        // a zero error adds nothing, also where sc = 0 (atol = 0 on a mode that is zero in
+        // both solutions: 0 * inf would be NaN)
+        if (er != 0.f || ei != 0.f) accf = fmaf(tr, tr, fmaf(ti, ti, accf));
       }
       acc[q] = f2d_bits(accf);
     }
@@ -218,7 +220,9 @@ __global__ void __launch_bounds__(kRedThreads) k_err_partials(const ErrArgs a) {
       const double2 a0 = u0[idx], a1 = u1[idx];
       const double m2 = fmax(fma(a0.x, a0.x, a0.y * a0.y), fma(a1.x, a1.x, a1.y * a1.y));
       const double sc = fma(rtol, sqrt_nr(m2), atol);
-      acc[q] = fma(fma(er, er, ei * ei), rcp_nr(sc * sc), acc[q]);
+      const double e2 = fma(er, er, ei * ei);
+      // a zero error adds nothing, also where sc = 0 (see the FP32 arm above)
+      if (e2 != 0.0) acc[q] = fma(e2, rcp_nr(sc * sc), acc[q]);
     }
   }
   }

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libdns.so")
 HEADER_PATH = os.path.join(os.path.dirname(_PKG), "include", "dns.h")
 
 DNS_OK = 0
+DNS_ERR_ARG = 1
 STATUS_NAMES = {0: "DNS_OK", 1: "DNS_ERR_ARG", 2: "DNS_ERR_CUDA", 3: "DNS_ERR_OOM",
                 4: "DNS_ERR_NONFINITE", 5: "DNS_ERR_STEP_UNDERFLOW", 6: "DNS_ERR_MAX_REJECTS",
                 7: "DNS_ERR_TIMEOUT", 8: "DNS_ERR_STATE", 9: "DNS_ERR_UNSUPPORTED"}
@@ -144,6 +145,21 @@ def declared_symbols():
 
 # ---- thin module-level wrappers with the C names ----------------------------------------
 
+def _spectral_dev(t, ncomp, shape, what):
+    """Address of a device spectral field: a contiguous complex128 CUDA tensor of
+    ncomp * nx * ny * (nz/2+1) elements.  Anything else raises ValueError before the library
+    is called, so that no kernel reads or writes past a caller's buffer."""
+    nx, ny, nz = shape
+    want = ncomp * nx * ny * (nz // 2 + 1)
+    if not hasattr(t, "data_ptr") or not getattr(t, "is_cuda", False):
+        raise ValueError(f"{what}: a CUDA tensor is required")
+    if str(t.dtype) != "torch.complex128":
+        raise ValueError(f"{what}: dtype complex128 required, got {t.dtype}")
+    if t.numel() != want:
+        raise ValueError(f"{what}: {t.numel()} elements, expected {want} = {ncomp} x {nx} x {ny} x {nz // 2 + 1}")
+    return _ptr(t)
+
+
 def _ptr(x):
     """Address of a torch tensor or numpy array (contiguous), or an int."""
     if x is None:
@@ -266,8 +282,9 @@ class Dns:
         return out
 
     def rhs(self, uhat_dev, f_dev):
-        self._check(self._lib.dns_rhs(self._h, C.c_void_p(_ptr(uhat_dev)), C.c_void_p(_ptr(f_dev))),
-                    "dns_rhs")
+        a = _spectral_dev(uhat_dev, self.ncomp, self.shape, "dns_rhs input")
+        b = _spectral_dev(f_dev, self.ncomp, self.shape, "dns_rhs output")
+        self._check(self._lib.dns_rhs(self._h, C.c_void_p(a), C.c_void_p(b)), "dns_rhs")
 
     def step(self, method, h, rtol=1e-6, atol=1e-6, t_end=float("inf")):
         info = dns_step_info()
@@ -390,8 +407,11 @@ def dns_rhs_noalloc(nx, ny, nz, nu, uhat_dev, f_dev, stream=None):
     """dns_rhs without a context or device allocation (grids up to 32^3); returns the status."""
     lib = load()
     h = getattr(stream, "cuda_stream", stream)
-    return lib.dns_rhs_noalloc(int(nx), int(ny), int(nz), float(nu), C.c_void_p(_ptr(uhat_dev)),
-                               C.c_void_p(_ptr(f_dev)), C.c_void_p(h) if h else None)
+    shape = (int(nx), int(ny), int(nz))
+    a = _spectral_dev(uhat_dev, 3, shape, "dns_rhs_noalloc input")
+    b = _spectral_dev(f_dev, 3, shape, "dns_rhs_noalloc output")
+    return lib.dns_rhs_noalloc(shape[0], shape[1], shape[2], float(nu), C.c_void_p(a),
+                               C.c_void_p(b), C.c_void_p(h) if h else None)
 
 
 def _st(stream):

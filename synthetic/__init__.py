@@ -4,7 +4,10 @@ This module is shared by the CPU oracle, the tests and the benchmark.  It holds
 only the definitions of the initial fields (closed-form Taylor-Green modes, a
 random-phase turbulence field, a Rayleigh-Taylor density profile) and a
 counter-based random number generator.  It does none of the method's arithmetic:
-no transforms, no right-hand side, no projection, no time stepping.
+no right-hand side, no projection, no dealiasing, no time stepping.  Its one transform
+is input construction: numpy's real FFT of the Rayleigh-Taylor density profile into the
+half-spectrum layout (``rayleigh_taylor_hat``), for callers that take the initial state in
+that layout (the oracle and the CUDA path each have their own transforms).
 
 Spectral arrays use the half-spectrum layout ``[3][nx][ny][nz//2+1]`` (complex128,
 component-major, kz contiguous) and the unnormalised forward DFT convention
@@ -26,6 +29,7 @@ __all__ = [
     "random_solenoidal_hat",
     "random_complex_hat",
     "rayleigh_taylor_fields",
+    "rayleigh_taylor_hat",
 ]
 
 _MASK64 = np.uint64(0xFFFFFFFFFFFFFFFF)
@@ -212,3 +216,14 @@ def rayleigh_taylor_fields(nx: int, ny: int, nz: int, seed: int = 7, atwood: flo
     zt = zeta[:, :, None]
     rho = atwood * (np.tanh((Z - z1 - zt) / width) - np.tanh((Z - z2 - zt) / width)) - atwood
     return rho, lengths
+
+
+def rayleigh_taylor_hat(nx: int, ny: int, nz: int, seed: int = 7, **kw):
+    """The Rayleigh-Taylor initial state in the half-spectrum layout: [4][nx][ny][nz//2+1]
+    complex128 with velocity zero and component 3 the unnormalised real DFT of the density
+    deviation of ``rayleigh_taylor_fields`` (numpy.fft.rfftn; input construction only).
+    Returns (state, lengths)."""
+    rho, lengths = rayleigh_taylor_fields(nx, ny, nz, seed=seed, **kw)
+    out = np.zeros((4, nx, ny, nz // 2 + 1), dtype=np.complex128)
+    out[3] = np.fft.rfftn(rho)
+    return out, lengths

@@ -43,10 +43,13 @@ def err_tolerance(h, ks, e, tab, u_old, u_new, atol, rtol, eps_rhs=1e-13):
                            for b, bh, k in zip(tab.b, tab.bhat, ks))
     sc = atol + rtol * np.maximum(np.abs(u_old), np.abs(u_new))
     ae = np.abs(e)
+    # modes with e = 0 contribute nothing to the norm (also where sc = 0, atol = 0)
+    live = ae > 0
+    isc2 = np.where(live, 1.0 / np.where(live, sc, 1.0) ** 2, 0.0)
     rel = 0.0
     for c in range(e.shape[0]):
-        num = float(np.sum(ae[c] * de / sc[c] ** 2))
-        den = float(np.sum(ae[c] ** 2 / sc[c] ** 2))
+        num = float(np.sum(ae[c] * de * isc2[c]))
+        den = float(np.sum(ae[c] ** 2 * isc2[c]))
         if den > 0:
             rel = max(rel, num / den)
     return rel + 1e-15

@@ -48,8 +48,9 @@ def test_at_error_interpolates_log_log():
 
 
 def test_reference_arm_prints_one_contract_line():
-    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    # a small grid keeps the test short; the arm is the same code at 256^3
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "4",
+                        "--warmup", "0", "--grid", "32"], capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
@@ -59,4 +60,8 @@ def test_reference_arm_prints_one_contract_line():
                 "cpu_baseline", "e2e"):
         assert key in d
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    # the oracle runs on every host core the memory allows (here 4 jobs: up to 4 workers)
+    assert d["cpu_baseline"]["cores"] == min(4, bench.cpu_workers(4, 32))
+    assert d["cpu_baseline"]["nproc"] >= d["cpu_baseline"]["cores"]
+    assert d["config"]["grid"] == [32, 32, 32]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["unit"] == d["unit"]

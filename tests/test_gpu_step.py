@@ -53,6 +53,27 @@ def test_single_bs5_attempt_matches_oracle():
         assert info.t == h
 
 
+def test_pure_relative_tolerance_is_refused_for_adaptive_methods():
+    # atol = 0 with an adaptive method: modes that the divergence-free constraint makes zero
+    # up to rounding (u_x at kappa = (kx, 0, 0)) would carry an error and a scale that are
+    # both rounding noise; the library refuses the call rather than run an arbitrary norm
+    from paper_1810_10197_gb300.dns import DNS_ERR_ARG, DnsError
+    shape, nu = (16, 16, 16), 0.01
+    g = sp.Grid(*shape)
+    uh = g.dealias(syn.random_solenoidal_hat(*shape, seed=21, k0=3.0))
+    for method in ("BS5_ADAPTIVE", "DP5_ADAPTIVE"):
+        d = make(shape, uh, nu)
+        with pytest.raises(DnsError) as ex:
+            d.step(method, 0.01, 1e-6, 0.0)
+        assert ex.value.status == DNS_ERR_ARG and "atol" in str(ex.value)
+        d.close()
+    # the oracle's own norm on such a field: the modes where u_old = u_new = e = 0 exactly add
+    # nothing (no NaN); a mode with rounding noise in e over a zero scale makes it infinite
+    u_new, e, _ = rk.rk_attempt(oracle_f(g, nu), uh, 0.01, rk.BS5)
+    err = rk.error_norm(uh, u_new, e, 0.0, 1e-6, g.nmodes_half)
+    assert not math.isnan(err)
+
+
 def test_rejected_attempt_keeps_state_and_shrinks_step():
     shape, nu = (16, 16, 16), 0.01
     g = sp.Grid(*shape)

@@ -276,6 +276,35 @@ def test_error_norm_closed_form_tg2d(nu, h, tol):
     assert np.max(np.abs(u_new - Rb * u0)) < 1e-13 * a
 
 
+@pytest.mark.parametrize("z,rtol", [(-0.5, 1e-4), (-0.36, 1e-6)])
+def test_error_norm_pure_relative_tolerance(z, rtol):
+    # atol = 0, a purely relative tolerance (Section 2.2.1 with the absolute part zero).  The
+    # arrays are those of one BS5 step of the linear problem f = lambda u on a field whose
+    # first two components hold 4 modes of modulus a and which is zero everywhere else (a
+    # 2D Taylor-Green layout): u_new = R_b(z) u, e = (R_b(z) - R_bhat(z)) u exactly, z = h
+    # lambda.  Every zero mode has sc = 0 and e = 0 and contributes nothing, so
+    # err = |dR| / max(1, |R_b|) * sqrt(4 / nmodes) / rtol, independent of a.
+    n = 16
+    nmodes = n * n * (n // 2 + 1)
+    Rb = float(stability_poly(rk.BS5, rk.BS5.b, z))
+    dR = float(stability_poly(rk.BS5, rk.BS5.b, z) - stability_poly(rk.BS5, rk.BS5.bhat, z))
+    expect = abs(dR) / (rtol * max(1.0, abs(Rb))) * math.sqrt(4.0 / nmodes)
+    errs = []
+    for a in (1.0, 1e6):
+        u = np.zeros((3, n, n, n // 2 + 1), complex)
+        for kx, ky in ((1, 1), (1, -1), (-1, 1), (-1, -1)):
+            u[0, kx, ky, 0] = -1j * a * np.sign(ky)
+            u[1, kx, ky, 0] = 1j * a * np.sign(kx)
+        err = rk.error_norm(u, Rb * u, dR * u, 0.0, rtol, nmodes)
+        assert math.isfinite(err) and abs(err - expect) < 1e-12 * expect
+        errs.append(err)
+    assert abs(errs[1] - errs[0]) < 1e-12 * errs[0]
+    # a nonzero error over a zero scale stays infinite (no tolerance can be met there)
+    e2 = dR * u
+    e2[2, 0, 0, 0] = 1e-3
+    assert rk.error_norm(u, Rb * u, e2, 0.0, rtol, nmodes) == math.inf
+
+
 def test_integrate_with_band_rescale_keeps_energy_and_refreshes_k1():
     # the Section 3.3.1 forcing after every accepted step: the energy stays at its initial value
     # and a first-same-as-last pair evaluates k_1 again for the rescaled state

@@ -21,7 +21,31 @@ def brute_dft_half(f, lengths=None):
     return np.einsum("ai,bj,ck,...ijk->...abc", ex, ey, ez, f)
 
 
-@pytest.mark.parametrize("shape", [(4, 4, 4), (6, 4, 8), (8, 6, 12), (12, 8, 6)])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 16, 17, 18, 24, 32, 36, 48, 96, 128, 192, 256, 384,
+                               512, 768])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_own_fft_is_the_dft_sum(n, sign):
+    # the oracle's Cooley-Tukey transform against the definition X[k] = sum_j x[j] w^(jk),
+    # w = exp(sign 2 pi i / n), summed term by term; lengths above 16 exercise the recursion
+    # (18 = 6 x 3, 768 = 16 x 16 x 3), and the transform runs along a middle axis, the last
+    # axis and the first axis (the three data layouts of its code)
+    from oracle import fft as offt
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal((2, n, 3)) + 1j * rng.standard_normal((2, n, 3))
+    jk = (np.arange(n)[:, None] * np.arange(n)[None, :]) % n
+    w = np.exp(sign * 2j * np.pi * jk / n)
+    ref = np.zeros_like(x)
+    for k in range(n):
+        ref[:, k, :] = np.sum(x * w[:, k][None, :, None], axis=1)
+    tol = 1e-14 * max(1.0, np.log2(n)) * np.max(np.abs(ref))
+    assert np.max(np.abs(offt.fft(x, axis=1, sign=sign) - ref)) <= tol
+    xl = np.ascontiguousarray(np.moveaxis(x, 1, -1))
+    assert np.max(np.abs(offt.fft(xl, axis=-1, sign=sign) - np.moveaxis(ref, 1, -1))) <= tol
+    xf = np.ascontiguousarray(np.moveaxis(x, 1, 0))
+    assert np.max(np.abs(offt.fft(xf, axis=0, sign=sign) - np.moveaxis(ref, 1, 0))) <= tol
+
+
+@pytest.mark.parametrize("shape", [(4, 4, 4), (6, 4, 8), (8, 6, 12), (12, 8, 6), (18, 24, 20)])
 def test_forward_transform_is_unnormalised_dft(shape):
     rng = np.random.default_rng(1)
     f = rng.standard_normal((3,) + shape)
@@ -31,7 +55,7 @@ def test_forward_transform_is_unnormalised_dft(shape):
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("shape", [(4, 4, 4), (6, 4, 8), (8, 6, 12)])
+@pytest.mark.parametrize("shape", [(4, 4, 4), (6, 4, 8), (8, 6, 12), (18, 24, 20)])
 def test_inverse_transform_carries_one_over_n3(shape):
     rng = np.random.default_rng(2)
     f = rng.standard_normal(shape)
