@@ -406,6 +406,17 @@ def run_ensemble(args):
         dist.destroy_process_group()
         return 0
     sim = len(all_specs) * t_end
+    # algorithmic HBM traffic of the batched run: each instance's right-hand sides (five
+    # passes) and attempts (stage sums, error norm) at its own grid
+    esz = 8 if prec in ("fp32_mixed", "fp32") else 16
+    ksz = 8 if prec == "fp32" else 16
+    ysz = (6 * 8 + 16) / 7 if prec == "fp32" else 16
+    moved = 0.0
+    for (n, k0, nu, i), inf in zip(specs, infos):
+        moved += inf.n_rhs * sum(pass_bytes(n, esz=esz, ksz=ksz, ysz=ysz).values())
+        moved += (inf.n_acc + inf.n_rej) * sum(step_kernel_bytes(n, ksz=ksz).values())
+    peaks, peak_src = load_peaks()
+    hbm_frac = moved / batched_s / 1e9 / peaks["hbm_gbs"] if ws == 1 else None
     out = {"metric": METRIC, "value": n_rhs / batched_s, "unit": UNIT, "n_gpus": ws, "steps": 1,
            "warmup": 1, "ms_per_step": batched_s * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": DTYPES[prec],
@@ -416,6 +427,10 @@ def run_ensemble(args):
            "sequential": {"rhs_evals_per_s": seq_rhs / seq_s, "sim_time_per_gpu_s": sim / seq_s,
                           "seconds": seq_s},
            "batched_seconds": batched_s, "speedup_vs_sequential": seq_s / batched_s,
+           "algorithmic_bytes": moved if ws == 1 else None,
+           "hbm_frac_of_measured": hbm_frac,
+           "hbm_frac_basis": "algorithmic bytes of every instance's passes and step kernels over "
+                             f"the batched wall time, against {peak_src} hbm_gbs",
            "rhs_evals": int(n_rhs), "rejected": int(n_rej)}
     print(json.dumps(out), flush=True)
     b.close()
@@ -658,11 +673,130 @@ def run_controllers(args):
     return 0
 
 
+PASS_NAMES = ("p1_x_inverse_curl", "p2_y_inverse", "p3_z_c2r_cross_r2c", "p4_y_forward",
+              "p5_x_forward_project")
+
+
+def fp64_instructions(n, kernel):
+    """FP64 thread instructions per launch of a pass at n^3 (ncu, kept in profiles/)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "fp64_instr.json")) as fh:
+            return json.load(fh).get(f"fp64_{n}", {}).get(kernel)
+    except Exception:
+        return None
+
+
+def analyse(precision, mode, n, prof, n_rhs, attempts, ms, peaks, peak_src, fp64_rate):
+    """Roofline of the dominant pass and HBM fractions from per-kernel CUDA-event times.
+
+    prof: {kernel: (launches, total ms)} over the timed region; n_rhs right-hand sides and
+    `attempts` step attempts in it (step mode), ms its length.  In step mode every attempt
+    also launches the passes for k_1, which return at once when first-same-as-last carries
+    k_1 over: a pass does work n_rhs times, not once per launch."""
+    fp32 = precision in ("fp32_mixed", "fp32")
+    lean = precision == "fp32"
+    dwp = precision == "fp32x2"
+    flops = pass_flops(n)
+    ksz = 8 if (lean and mode == "step") else 16
+    ysz = (6 * 8 + 16) / 7 if (lean and mode == "step") else 16
+    byts = pass_bytes(n, esz=8 if fp32 else 16, ksz=ksz, ysz=ysz)
+    dom = max(PASS_NAMES, key=lambda k: prof.get(k, (0, 0.0))[1])
+    nl, tot_ms = prof[dom]
+    n_work = n_rhs if mode == "step" else nl
+    avg_s = tot_ms * 1e-3 / n_work
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            traffic = json.load(fh).get(f"{precision}_{n}", {}).get(dom)
+    except Exception:
+        pass
+    hbm_gbs = byts[dom] / avg_s / 1e9
+    if fp32:
+        roof = {"bound": "hbm", "kernel": dom, "achieved": hbm_gbs, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": hbm_gbs / peaks["hbm_gbs"], "traffic": traffic,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                "flops_achieved_tflops": flops[dom] / avg_s / 1e12}
+    elif dwp:
+        achieved = flops[dom] / avg_s / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": DW_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / DW_PEAK_TFLOPS, "traffic": traffic,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz = 40.3e12 FP32 "
+                               "instructions/s over 7.6 FP32 instructions per nominal FFT flop in "
+                               "double-word arithmetic",
+                "hbm_achieved_gbs": hbm_gbs, "hbm_frac_of_measured": hbm_gbs / peaks["hbm_gbs"],
+                "hbm_peak_source": peak_src}
+    else:
+        # bound by the FP64 pipe: FP64 instructions per launch (ncu count) over the time,
+        # against the pipe's issue rate measured in this run; nominal flops beside it
+        nominal = flops[dom] / avg_s / 1e12
+        instr = fp64_instructions(n, dom)
+        roof = {"bound": "alu", "kernel": dom, "traffic": traffic,
+                "hbm_achieved_gbs": hbm_gbs, "hbm_frac_of_measured": hbm_gbs / peaks["hbm_gbs"],
+                "hbm_peak_source": peak_src,
+                "nominal_flops_tflops": nominal, "nominal_frac_of_1p25_tflops": nominal / 1.25}
+        if instr and fp64_rate:
+            achieved = instr / avg_s / 1e12
+            roof.update({"achieved": achieved, "peak": fp64_rate / 1e12, "unit": "T FP64 instr/s",
+                         "frac": achieved / (fp64_rate / 1e12),
+                         "fp64_instructions_per_launch": instr,
+                         "peak_source": "FP64 pipe issue rate measured in this run "
+                                        "(dns_measure_fp64_rate: independent DFMA chains on every SM); "
+                                        "instructions per launch from ncu (profiles/fp64_instr.json)"})
+        else:
+            roof.update({"achieved": nominal, "peak": 1.25, "unit": "TFLOP/s", "frac": nominal / 1.25,
+                         "peak_source": "nominal FP64 rate (1.25 TFLOP/s): no measured issue rate "
+                                        "or instruction count for this grid"})
+    per_kernel = {k: {"launches": v[0], "total_ms": round(v[1], 3), "share": round(v[1] / ms, 4),
+                      "avg_ms": round(v[1] / max(v[0], 1), 4)}
+                  for k, v in prof.items()}
+    rhs_bytes = sum(byts.values())
+    moved = {k: byts[k] * n_rhs for k in byts}
+    for k, b in step_kernel_bytes(n, ksz=ksz).items():
+        moved[k] = b * attempts
+    for k, b in moved.items():
+        if k in prof and prof[k][1] > 0 and b > 0:
+            gbs = b / (prof[k][1] * 1e-3) / 1e9
+            per_kernel[k]["hbm_gbs"] = round(gbs, 1)
+            per_kernel[k]["hbm_frac_of_measured"] = round(gbs / peaks["hbm_gbs"], 4)
+    # per right-hand-side evaluation: the five passes' algorithmic bytes over their time
+    pass_ms = sum(prof.get(k, (0, 0.0))[1] for k in PASS_NAMES)
+    rhs_frac = rhs_bytes * n_rhs / (pass_ms * 1e-3) / 1e9 / peaks["hbm_gbs"] if pass_ms > 0 else None
+    step_frac = sum(moved.values()) / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]
+    return {"roofline": roof, "kernels": per_kernel, "rhs_bytes": rhs_bytes,
+            "rhs_hbm_frac_of_measured": rhs_frac, "step_hbm_frac_of_measured": step_frac,
+            "rhs_pass_ms": pass_ms / max(n_rhs, 1)}
+
+
+def timed_attempts(d, stream, steps, warmup, barrier, clocks=None):
+    """W untimed then K timed BS5 attempts from the context's state (CUDA events on its
+    stream, per-kernel profile).  Returns (ms, profile, info before, info after, clocks)."""
+    import torch
+    d.enqueue_attempts(warmup, "BS5_ADAPTIVE", TOL, TOL, t_end=T_END, h0=H0)
+    i0 = d.info()
+    d.profile_enable(True)
+    if clocks:
+        clocks.start()
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    d.enqueue_attempts(steps, "BS5_ADAPTIVE", TOL, TOL, t_end=T_END, h0=0.0)
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop() if clocks else None
+    i1 = d.info()
+    prof = d.profile()
+    d.profile_enable(False)
+    return ms, prof, i0, i1, clk
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
 
     from paper_1810_10197_gb300 import Dns, build
+    from paper_1810_10197_gb300.dns import dns_measure_fp64_rate
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -682,46 +816,55 @@ def run_gpu(args):
         _, _, eps0 = d0.diagnostics()
         d0.close()
         forcing = (FLOWS["hit"]["forcing"][0], eps0)
-    d = Dns(n, nu=nu, precision=args.precision, forcing=forcing, stream=stream)
-    tiles = d.autotune()
-    d.set_state(u0_dev, 0.0)
+    fp64_rate = None
+    if args.precision == "fp64" or args.forms:
+        fp64_rate = dns_measure_fp64_rate(stream)[0]
 
     def barrier():
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
+    def make(precision):
+        dd = Dns(n, nu=nu, precision=precision, forcing=forcing, stream=stream)
+        if args.tiles and precision == args.precision:
+            dd.set_tiles(*args.tiles)
+            tl = list(args.tiles)
+        else:
+            tl = dd.autotune()
+        dd.set_state(u0_dev, 0.0)
+        return dd, tl
+
+    d, tiles = make(args.precision)
     f_dev = torch.empty_like(u0_dev)
+    clocks = ClockSampler(local)
     if args.mode == "rhs":
         for _ in range(args.warmup):
             d.rhs(u0_dev, f_dev)
-    else:
-        # warm-up attempts (untimed)
-        d.enqueue_attempts(args.warmup, "BS5_ADAPTIVE", TOL, TOL, t_end=T_END, h0=H0)
-    i0 = d.info()
-    d.profile_enable(True)
-    clocks = ClockSampler(local)
-    clocks.start()
-    barrier()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    if args.mode == "rhs":
+        i0 = d.info()
+        d.profile_enable(True)
+        clocks.start()
+        barrier()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
         for _ in range(args.steps):
             d.rhs(u0_dev, f_dev)
+        ev1.record(stream)
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        clk = clocks.stop()
+        i1 = d.info()
+        prof = d.profile()
+        d.profile_enable(False)
     else:
-        d.enqueue_attempts(args.steps, "BS5_ADAPTIVE", TOL, TOL, t_end=T_END, h0=0.0)
-    ev1.record(stream)
-    barrier()
-    ms = ev0.elapsed_time(ev1)
-    clk = clocks.stop()
-    i1 = d.info()
-    prof = d.profile()
-    d.profile_enable(False)
+        ms, prof, i0, i1, clk = timed_attempts(d, stream, args.steps, args.warmup, barrier, clocks)
     n_rhs = (i1.n_rhs - i0.n_rhs) if args.mode == "step" else args.steps
     sim = (i1.t - i0.t) if args.mode == "step" else 0.0
+    attempts = (i1.n_acc - i0.n_acc) + (i1.n_rej - i0.n_rej) if args.mode == "step" else 0
     ms_max, n_rhs_tot, sim_tot = aggregate(dist, ws, ms, n_rhs, sim, "cuda")
     value = n_rhs_tot / (ms_max * 1e-3)
+    final_state = d.get_state() if (args.forms and args.mode == "step" and ws == 1) else None
 
     # ---- end to end through the public API with host buffers (pinned) -------------------
     e2e = None
@@ -770,73 +913,56 @@ def run_gpu(args):
             note += " (the upload copies only the retained modes)"
         e2e = {"value": e2e_rhs / e2e_s * ws, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": state_bytes, "steps": e2e_steps, "note": note}
+    d.close()
 
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
         return 0
 
-    # ---- roofline of the dominant kernel -------------------------------------------------
     peaks, peak_src = load_peaks()
-    fp32 = args.precision in ("fp32_mixed", "fp32")
-    lean = args.precision == "fp32"
-    dwp = args.precision == "fp32x2"
-    flops = pass_flops(n)
-    ksz = 8 if (lean and args.mode == "step") else 16
-    ysz = (6 * 8 + 16) / 7 if (lean and args.mode == "step") else 16
-    byts = pass_bytes(n, esz=8 if fp32 else 16, ksz=ksz, ysz=ysz)
-    names = list(flops)
-    dom = max(names, key=lambda k: prof.get(k, (0, 0.0))[1])
-    nl, tot_ms = prof[dom]
-    # in step mode every attempt also launches the passes for k_1, which return at once when
-    # first-same-as-last carries k_1 over: a pass does work n_rhs times, not nl times
-    n_work = n_rhs if args.mode == "step" else nl
-    avg_s = tot_ms * 1e-3 / n_work
-    traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
-            traffic = json.load(fh).get(f"{args.precision}_{n}", {}).get(dom)
-    except Exception:
-        pass
-    hbm_gbs = byts[dom] / avg_s / 1e9
-    if fp32:
-        roof = {"bound": "hbm", "kernel": dom, "achieved": hbm_gbs, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": hbm_gbs / peaks["hbm_gbs"], "traffic": traffic,
-                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
-                "flops_achieved_tflops": flops[dom] / avg_s / 1e12}
-    elif dwp:
-        achieved = flops[dom] / avg_s / 1e12
-        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": DW_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / DW_PEAK_TFLOPS, "traffic": traffic,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz = 40.3e12 FP32 "
-                               "instructions/s over 7.6 FP32 instructions per nominal FFT flop in "
-                               "double-word arithmetic",
-                "hbm_achieved_gbs": hbm_gbs, "hbm_frac_of_measured": hbm_gbs / peaks["hbm_gbs"],
-                "hbm_peak_source": peak_src}
-    else:
-        fp64_peak_tflops = 1.25   # nominal FP64 rate of this part (FMA = 2 flops)
-        achieved = flops[dom] / avg_s / 1e12
-        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp64_peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / fp64_peak_tflops, "traffic": traffic,
-                "peak_source": "nominal FP64 rate (1.25 TFLOP/s); the FP64 pipe bounds these passes",
-                "hbm_achieved_gbs": hbm_gbs, "hbm_frac_of_measured": hbm_gbs / peaks["hbm_gbs"],
-                "hbm_peak_source": peak_src}
+    a = analyse(args.precision, args.mode, n, prof, n_rhs, attempts, ms, peaks, peak_src, fp64_rate)
+
+    # ---- the other arithmetic forms on the same field, same step count, same process ------
+    forms = None
+    if final_state is not None:
+        def reference(t):
+            # time-converged FP64 state at t: BS5 adaptive, tolerance 1e-10 (Section 3's
+            # accuracy reference: the same flow integrated far more accurately)
+            r = Dns(n, nu=nu, precision="fp64", forcing=forcing, stream=stream)
+            r.set_state(u0_dev, 0.0)
+            r.integrate(t, "BS5_ADAPTIVE", 1e-10, 1e-10, h0=H0)
+            u = r.get_state()
+            r.close()
+            return u
+
+        def l2(u, t):
+            ref = reference(t)
+            return float(np.linalg.norm(u - ref) / np.linalg.norm(ref))
+
+        forms = {"reference": "FP64 BS5 adaptive, tolerance 1e-10, to each run's final time",
+                 args.precision: {"value": value, "sim_time_per_gpu_s": sim_tot / (ms_max * 1e-3),
+                                  "t_end_state": i1.t, "l2_error_vs_reference": l2(final_state, i1.t),
+                                  "rhs_hbm_frac_of_measured": a["rhs_hbm_frac_of_measured"]}}
+        for prec in args.forms:
+            if prec == args.precision:
+                continue
+            dd, tl = make(prec)
+            fms, fprof, f0, f1, _ = timed_attempts(dd, stream, args.steps, args.warmup, barrier)
+            fu = dd.get_state()
+            dd.close()
+            fr = f1.n_rhs - f0.n_rhs
+            fa = analyse(prec, "step", n, fprof, fr, (f1.n_acc - f0.n_acc) + (f1.n_rej - f0.n_rej),
+                         fms, peaks, peak_src, fp64_rate)
+            forms[prec] = {"value": fr / (fms * 1e-3), "unit": UNIT, "dtype": DTYPES[prec], "tiles": tl,
+                           "sim_time_per_gpu_s": (f1.t - f0.t) / (fms * 1e-3),
+                           "rhs_evals": fr, "accepted": f1.n_acc - f0.n_acc, "rejected": f1.n_rej - f0.n_rej,
+                           "t_end_state": f1.t, "l2_error_vs_reference": l2(fu, f1.t),
+                           "rhs_hbm_frac_of_measured": fa["rhs_hbm_frac_of_measured"],
+                           "step_hbm_frac_of_measured": fa["step_hbm_frac_of_measured"],
+                           "rhs_pass_ms": fa["rhs_pass_ms"], "roofline": fa["roofline"]}
+
     launches = sum(v[0] for v in prof.values())
-    per_kernel = {k: {"launches": v[0], "total_ms": round(v[1], 3), "share": round(v[1] / ms, 4),
-                      "avg_ms": round(v[1] / max(v[0], 1), 4)}
-                  for k, v in prof.items()}
-    rhs_bytes = sum(byts.values())
-    # algorithmic bytes moved in the timed region, per kernel and for the whole step
-    attempts = (i1.n_acc - i0.n_acc) + (i1.n_rej - i0.n_rej) if args.mode == "step" else 0
-    moved = {k: byts[k] * n_rhs for k in byts}
-    for k, b in step_kernel_bytes(n, ksz=ksz).items():
-        moved[k] = b * attempts
-    for k, b in moved.items():
-        if k in prof and prof[k][1] > 0 and b > 0:
-            gbs = b / (prof[k][1] * 1e-3) / 1e9
-            per_kernel[k]["hbm_gbs"] = round(gbs, 1)
-            per_kernel[k]["hbm_frac_of_measured"] = round(gbs / peaks["hbm_gbs"], 4)
-    step_hbm_frac = sum(moved.values()) / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]
     cpu = None
     if ws == 1 and not args.no_cpu:
         k = cpu_workers(host_info()["nproc"], N_GRID)
@@ -849,24 +975,28 @@ def run_gpu(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32+f64" if fp32 else ("f32x2+f64" if dwp else "f64"),
+           "dtype": DTYPES[args.precision],
            "data": "synthetic",
            "config": {"workload": workload_name(args), "grid": [n, n, n], "nu": nu,
                       "method": "BS5_ADAPTIVE" if args.mode == "step" else "rhs",
                       "rtol": TOL, "atol": TOL, "h0": H0, "precision": args.precision,
                       "forcing": forcing, "tiles": tiles,
                       "l2": "inputs larger than L2 (per right-hand side: "
-                            f"{rhs_bytes / 1e9:.2f} GB algorithmic traffic)",
+                            f"{a['rhs_bytes'] / 1e9:.2f} GB algorithmic traffic)",
                       "parallelism": f"replicas{ws}"},
            "sim_time_per_gpu_s": sim_tot / (ms_max * 1e-3),
            "sim_time_advanced": sim, "rhs_evals": n_rhs, "t_end_state": i1.t,
            "accepted": i1.n_acc - i0.n_acc, "rejected": i1.n_rej - i0.n_rej,
-           "rhs_hbm_frac_of_measured": rhs_bytes * value / ws / 1e9 / peaks["hbm_gbs"],
-           "step_hbm_frac_of_measured": step_hbm_frac,
+           "rhs_hbm_frac_of_measured": a["rhs_hbm_frac_of_measured"],
+           "rhs_hbm_frac_basis": "the five passes' algorithmic bytes per right-hand side over their "
+                                 "CUDA-event time per right-hand side that does work",
+           "rhs_rate_hbm_frac_of_measured": a["rhs_bytes"] * value / ws / 1e9 / peaks["hbm_gbs"],
+           "step_hbm_frac_of_measured": a["step_hbm_frac_of_measured"],
            "e2e": e2e,
            "gpu_launches": launches,
-           "kernels": per_kernel,
-           "roofline": roof,
+           "kernels": a["kernels"],
+           "roofline": a["roofline"],
+           "forms": forms,
            "clocks": clk,
            "cpu_baseline": cpu}
     print(json.dumps(out), flush=True)
@@ -884,6 +1014,12 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--grid", type=int, default=N_GRID)
+    ap.add_argument("--forms", nargs="*", default=["fp32_mixed", "fp32", "fp32x2"],
+                    choices=["fp64", "fp32_mixed", "fp32x2", "fp32"],
+                    help="other arithmetic forms timed on the same field after the headline run "
+                         "(step mode, one GPU); none with an empty list")
+    ap.add_argument("--tiles", type=int, nargs=2, default=None,
+                    help="y-pass variant and z-pass code instead of the autotuner's choice")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_mixed", "fp32x2", "fp32"])
     ap.add_argument("--flow", default="tg", choices=["tg", "hit"])
     ap.add_argument("--mode", default="step", choices=["step", "rhs"])

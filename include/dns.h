@@ -256,8 +256,9 @@ DNS_API dns_status dns_mlp_train(float* params, const float* x, const float* t, 
  * with dns_get_state); the contexts belong to the batch: do not destroy them yourself.
  * dns_integrate_batch integrates every instance i from its current time to t_end[i] with its
  * own tolerances and first step h0[i] (<= 0 keeps the current proposal), by ONE launch of a
- * CUDA graph: a conditional loop whose body runs one attempt of every instance (instances in
- * parallel branches) and continues while any instance is unfinished (at most 10^7 rounds).
+ * CUDA graph: one conditional loop per instance, side by side, each running that instance's
+ * attempts until it is done or fails (at most 10^7 attempts each).  The loops do not wait
+ * for one another.
  * The graph is built on the first call for a method and reused.  Synchronous; info[i]
  * receives each instance's outcome; returns the first non-OK instance status (or DNS_OK). */
 typedef struct dns_batch dns_batch;
@@ -277,8 +278,14 @@ DNS_API dns_status dns_integrate_batch(dns_batch* batch, int method, const doubl
  * events on its stream, keeps the fastest, and caches the choice per (grid, precision, form)
  * for the process and, if the environment variable DNS_TUNE_CACHE names a file, in that file
  * (read on first use, appended to).  variants (may be NULL) receives {y pass, z pass code}.
+ * z pass codes 4 and 5 are the register-resident FP32 kernel (two real fields per complex
+ * line transform held in registers, u x omega between the transforms without a
+ * shared-memory round trip, persistent CTAs fed by bulk copies that overlap the previous
+ * tile's transforms) with paired (FADD2/FFMA2) or scalar FP32 arithmetic; it applies to the single-precision forms of the
+ * velocity equations with nz = 64, 128 or 256, and where it does not apply codes 4 and 5
+ * run codes 0 and 1.
  * dns_create_batch tunes every instance.  dns_set_tiles sets them by hand (var_py 0..1,
- * var_p3 0..3; the default is 0, 0).  Synchronous.
+ * var_p3 0..5; the default is 0 and 4).  Synchronous.
  * A bulk copy's completion is awaited with a bound (about half a second); a wait that runs
  * out marks the step controller DNS_ERR_TIMEOUT instead of hanging. */
 DNS_API dns_status dns_autotune(dns_ctx* ctx, int reps, int* variants);
@@ -342,6 +349,15 @@ DNS_API dns_status dns_debug_poison(dns_ctx* ctx, int on);
  * (NULL: the legacy default stream).  DNS_ERR_ARG for n < 0 or a NULL pointer with n > 0;
  * DNS_ERR_CUDA if the launch fails. */
 DNS_API dns_status dns_debug_f32_from_f64(const double* x_dev, float* y_dev, long long n, void* stream);
+
+/* The FP64 pipe's issue rate on the current device, measured: chains of independent DFMA
+ * (and, separately, DADD) instructions on every SM, timed with CUDA events on `stream` (NULL:
+ * the legacy default stream).  Writes thread instructions per second.  The FP64 form of the
+ * passes is bound by this pipe (Section 2.1's transforms in FP64 do about 2 flops per byte of
+ * traffic on this part), and its roofline is stated against this rate.  Allocates and frees
+ * 8 bytes of device memory; synchronous (about 0.2 s).  DNS_ERR_ARG for NULL outputs,
+ * DNS_ERR_CUDA if a launch fails. */
+DNS_API dns_status dns_measure_fp64_rate(void* stream, double* dfma_per_s, double* dadd_per_s);
 
 /* Grid facts: retained cut-offs K[3] and the number of device bytes the context holds. */
 DNS_API dns_status dns_query(const dns_ctx* ctx, int* K3, size_t* device_bytes);

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdns.so")
 SOURCES = ["api.cu", "stepper.cu", "passes_f64.cu", "passes_f32.cu", "passes_dw.cu", "passes_dw_p1.cu", "passes_dw_p2.cu", "passes_dw_p3.cu", "passes_dw_p4.cu",
-           "passes_dw_p5.cu", "noalloc.cu", "mlp.cu"]
+           "passes_dw_p5.cu", "noalloc.cu", "mlp.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-Xcompiler", "-fvisibility=hidden"]

@@ -120,6 +120,7 @@ struct dns_ctx {
   float* mlp_buf = nullptr;        // learned-controller parameters (dns_set_controller)
   int var_py = 0, var_p3 = 0;      // tile variants (dns_autotune)
   int p3_bulk = 1;                 // z pass input by bulk copies where possible (dns_autotune)
+  int p3_rr = 1;                   // z pass: register-resident FP32 kernel where it applies
   bool stall_pending = false;      // dns_debug_stall: the next host-enqueued z pass stalls
   bool capturing = false;          // building dns_integrate's graph
   size_t bytesA = 0, bytesB = 0;   // sizes of the scratch buffers A and B
@@ -251,6 +252,7 @@ dns_status enqueue_rhs(dns_ctx* c, DnsCtrl* ctrl, int yslot, int kslot, int gate
   a.var_py = c->var_py;
   a.var_p3 = c->var_p3;
   a.p3_bulk = c->p3_bulk;
+  a.p3_rr = c->p3_rr;
   if (c->stall_pending && !c->capturing) {
     a.p3_stall = 16;
     c->stall_pending = false;
@@ -1109,10 +1111,13 @@ dns_status dns_autotune(dns_ctx* c, int reps, int* variants) {
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
       const int z = it->second.second;
-      if (c->var_py != it->second.first || c->var_p3 != (z & 1) || c->p3_bulk != !(z & 2)) drop_graphs(c);
+      if (c->var_py != it->second.first || c->var_p3 != (z & 1) || c->p3_bulk != !(z & 2) ||
+          c->p3_rr != ((z & 4) != 0))
+        drop_graphs(c);
       c->var_py = it->second.first;
       c->var_p3 = z & 1;
       c->p3_bulk = !(z & 2);
+      c->p3_rr = (z & 4) != 0;
       if (variants) { variants[0] = c->var_py; variants[1] = z; }
       return DNS_OK;
     }
@@ -1129,13 +1134,17 @@ dns_status dns_autotune(dns_ctx* c, int reps, int* variants) {
   CK(cudaEventCreate(&e0), "event");
   CK(cudaEventCreate(&e1), "event");
   // y pass: tile variants 0, 1; z pass: codes 0..3 (bit 0 tile variant, bit 1 per-element
-  // copies instead of bulk copies)
-  float best[2][4] = {{0, 0, 1e30f, 1e30f}, {0, 0, 0, 0}};
+  // copies instead of bulk copies) and, where it applies, 4 and 5 (the register-resident
+  // FP32 kernel with its two tile variants)
+  a.p3_rr = 1;
+  const bool rr_ok = (c->precision == DNS_FP32_MIXED || c->precision == DNS_FP32) && p3_rr_applies(a);
+  float best[2][6] = {{0, 0, 1e30f, 1e30f, 1e30f, 1e30f}, {0, 0, 0, 0, 1e30f, 1e30f}};
   for (int which = 0; which < 2; ++which) {        // 0: y pass (P2), 1: z pass (P3)
-    for (int v = 0; v < (which == 0 ? 2 : 4); ++v) {
+    for (int v = 0; v < (which == 0 ? 2 : (rr_ok ? 6 : 4)); ++v) {
       a.var_py = which == 0 ? v : 0;
       a.var_p3 = which == 1 ? (v & 1) : 0;
       a.p3_bulk = which == 1 ? !(v & 2) : 1;
+      a.p3_rr = which == 1 && (v & 4) != 0;
       if (which == 0) { a.in = c->bufA; a.out = c->bufB; a.tw = c->tw[1]; }
       else { a.in = c->bufB; a.out = c->bufA; a.tw = c->tw[2]; }
       const int pass_id = which == 0 ? 2 : 3;
@@ -1152,9 +1161,10 @@ dns_status dns_autotune(dns_ctx* c, int reps, int* variants) {
   drop_graphs(c);
   c->var_py = best[0][1] < best[0][0] ? 1 : 0;
   int z = 0;
-  for (int v = 1; v < 4; ++v) if (best[1][v] < best[1][z]) z = v;
+  for (int v = 1; v < 6; ++v) if (best[1][v] < best[1][z]) z = v;
   c->var_p3 = z & 1;
   c->p3_bulk = !(z & 2);
+  c->p3_rr = (z & 4) != 0;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[key] = {c->var_py, z};
@@ -1190,11 +1200,14 @@ dns_status dns_debug_f32_from_f64(const double* x, float* y, long long n, void* 
 }
 
 dns_status dns_set_tiles(dns_ctx* c, int var_py, int var_p3) {
-  if (!c || var_py < 0 || var_py > 1 || var_p3 < 0 || var_p3 > 3) return DNS_ERR_ARG;
-  if (c->var_py != var_py || c->var_p3 != (var_p3 & 1) || c->p3_bulk != !(var_p3 & 2)) drop_graphs(c);
+  if (!c || var_py < 0 || var_py > 1 || var_p3 < 0 || var_p3 > 5) return DNS_ERR_ARG;
+  if (c->var_py != var_py || c->var_p3 != (var_p3 & 1) || c->p3_bulk != !(var_p3 & 2) ||
+      c->p3_rr != ((var_p3 & 4) != 0))
+    drop_graphs(c);
   c->var_py = var_py;
   c->var_p3 = var_p3 & 1;
   c->p3_bulk = !(var_p3 & 2);
+  c->p3_rr = (var_p3 & 4) != 0;
   return DNS_OK;
 }
 
@@ -1209,33 +1222,18 @@ dns_status dns_query(const dns_ctx* c, int* K3, size_t* device_bytes) {
 
 
 // ------------------------------------------------------------------------------------------
-// Batched ensembles: independent contexts advanced together by one graph launch.  The graph
-// holds a conditional WHILE node; its body enqueues one attempt of every instance, each in
-// its own branch (so instances run concurrently), then a kernel that keeps the loop going
-// while any instance is unfinished, with a hard cap on the number of iterations.
+// Batched ensembles: independent contexts advanced by one graph launch.  The graph holds one
+// conditional WHILE node per instance, side by side with no dependencies between them; the
+// body of instance i is one attempt of that instance and a kernel that keeps its own loop
+// going while it is unfinished (hard cap on its iterations).  The instances loop
+// independently: one that has finished, or whose attempts are short, does not wait for the
+// others, and the GPU runs the attempts of all unfinished instances concurrently.
 // ------------------------------------------------------------------------------------------
-namespace {
-
-__global__ void k_batch_continue(cudaGraphConditionalHandle h, DnsCtrl* const* ctrls, int n,
-                                 unsigned long long* iter, unsigned long long max_iter) {
-  int any = 0;
-  for (int i = 0; i < n; ++i)
-    if (!ctrls[i]->done && ctrls[i]->status == 0) any = 1;
-  const unsigned long long it = ++(*iter);
-  if (it >= max_iter) any = 0;
-  cudaGraphSetConditional(h, any ? 1u : 0u);
-}
-
-}  // namespace
-
 struct dns_batch {
   std::vector<dns_ctx*> ctx;
-  std::vector<cudaStream_t> streams;   // one branch stream per instance
+  std::vector<cudaStream_t> streams;   // one capture stream per instance
   cudaStream_t stream = nullptr;       // launch stream
-  cudaEvent_t fork = nullptr;
-  std::vector<cudaEvent_t> joins;
-  DnsCtrl** d_ctrls = nullptr;
-  unsigned long long* d_iter = nullptr;
+  unsigned long long* d_iter = nullptr;   // per-instance loop counters
   cudaGraphExec_t exec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   cudaGraph_t graph[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   int device = 0;
@@ -1254,10 +1252,7 @@ void dns_destroy_batch(dns_batch* b) {
   }
   for (dns_ctx* c : b->ctx) dns_destroy(c);
   for (cudaStream_t s : b->streams) if (s) cudaStreamDestroy(s);
-  for (cudaEvent_t e : b->joins) if (e) cudaEventDestroy(e);
-  if (b->fork) cudaEventDestroy(b->fork);
   if (b->stream) cudaStreamDestroy(b->stream);
-  if (b->d_ctrls) cudaFree(b->d_ctrls);
   if (b->d_iter) cudaFree(b->d_iter);
   delete b;
 }
@@ -1275,19 +1270,11 @@ dns_status dns_create_batch(int count, const dns_config* cfgs, dns_batch** out) 
   }
   if (s == DNS_OK) {
     bool ok = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
-              cudaMalloc((void**)&b->d_ctrls, count * sizeof(DnsCtrl*)) == cudaSuccess &&
-              cudaMalloc((void**)&b->d_iter, sizeof(unsigned long long)) == cudaSuccess;
+              cudaMalloc((void**)&b->d_iter, count * sizeof(unsigned long long)) == cudaSuccess;
     b->streams.assign(count, nullptr);
-    b->joins.assign(count, nullptr);
     for (int i = 0; ok && i < count; ++i)
-      ok = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) == cudaSuccess &&
-           cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming) == cudaSuccess;
-    if (ok) {
-      std::vector<DnsCtrl*> h(count);
-      for (int i = 0; i < count; ++i) { h[i] = b->ctx[i]->ctrl; b->ctx[i]->stream = b->stream; }
-      ok = cudaMemcpy(b->d_ctrls, h.data(), count * sizeof(DnsCtrl*), cudaMemcpyHostToDevice) == cudaSuccess;
-    }
+      ok = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; ok && i < count; ++i) b->ctx[i]->stream = b->stream;
     // tile variants per distinct grid from the autotuner (timed once per shape, cached)
     for (int i = 0; ok && i < count; ++i) ok = dns_autotune(b->ctx[i], 3, nullptr) == DNS_OK;
     if (!ok) { cudaGetLastError(); s = DNS_ERR_CUDA; }
@@ -1326,41 +1313,38 @@ dns_status dns_integrate_batch(dns_batch* b, int method, const double* t_end, co
   if (!b->exec[method]) {
     cudaGraph_t g = nullptr;
     if (!cuda(cudaGraphCreate(&g, 0), "graph create")) return DNS_ERR_CUDA;
-    cudaGraphConditionalHandle handle;
-    if (!cuda(cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault), "conditional handle"))
-      return DNS_ERR_CUDA;
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = handle;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t node;
-    if (!cuda(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp), "conditional node")) return DNS_ERR_CUDA;
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    if (!cuda(cudaStreamBeginCaptureToGraph(b->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed),
-              "begin capture"))
-      return DNS_ERR_CUDA;
-    bool ok = cuda(cudaEventRecord(b->fork, b->stream), "fork");
+    bool ok = true;
     for (int i = 0; ok && i < n; ++i) {
       dns_ctx* c = b->ctx[i];
-      ok = cuda(cudaStreamWaitEvent(b->streams[i], b->fork, 0), "fork wait");
+      cudaGraphConditionalHandle handle;
+      ok = cuda(cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault), "conditional handle");
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = handle;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t node;
+      ok = ok && cuda(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp), "conditional node");
+      ok = ok && cuda(cudaStreamBeginCaptureToGraph(b->streams[i], cp.conditional.phGraph_out[0], nullptr, nullptr,
+                                                     0, cudaStreamCaptureModeRelaxed), "begin capture");
+      if (!ok) break;
       c->stream = b->streams[i];
-      if (ok && enqueue_attempt(c, method) != DNS_OK) { b->err = c->err; ok = false; }
+      c->capturing = true;
+      if (enqueue_attempt(c, method) != DNS_OK) { b->err = c->err; ok = false; }
+      c->capturing = false;
+      if (ok) {
+        k_ctx_continue<<<1, 1, 0, b->streams[i]>>>(handle, c->ctrl, b->d_iter + i, 10000000ULL);
+        ok = cuda(cudaGetLastError(), "continue kernel");
+      }
       c->stream = b->stream;
-      ok = ok && cuda(cudaEventRecord(b->joins[i], b->streams[i]), "join") &&
-           cuda(cudaStreamWaitEvent(b->stream, b->joins[i], 0), "join wait");
+      cudaGraph_t captured = nullptr;
+      ok = cuda(cudaStreamEndCapture(b->streams[i], &captured), "end capture") && ok;
     }
-    if (ok) {
-      k_batch_continue<<<1, 1, 0, b->stream>>>(handle, b->d_ctrls, n, b->d_iter, 10000000ULL);
-      ok = cuda(cudaGetLastError(), "continue kernel");
-    }
-    cudaGraph_t captured = nullptr;
-    const bool ended = cuda(cudaStreamEndCapture(b->stream, &captured), "end capture");
-    if (!ok || !ended) { cudaGraphDestroy(g); return DNS_ERR_CUDA; }
+    if (!ok) { cudaGraphDestroy(g); return DNS_ERR_CUDA; }
     if (!cuda(cudaGraphInstantiate(&b->exec[method], g, 0), "instantiate")) { cudaGraphDestroy(g); return DNS_ERR_CUDA; }
     b->graph[method] = g;
   }
-  if (!cuda(cudaMemsetAsync(b->d_iter, 0, sizeof(unsigned long long), b->stream), "reset counter") ||
+  if (!cuda(cudaMemsetAsync(b->d_iter, 0, n * sizeof(unsigned long long), b->stream), "reset counters") ||
       !cuda(cudaGraphLaunch(b->exec[method], b->stream), "graph launch") ||
       !cuda(cudaStreamSynchronize(b->stream), "synchronize"))
     return DNS_ERR_CUDA;

@@ -42,7 +42,18 @@ struct PassArgs {
   int p3_bulk;           // z pass: stage input rows with bulk copies (rows a multiple of 16 B)
   int p3_stall;          // debug: block 0's bulk-copy barrier expects this many extra bytes
   int epi32;             // P5 epilogue (viscous term, forcing) in FP32 (DNS_FP32 form)
+  int p3_rr;             // z pass: the register-resident FP32 kernel where it applies (autotuned)
 };
+
+// The register-resident FP32 z pass (zpass_rr.cuh) handles nz = 64, 128, 256 in the velocity
+// form.  It takes a launch when selected and when a tile's rows can be bulk-copied: TL Mz
+// complex values per field starting on a 16-byte boundary, a multiple of 16 bytes long
+// (Mz even, or nx ny even).
+__host__ __device__ constexpr bool zrr_supported(int nz) { return nz == 64 || nz == 128 || nz == 256; }
+inline bool p3_rr_applies(const PassArgs& a) {
+  return a.p3_rr && !a.g.bouss && zrr_supported(a.g.nz) &&
+         (a.g.Mz % 2 == 0 || ((long long)a.g.nx * a.g.ny) % 2 == 0);
+}
 
 // ---- bulk copies (TMA engine) completing on a CTA-local mbarrier ---------------------------
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }

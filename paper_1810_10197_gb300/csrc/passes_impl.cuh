@@ -3,12 +3,27 @@
 #pragma once
 
 #include "passes.cuh"
+#include "zpass_rr.cuh"
 
 namespace dns {
 
 template <typename K>
 static cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Persistent grid: as many CTAs as the device holds at once (at most one per tile).
+template <typename K>
+static cudaError_t persistent_grid(K kernel, int threads, size_t smem, long long tiles, unsigned* grid) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem)) != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const long long cap = (long long)sms * per_sm;
+  *grid = (unsigned)(tiles < cap ? (tiles > 0 ? tiles : 1) : cap);
+  return cudaSuccess;
 }
 
 template <typename T, int N, bool B>
@@ -76,8 +91,30 @@ static cudaError_t launch_p3_v(const PassArgs& a, cudaStream_t s) {
   k_p3<T, MZ, B, VAR><<<grid, FftPlan<MZ>::G * NIN * TL, smem, s>>>(b);
   return cudaGetLastError();
 }
+// The register-resident FP32 z pass: persistent CTAs of 128 threads, as many as fit on the
+// device at once; the tile variant selects paired (0) or scalar (1) FP32 arithmetic.
+template <int N, bool PAIRED>
+static cudaError_t launch_p3_rr_v(const PassArgs& a, cudaStream_t s) {
+  const size_t smem = zrr_smem<N>(a.g.Mz);
+  cudaError_t e = set_smem(k_p3_rr<N, PAIRED>, smem);
+  if (e != cudaSuccess) return e;
+  const long long nxy = (long long)a.g.nx * a.g.ny;
+  const long long tiles = (nxy + ZrrPlan<N, 128>::TL - 1) / ZrrPlan<N, 128>::TL;
+  unsigned grid = 0;
+  if ((e = persistent_grid(k_p3_rr<N, PAIRED>, 128, smem, tiles, &grid)) != cudaSuccess) return e;
+  k_p3_rr<N, PAIRED><<<grid, 128, smem, s>>>(a);
+  return cudaGetLastError();
+}
+template <int N>
+static cudaError_t launch_p3_rr(const PassArgs& a, cudaStream_t s) {
+  return a.var_p3 ? launch_p3_rr_v<N, false>(a, s) : launch_p3_rr_v<N, true>(a, s);
+}
+
 template <typename T, int MZ, bool B>
 static cudaError_t launch_p3(const PassArgs& a, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value && !B && zrr_supported(2 * MZ)) {
+    if (p3_rr_applies(a)) return launch_p3_rr<2 * MZ>(a, s);
+  }
   return a.var_p3 ? launch_p3_v<T, MZ, B, 1>(a, s) : launch_p3_v<T, MZ, B, 0>(a, s);
 }
 

@@ -112,6 +112,7 @@ _SIGS.update({
     "dns_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "dns_crc32": (C.c_uint, [C.c_void_p, C.c_size_t, C.c_uint]),
     "dns_debug_f32_from_f64": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]),
+    "dns_measure_fp64_rate": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
 })
 TRACE_COLS = 8
 MLP_PARAMS = 5313
@@ -392,6 +393,16 @@ def dns_crc32(data: bytes, crc: int = 0) -> int:
     """CRC-32 of the checkpoint trailer (host code, no GPU needed)."""
     buf = C.create_string_buffer(bytes(data), len(data))
     return int(load().dns_crc32(buf, len(data), crc))
+
+
+def dns_measure_fp64_rate(stream=None):
+    """(DFMA, DADD) thread instructions per second of the current device's FP64 pipe."""
+    a, b = C.c_double(), C.c_double()
+    h = getattr(stream, "cuda_stream", stream)
+    st = load().dns_measure_fp64_rate(C.c_void_p(h) if h else None, C.byref(a), C.byref(b))
+    if st != DNS_OK:
+        raise DnsError(st, "dns_measure_fp64_rate")
+    return a.value, b.value
 
 
 def dns_debug_f32_from_f64(x_dev, y_dev, stream=None):

@@ -7,7 +7,7 @@ import pytest
 import synthetic as syn
 from oracle import rk
 from oracle import spectral as sp
-from tests.gpu_helpers import lib_ready, rel_l2, require_gpu, to_dev
+from tests.gpu_helpers import rel_max, lib_ready, rel_l2, require_gpu, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -75,8 +75,23 @@ def test_tile_variants_give_identical_results_and_autotune_picks_one(shape, prec
         outs.append(f.cpu().numpy())
     for o in outs[1:]:
         assert np.array_equal(o, outs[0])      # the same arithmetic per line, any tiling
+    # z pass codes 4 and 5: the register-resident FP32 kernel (single-precision forms, nz = 64,
+    # 128, 256; elsewhere codes 0 and 1) with paired or scalar FP32 instructions (the scalar
+    # form lets the compiler fuse some products into FMAs): against each other and against
+    # codes 0..3 (another schedule) they agree to FP32 rounding
+    rr = []
+    for v in ((0, 4), (1, 5)):
+        d.set_tiles(*v)
+        f = torch.empty_like(u)
+        d.rhs(u, f)
+        torch.cuda.synchronize()
+        rr.append(f.cpu().numpy())
+    if precision == "fp64":
+        assert np.array_equal(rr[0], outs[0]) and np.array_equal(rr[1], outs[0])
+    else:
+        assert rel_max(rr[1], rr[0]) < 2e-5 and rel_max(rr[0], outs[0]) < 2e-5
     vpy, vp3 = d.autotune(reps=2)
-    assert vpy in (0, 1) and vp3 in (0, 1, 2, 3)   # z pass: bit 0 tile, bit 1 element copies
+    assert vpy in (0, 1) and vp3 in range(6)   # z pass: bit 0 tile, bit 1 element copies, bit 2 RR kernel
     d.close()
 
 
