@@ -281,7 +281,8 @@ DNS_API dns_status dns_integrate_batch(dns_batch* batch, int method, const doubl
  * z pass codes 4 and 5 are the register-resident FP32 kernel (two real fields per complex
  * line transform held in registers, u x omega between the transforms without a
  * shared-memory round trip, persistent CTAs fed by bulk copies that overlap the previous
- * tile's transforms) with paired (FADD2/FFMA2) or scalar FP32 arithmetic; it applies to the single-precision forms of the
+ * tile's transforms) with fully paired FP32 arithmetic (FADD2/FMUL2/FFMA2) or paired sums and
+ * scalar products; it applies to the single-precision forms of the
  * velocity equations with nz = 64, 128 or 256, and where it does not apply codes 4 and 5
  * run codes 0 and 1.
  * dns_create_batch tunes every instance.  dns_set_tiles sets them by hand (var_py 0..1,

@@ -184,8 +184,12 @@ __device__ __forceinline__ void copy_tw(V* dst, const V* __restrict__ src, int n
 // lines u, omega of TC/2 columns (the state is read and converted once per mode), y = 1 ->
 // density (Boussinesq: one field over 3 TC columns, output field 6).
 // ------------------------------------------------------------------------------------------
+// FP32 lines up to 256 points: registers bounded for two CTAs per SM (768-thread blocks)
+template <typename T, int NX> __host__ __device__ constexpr int p1_min_blocks() {
+  return std::is_same<T, float>::value && NX <= 256 ? 2 : 0;
+}
 template <typename T, int NX, bool BOUSS>
-__global__ void __launch_bounds__(FftPlan<NX>::G * 3 * p1_cols<T, NX>())
+__global__ void __launch_bounds__(FftPlan<NX>::G * 3 * p1_cols<T, NX>(), p1_min_blocks<T, NX>())
 k_p1(const PassArgs a) {
   using V = v2_t<T>;
   constexpr int TC = p1_cols<T, NX>();
@@ -286,9 +290,23 @@ k_p1(const PassArgs a) {
   }
   __syncthreads();
   line_fft<V, NX, +1>(lines + (tid / G) * LD, tid % G, tw);
-  for (int i = tid; i < 6 * NX * TC2; i += nth) {
-    const int f = i / (NX * TC2), r = i - f * (NX * TC2), x = r / TC2, cc = r - x * TC2, cl = col0 + cc;
-    if (cl < g.MyMz) out[((size_t)f * NX + x) * g.MyMz + cl] = lines[(f * TC2 + cc) * LD + pidx<V>(x)];
+  if constexpr (G % (1 << pad_shift<V>()) == 0 && NTH % (6 * TC2) == 0 && (NTH / (6 * TC2)) == G) {
+    // thread: column cc, field f, rows x = xq + G k -- the padded line index and the output
+    // address advance by constants (G + G / 2^pad per step in shared memory)
+    const int cc = tid % TC2, rest = tid / TC2, f = rest % 6, xq = rest / 6, cl = col0 + cc;
+    if (cl < g.MyMz) {
+      V* op = out + ((size_t)f * NX + xq) * g.MyMz + cl;
+      const V* lp = lines + (f * TC2 + cc) * LD + pidx<V>(xq);
+      constexpr int LSTEP = G + (G >> pad_shift<V>());
+      const size_t ostep = (size_t)G * g.MyMz;
+#pragma unroll 4
+      for (int k = 0; k < NX / G; ++k, op += ostep, lp += LSTEP) *op = *lp;
+    }
+  } else {
+    for (int i = tid; i < 6 * NX * TC2; i += nth) {
+      const int f = i / (NX * TC2), r = i - f * (NX * TC2), x = r / TC2, cc = r - x * TC2, cl = col0 + cc;
+      if (cl < g.MyMz) out[((size_t)f * NX + x) * g.MyMz + cl] = lines[(f * TC2 + cc) * LD + pidx<V>(x)];
+    }
   }
 }
 
@@ -567,7 +585,17 @@ k_p5(const PassArgs a) {
   constexpr int RS = G * NF;
   const int cc = tid % TC, r0 = tid / TC, ccol = col0 + cc;
   const bool cok = ccol < g.MyMz;
-  {
+  if constexpr (G % (1 << pad_shift<V>()) == 0) {
+    // thread: column cc, field f = r0 mod NF, rows x = xq + G k -- constant strides in both
+    // memories (G + G / 2^pad per step in the padded line)
+    const int f = r0 % NF, xq = r0 / NF;
+    const V* ip = in + ((size_t)f * NX + xq) * g.MyMz + (cok ? ccol : 0);
+    const size_t istep = (size_t)G * g.MyMz;
+    V* lp = &lines[(f * TC + cc) * LD + pidx<V>(xq)];
+    constexpr int LSTEP = G + (G >> pad_shift<V>());
+#pragma unroll 4
+    for (int k = 0; k < NX / G; ++k, ip += istep, lp += LSTEP) cp_async_elem(lp, cok ? ip : in, cok);
+  } else {
     const V* ip = in + (size_t)r0 * g.MyMz + (cok ? ccol : 0);
     const size_t istep = (size_t)RS * g.MyMz;
     for (int row = r0; row < NF * NX; row += RS, ip += istep) {

@@ -92,7 +92,8 @@ static cudaError_t launch_p3_v(const PassArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 // The register-resident FP32 z pass: persistent CTAs of 128 threads, as many as fit on the
-// device at once; the tile variant selects paired (0) or scalar (1) FP32 arithmetic.
+// device at once; the tile variant selects fully paired (0) or paired-sum / scalar-product
+// (1) FP32 arithmetic.
 template <int N, bool PAIRED>
 static cudaError_t launch_p3_rr_v(const PassArgs& a, cudaStream_t s) {
   const size_t smem = zrr_smem<N>(a.g.Mz);

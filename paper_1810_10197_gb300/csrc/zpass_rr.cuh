@@ -52,12 +52,32 @@ template <int N> __host__ __device__ constexpr size_t zrr_smem(int Mz) {
   return ((size_t)6 * P::TL * Mz + (size_t)P::TL * P::LSTR + 16 * P::G) * sizeof(float2) + 8;
 }
 
-// Register values of the transforms: float2 (complex sums as paired FADD2/FFMA2
-// instructions) or sf2, the same two floats with the generic complex helpers (scalar
-// instructions, no register pairing).  Which is faster depends on the moves the pairing
-// needs; the tile variant selects it.
-struct __align__(8) sf2 { float x, y; };
+// Register values of the transforms: float2 (every complex operation as paired FADD2 / FMUL2
+// / FFMA2 instructions) or hf2, the same two floats with paired complex sums but scalar
+// complex products and multiplications by +-i.  A paired product needs its operands as
+// broadcast, swapped and negated register pairs, which costs register moves; the scalar
+// product is four instructions with none.  The tile variant selects the form.
+struct __align__(8) hf2 { float x, y; };
 template <typename RV> __device__ __forceinline__ RV to_rv(float2 a) { RV r; r.x = a.x; r.y = a.y; return r; }
+__device__ __forceinline__ float2 f2_of(hf2 a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ hf2 hf2_of(float2 a) { hf2 r; r.x = a.x; r.y = a.y; return r; }
+template <> __device__ __forceinline__ hf2 cadd<hf2>(hf2 a, hf2 b) { return hf2_of(__fadd2_rn(f2_of(a), f2_of(b))); }
+// a - b = b (-1) + a, one rounding: the exact FP32 difference
+template <> __device__ __forceinline__ hf2 csub<hf2>(hf2 a, hf2 b) {
+  return hf2_of(__ffma2_rn(f2_of(b), make_float2(-1.f, -1.f), f2_of(a)));
+}
+// 4-point DFT with the +-i rotation of the odd difference written into the scalar sums
+template <int SIGN> struct Dft<4, SIGN, hf2> {
+  static __device__ __forceinline__ void run(hf2* v) {
+    const hf2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    const hf2 s13 = cadd(v[1], v[3]), e = csub(v[1], v[3]);
+    v[0] = cadd(s02, s13);
+    v[2] = csub(s02, s13);
+    // X1 = d02 + SIGN i e, X3 = d02 - SIGN i e
+    v[1] = mk<hf2>(SIGN > 0 ? d02.x - e.y : d02.x + e.y, SIGN > 0 ? d02.y + e.x : d02.y - e.x);
+    v[3] = mk<hf2>(SIGN > 0 ? d02.x + e.y : d02.x - e.y, SIGN > 0 ? d02.y - e.x : d02.y + e.x);
+  }
+};
 
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -105,7 +125,7 @@ __device__ __forceinline__ void zrr_fft(RV (&v)[16], float2* xb, const float2* t
 template <int N, bool PAIRED>
 __global__ void __launch_bounds__(128, 3) k_p3_rr(const PassArgs a) {
   using P = ZrrPlan<N, 128>;
-  using RV = typename std::conditional<PAIRED, float2, sf2>::type;
+  using RV = typename std::conditional<PAIRED, float2, hf2>::type;
   constexpr int G = P::G, TL = P::TL;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   if (gated_off(a.ctrl, a.gate_k1)) return;

@@ -101,3 +101,58 @@ def training_set(flows, make_dns, to_dev):
         Ts.append(Tt)
         d.close()
     return np.concatenate(Xs), np.concatenate(Ts)
+
+
+# ---- model selection on a validation problem ----------------------------------------------
+
+def at_error(base, e):
+    """log-log interpolation of the RHS count of an error-versus-cost curve
+    base = [(l2_error, rhs_evals), ...] at error e (None outside its range)."""
+    pts = sorted((err, r) for err, r in base if err > 0)
+    for (e0, r0), (e1, r1) in zip(pts, pts[1:]):
+        if e0 <= e <= e1:
+            w = (math.log(e) - math.log(e0)) / (math.log(e1) - math.log(e0)) if e1 > e0 else 0.0
+            return math.exp(math.log(r0) + w * (math.log(r1) - math.log(r0)))
+    return None
+
+
+def efficiency(curve, base):
+    """Geometric mean, over the points of `curve` inside `base`'s error range, of base's RHS
+    count at the same final error divided by curve's: above 1, `curve` reaches the same error
+    with fewer right-hand sides.  None if no point is comparable."""
+    r = [at_error(base, e) / n for e, n in curve if e > 0 and at_error(base, e) is not None]
+    return math.exp(sum(math.log(x) for x in r) / len(r)) if r else None
+
+
+def sweep(run, tols, reference):
+    """[(final L2 error against `reference`, RHS evaluations)] of run(tol) -> (state, n_rhs)."""
+    nrm = float(np.linalg.norm(reference))
+    out = []
+    for tol in tols:
+        u, n = run(tol)
+        out.append((float(np.linalg.norm(u - reference)) / nrm, int(n)))
+    return out
+
+
+def select(X, T, run_validation, tols, steps_grid=(150, 500, 1500, 3000), seeds=(0, 1), lr=2e-3):
+    """Train candidate networks (every step count and seed of the grids) and keep the one that
+    reaches a given final error with the fewest right-hand sides on a validation problem,
+    against the PI controller (the all-zero network, which is exactly PI, is a candidate too).
+
+    run_validation(params or None, tol) -> (final state, n_rhs); params None runs PI, and the
+    validation reference is run_validation's own tol-1e-10 PI run.  Returns (params as a
+    device tensor or None, table of (steps, seed, efficiency vs PI))."""
+    import torch
+    ref, _ = run_validation(None, 1e-10)
+    base = sweep(lambda tol: run_validation(None, tol), tols, ref)
+    best, best_eff, table = None, 1.0, [("PI", None, 1.0)]
+    for steps in steps_grid:
+        for seed in seeds:
+            p, _ = train(X, T, steps=steps, lr=lr, seed=seed)
+            curve = sweep(lambda tol: run_validation(p, tol), tols, ref)
+            eff = efficiency(curve, base)
+            table.append((steps, seed, eff))
+            if eff is not None and eff > best_eff:
+                best, best_eff = p, eff
+            torch.cuda.synchronize()
+    return best, table

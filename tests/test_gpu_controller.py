@@ -128,47 +128,75 @@ def trajectories(flows):
     return learned.training_set(flows, lambda shape, nu, forcing: Dns(*shape, nu=nu, forcing=forcing), to_dev)
 
 
-def test_learned_controller_gain_on_rayleigh_taylor():
-    """Train on TG and forced-HIT trajectories, apply to a Rayleigh-Taylor run (held out)."""
-    from paper_1810_10197_gb300 import Dns, learned
+def rt_run(shape, seed, kind, tol, T, params=None):
+    """Periodic Rayleigh-Taylor (Section 3.2, the two-interface periodic setup) from rest;
+    returns (final state, RHS evaluations)."""
+    from paper_1810_10197_gb300 import Dns
+    Y, L = syn.rayleigh_taylor_hat(*shape, seed=seed, width=0.2, amplitude=1e-2)
+    d = Dns(*shape, nu=1e-3, lengths=L, boussinesq=(1e-3, 1.0))
+    d.set_state(to_dev(Y), 0.0)
+    if kind == "MLP":
+        d.set_controller("MLP", params)
+    elif kind == "PI":
+        d.set_controller("PI")
+    info = d.integrate(T, "BS5_ADAPTIVE", tol, tol, h0=1e-3)
+    u = d.get_state()
+    d.close()
+    return u, info.n_rhs
+
+
+def test_learned_controller_selected_on_validation_and_applied_to_held_out_rt():
+    """Train candidates on PI trajectories of Taylor-Green, forced HIT and small Rayleigh-Taylor
+    runs; keep the candidate that is most efficient at equal final error on a validation RT
+    problem (the all-zero network, i.e. PI itself, included); apply it to a held-out RT problem
+    (other seed and grid) and compare RHS evaluations at equal final error with PI and with the
+    Section 2.2.1 controller over a tolerance sweep."""
+    from paper_1810_10197_gb300 import learned
     flows = []
     for tol in (1e-5, 1e-6, 1e-7, 1e-8):
         for n, nu in ((32, 0.01), (32, 0.005)):
             flows.append(((n, n, n), syn.taylor_green_3d_hat(n, n, n), nu, None, tol, 2.0))
-            flows.append(((n, n, n), syn.random_solenoidal_hat(n, n, n, seed=3, k0=3.0), nu, (2.5, 0.05),
-                          tol, 1.0))
+        flows.append(((32, 32, 32), syn.random_solenoidal_hat(32, 32, 32, seed=3, k0=3.0), 0.01, (2.5, 0.05),
+                      tol, 1.0))
     X, T = trajectories(flows)
-    assert len(X) > 100
-    params, hist = learned.train(X, T, steps=3000, lr=2e-3, seed=0)
-    assert hist[-200:].mean() < hist[:20].mean()
-    # held-out problem: periodic RT at 32 x 32 x 64, from rest to t = 3
-    shape = (32, 32, 64)
-    rho, L = syn.rayleigh_taylor_fields(*shape, seed=7, width=0.2, amplitude=1e-2)
-    g = sp.Grid(*shape, lengths=L)
-    Y = np.zeros((4, 32, 32, 33), complex)
-    Y[3] = g.dealias(g.to_spectral(rho))
-    res = {}
-    for kind in ("I", "PI", "MLP", "REF"):
-        d = Dns(*shape, nu=1e-3, lengths=L, boussinesq=(1e-3, 1.0))
-        d.set_state(to_dev(Y), 0.0)
-        if kind == "MLP":
-            d.set_controller("MLP", params)
-        elif kind == "PI":
+    Xr, Tr = [], []
+    from paper_1810_10197_gb300 import Dns
+    for seed in (11, 12):
+        for tol in (1e-5, 1e-6, 1e-7):
+            Y, L = syn.rayleigh_taylor_hat(16, 16, 32, seed=seed, width=0.2, amplitude=1e-2)
+            d = Dns(16, 16, 32, nu=1e-3, lengths=L, boussinesq=(1e-3, 1.0))
             d.set_controller("PI")
-        tol = 1e-10 if kind == "REF" else 1e-6
-        d.set_trace(100000)
-        info = d.integrate(3.0, "BS5_ADAPTIVE", tol, tol, h0=1e-3)
-        tr = d.trace()
-        acc = tr[tr[:, 3] > 0.5]
-        assert np.all(acc[:, 2] <= 1.0)
-        res[kind] = (info.n_rhs, info.n_rej, d.get_state())
-        d.close()
-    ref = res["REF"][2]
-    line = []
+            d.set_state(to_dev(Y), 0.0)
+            d.set_trace(20000)
+            d.integrate(3.0, "BS5_ADAPTIVE", tol, tol, h0=1e-3)
+            a, b = learned.pairs_from_trace(d.trace())
+            Xr.append(a)
+            Tr.append(b)
+            d.close()
+    X, T = np.concatenate([X] + Xr), np.concatenate([T] + Tr)
+    assert len(X) > 200
+    tols = (1e-5, 1e-6, 1e-7)
+    params, table = learned.select(X, T, lambda p, tol: rt_run((24, 24, 48), 13, "PI" if p is None else "MLP",
+                                                               tol, 2.0, p), tols)
+    best = max(e for _, _, e in table if e is not None)
+    assert best >= 1.0        # PI is a candidate: the selection never picks a worse one
+    # held-out problem: RT 32 x 32 x 64, seed 7, from rest to t = 3
+    ref, _ = rt_run((32, 32, 64), 7, "I", 1e-10, 3.0)
+    curves = {}
     for kind in ("I", "PI", "MLP"):
-        nr, nj, u = res[kind]
-        line.append(f"{kind}: {nr} RHS, {nj} rejected, L2 err vs tol-1e-10 run {rel_l2(u, ref):.2e}")
-    print("\nRT 32x32x64 to t=3, tol 1e-6 | " + " | ".join(line))
-    # every controller reaches t_end within the tolerance regime (error well below 1e-3)
-    for kind in ("I", "PI", "MLP"):
-        assert rel_l2(res[kind][2], ref) < 1e-3
+        k = "MLP" if (kind == "MLP" and params is not None) else ("PI" if kind == "MLP" else kind)
+        curves[kind] = learned.sweep(lambda tol: rt_run((32, 32, 64), 7, k, tol, 3.0, params), tols, ref)
+    eff_pi = learned.efficiency(curves["MLP"], curves["PI"])
+    eff_i = learned.efficiency(curves["MLP"], curves["I"])
+    pi_vs_i = learned.efficiency(curves["PI"], curves["I"])
+    print(f"\nvalidation (RT 24x24x48, seed 13) efficiency vs PI per candidate: {table}")
+    print(f"held out (RT 32x32x64, seed 7): selected network vs PI {eff_pi}, vs I {eff_i}; PI vs I {pi_vs_i}")
+    print("curves (L2 error, RHS):", curves)
+    # every run reaches t_end within the tolerance regime
+    for c in curves.values():
+        assert all(e < 1e-3 for e, _ in c)
+    # the measured relation: the validation-selected controller is within 10% of PI at equal
+    # error on the held-out problem (identical to PI when the selection keeps the zero network)
+    assert eff_pi is not None and eff_pi >= 0.9
+    if params is None:
+        assert curves["MLP"] == curves["PI"]
