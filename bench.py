@@ -578,10 +578,12 @@ def run_controllers(args):
     """The learned step-size proposal against the Section 2.2.1 (I) and PI controllers on
     periodic Boussinesq Rayleigh-Taylor (128 x 128 x 256, Atwood 0.5, tanh interfaces of width
     0.05, multimode perturbation 1e-3, nu = kappa = 1e-3, Ri = 1), each over a tolerance
-    sweep and compared at equal final error.  The network corrects the PI factor; it is
-    trained on the GPU from PI-controlled trajectories of Taylor-Green and forced-HIT flows
-    (32^3 and 48^3, tolerances 1e-5..1e-8); every run is measured against a tol-1e-9 FP64
-    reference of the same problem."""
+    sweep and compared at equal final error.  The network corrects the PI factor; candidates
+    are trained on the GPU from PI-controlled trajectories of Taylor-Green and forced-HIT
+    flows (32^3 and 48^3, tolerances 1e-5..1e-8) and small RT runs (16x16x32, seeds 11, 12),
+    and the one most efficient at equal error on a validation RT problem (default 64x64x128,
+    seed 13, interface width 0.1) is kept (PI itself is a candidate); every run is measured
+    against a tol-1e-9 FP64 reference of the same problem."""
     import torch
 
     import synthetic as syn
@@ -596,7 +598,39 @@ def run_controllers(args):
             flows.append(((m, m, m), syn.random_solenoidal_hat(m, m, m, seed=3 + m, k0=3.0), nu, (2.5, 0.05), tol, 1.0))
     X, T = learned.training_set(flows, lambda shape, nu, forcing: Dns(*shape, nu=nu, forcing=forcing),
                                 lambda a: torch.from_numpy(a).cuda())
-    params, hist = learned.train(X, T, steps=3000, lr=2e-3, seed=0)
+    # small periodic Rayleigh-Taylor runs (seeds 11, 12; neither the validation nor the
+    # measured problem) under PI, as in the controller test
+    Xr, Tr = [X], [T]
+    for seed in (11, 12):
+        for tol in (1e-5, 1e-6, 1e-7):
+            Ys, Ls = syn.rayleigh_taylor_hat(16, 16, 32, seed=seed, width=0.2, amplitude=1e-2)
+            d = Dns(16, 16, 32, nu=1e-3, lengths=Ls, boussinesq=(1e-3, 1.0))
+            d.set_controller("PI")
+            d.set_state(torch.from_numpy(Ys).cuda(), 0.0)
+            d.set_trace(20000)
+            d.integrate(3.0, "BS5_ADAPTIVE", tol, tol, h0=1e-3)
+            a, b = learned.pairs_from_trace(d.trace())
+            Xr.append(a)
+            Tr.append(b)
+            d.close()
+    X, T = np.concatenate(Xr), np.concatenate(Tr)
+
+    vshape = tuple(args.val_shape)
+
+    def run_validation(p, tol):
+        # validation problem: the same family as the measured one at a smaller grid and
+        # another seed (13), interfaces as wide as the grid resolves, from rest to t_end
+        Yv, Lv = syn.rayleigh_taylor_hat(*vshape, seed=13, width=args.val_width)
+        d = Dns(*vshape, nu=1e-3, lengths=Lv, boussinesq=(1e-3, 1.0))
+        d.set_state(torch.from_numpy(Yv).cuda(), 0.0)
+        d.set_controller("PI" if p is None else "MLP", p)
+        info = d.integrate(args.t_end, "BS5_ADAPTIVE", tol, tol, h0=1e-3)
+        u = d.get_state()
+        d.close()
+        return u, info.n_rhs
+
+    params, table = learned.select(X, T, run_validation, (1e-5, 1e-6, 1e-7))
+    hist = np.zeros(1)
     train_s = time.perf_counter() - t_start
     nx, ny, nz = args.rt_shape
     Y, L = syn.rayleigh_taylor_hat(nx, ny, nz, seed=7)   # set_state keeps the 2/3 box
@@ -607,10 +641,10 @@ def run_controllers(args):
         d = Dns(nx, ny, nz, nu=1e-3, lengths=L, boussinesq=(1e-3, 1.0), precision=precision)
         d.autotune()
         d.set_state(Yd, 0.0)
-        if kind == "MLP":
+        if kind == "MLP" and params is not None:
             d.set_controller("MLP", params)
-        elif kind == "PI":
-            d.set_controller("PI")
+        elif kind in ("PI", "MLP"):
+            d.set_controller("PI")            # the selection kept the zero network: PI itself
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record()
@@ -661,8 +695,12 @@ def run_controllers(args):
                       "precision": args.precision,
                       "reference": f"BS5 adaptive tol {args.ref_tol:g} (I controller)",
                       "reference_rhs_evals": int(i_ref.n_rhs), "training_pairs": int(len(X)),
-                      "training_loss_first_last": [float(hist[:20].mean()), float(hist[-200:].mean())],
-                      "training_seconds_incl_trajectories": train_s},
+                      "selection": {"validation": f"RT {vshape[0]}x{vshape[1]}x{vshape[2]} seed 13, interface "
+                                                  f"width {args.val_width}, t 0-{args.t_end:g}, "
+                                                  "tolerances 1e-5..1e-7",
+                                    "candidates_efficiency_vs_PI": [list(r) for r in table],
+                                    "selected": "zero network (PI)" if params is None else "trained network"},
+                      "training_seconds_incl_trajectories_and_selection": train_s},
            "runs": rows,
            "curves": curves,
            "at_equal_error_vs_I": equal_error,
@@ -1025,6 +1063,10 @@ def main():
     ap.add_argument("--mode", default="step", choices=["step", "rhs"])
     ap.add_argument("--workload", default="single", choices=["single", "ensemble", "accuracy", "controllers"])
     ap.add_argument("--rt-shape", type=int, nargs=3, default=[128, 128, 256])
+    ap.add_argument("--val-shape", type=int, nargs=3, default=[64, 64, 128],
+                    help="grid of the controllers workload's validation problem (seed 13)")
+    ap.add_argument("--val-width", type=float, default=0.1,
+                    help="interface width of the validation problem")
     ap.add_argument("--ref-tol", type=float, default=1e-9)
     ap.add_argument("--ctrl-tols", type=float, nargs="+", default=[1e-5, 1e-6, 1e-7, 1e-8],
                     help="tolerance sweep of the controllers workload")
