@@ -20,9 +20,11 @@ FP64_TOL = 1e-13
 FP32_TOL = 2e-5
 
 
-def run_rhs(shape, uh, nu, precision="fp64", lengths=None, forcing=None):
+def run_rhs(shape, uh, nu, precision="fp64", lengths=None, forcing=None, tiles=None):
     from paper_1810_10197_gb300 import Dns
     d = Dns(*shape, nu=nu, precision=precision, lengths=lengths, forcing=forcing)
+    if tiles is not None:
+        d.set_tiles(*tiles)
     u = to_dev(uh)
     f = torch.empty_like(u)
     d.rhs(u, f)
@@ -94,6 +96,12 @@ def test_rhs_full_size_256_against_oracle():
         ref = sp.rhs(g, uh, nu)
         got = run_rhs(shape, uh, nu)
         assert rel_max(got, ref) < FP64_TOL
+        # the single-precision forms at this size, with the register-resident z pass (tile
+        # code 4) and with the shared-memory one (code 0)
+        for precision in ("fp32_mixed", "fp32"):
+            for tiles in ((0, 4), (1, 0)):
+                got = run_rhs(shape, uh, nu, precision, tiles=tiles)
+                assert rel_max(got, ref) < FP32_TOL, (precision, tiles)
 
 
 @pytest.fixture(scope="module")
