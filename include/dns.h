@@ -270,7 +270,10 @@ DNS_API dns_status dns_integrate_batch(dns_batch* batch, int method, const doubl
                                const double* atol, const double* h0, dns_step_info* info);
 
 /* Autotuner of the FFT tile shapes.  The y passes (columns per CTA) have two compiled tile
- * variants (0: full, 1: half).  The z pass has four codes: bit 0 the tile variant (lines per
+ * variants (0: full, 1: half) and, in the single-precision forms at ny = 256 with an even
+ * number of retained kz planes, a third (2: the plane's rows moved by bulk copies, the TMA
+ * engine, one per row of the tile's 8 columns, into a padded shared-memory stage, line
+ * transforms held in registers, rows stored by bulk copies; elsewhere 2 runs variant 0).  The z pass has four codes: bit 0 the tile variant (lines per
  * CTA, full or half), bit 1 set = input rows copied element by element instead of by bulk
  * copies (the TMA engine, completing on a shared-memory barrier; used where a row is a
  * multiple of 16 bytes and the staging fits in shared memory, else element copies anyway).
@@ -285,8 +288,8 @@ DNS_API dns_status dns_integrate_batch(dns_batch* batch, int method, const doubl
  * scalar products; it applies to the single-precision forms of the
  * velocity equations with nz = 64, 128 or 256, and where it does not apply codes 4 and 5
  * run codes 0 and 1.
- * dns_create_batch tunes every instance.  dns_set_tiles sets them by hand (var_py 0..1,
- * var_p3 0..5; the default is 0 and 4).  Synchronous.
+ * dns_create_batch tunes every instance.  dns_set_tiles sets them by hand (var_py 0..2,
+ * var_p3 0..5; the default is 2 and 4).  Synchronous.
  * A bulk copy's completion is awaited with a bound (about half a second); a wait that runs
  * out marks the step controller DNS_ERR_TIMEOUT instead of hanging. */
 DNS_API dns_status dns_autotune(dns_ctx* ctx, int reps, int* variants);

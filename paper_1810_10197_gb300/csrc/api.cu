@@ -118,7 +118,7 @@ struct dns_ctx {
   double* trace_buf = nullptr;     // attempt records (dns_set_trace)
   int trace_diag = 0;
   float* mlp_buf = nullptr;        // learned-controller parameters (dns_set_controller)
-  int var_py = 0, var_p3 = 0;      // tile variants (dns_autotune)
+  int var_py = 2, var_p3 = 0;      // tile variants (dns_autotune; y variant 2 runs 0 where it does not apply)
   int p3_bulk = 1;                 // z pass input by bulk copies where possible (dns_autotune)
   int p3_rr = 1;                   // z pass: register-resident FP32 kernel where it applies
   bool stall_pending = false;      // dns_debug_stall: the next host-enqueued z pass stalls
@@ -1133,14 +1133,17 @@ dns_status dns_autotune(dns_ctx* c, int reps, int* variants) {
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0), "event");
   CK(cudaEventCreate(&e1), "event");
-  // y pass: tile variants 0, 1; z pass: codes 0..3 (bit 0 tile variant, bit 1 per-element
-  // copies instead of bulk copies) and, where it applies, 4 and 5 (the register-resident
-  // FP32 kernel with its two tile variants)
+  // y pass: tile variants 0, 1 and, where it applies, 2 (tensor-map tile copies and
+  // register-resident transforms, FP32 forms); z pass: codes 0..3 (bit 0 tile variant, bit 1
+  // per-element copies instead of bulk copies) and, where it applies, 4 and 5 (the
+  // register-resident FP32 kernel with its two tile variants)
   a.p3_rr = 1;
-  const bool rr_ok = (c->precision == DNS_FP32_MIXED || c->precision == DNS_FP32) && p3_rr_applies(a);
+  const bool f32 = c->precision == DNS_FP32_MIXED || c->precision == DNS_FP32;
+  const bool rr_ok = f32 && p3_rr_applies(a);
+  const bool yb_ok = f32 && ytma_supported(c->g.ny, c->g.Mz);
   float best[2][6] = {{0, 0, 1e30f, 1e30f, 1e30f, 1e30f}, {0, 0, 0, 0, 1e30f, 1e30f}};
   for (int which = 0; which < 2; ++which) {        // 0: y pass (P2), 1: z pass (P3)
-    for (int v = 0; v < (which == 0 ? 2 : (rr_ok ? 6 : 4)); ++v) {
+    for (int v = 0; v < (which == 0 ? (yb_ok ? 3 : 2) : (rr_ok ? 6 : 4)); ++v) {
       a.var_py = which == 0 ? v : 0;
       a.var_p3 = which == 1 ? (v & 1) : 0;
       a.p3_bulk = which == 1 ? !(v & 2) : 1;
@@ -1159,7 +1162,8 @@ dns_status dns_autotune(dns_ctx* c, int reps, int* variants) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   drop_graphs(c);
-  c->var_py = best[0][1] < best[0][0] ? 1 : 0;
+  c->var_py = 0;
+  for (int v = 1; v < 3; ++v) if (best[0][v] < best[0][c->var_py]) c->var_py = v;
   int z = 0;
   for (int v = 1; v < 6; ++v) if (best[1][v] < best[1][z]) z = v;
   c->var_p3 = z & 1;
@@ -1200,7 +1204,7 @@ dns_status dns_debug_f32_from_f64(const double* x, float* y, long long n, void* 
 }
 
 dns_status dns_set_tiles(dns_ctx* c, int var_py, int var_p3) {
-  if (!c || var_py < 0 || var_py > 1 || var_p3 < 0 || var_p3 > 5) return DNS_ERR_ARG;
+  if (!c || var_py < 0 || var_py > 2 || var_p3 < 0 || var_p3 > 5) return DNS_ERR_ARG;
   if (c->var_py != var_py || c->var_p3 != (var_p3 & 1) || c->p3_bulk != !(var_p3 & 2) ||
       c->p3_rr != ((var_p3 & 4) != 0))
     drop_graphs(c);

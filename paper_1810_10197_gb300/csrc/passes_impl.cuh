@@ -4,6 +4,7 @@
 
 #include "passes.cuh"
 #include "zpass_rr.cuh"
+#include "ypass_tma.cuh"
 
 namespace dns {
 
@@ -65,9 +66,57 @@ static cudaError_t launch_py_v(const PassArgs& a, cudaStream_t s) {
   k_py<T, N, INV, VAR><<<grid, FftPlan<N>::G * TZ, smem, s>>>(a);
   return cudaGetLastError();
 }
+// y-pass variant 2: tensor-map tile copies and register-resident transforms (FP32,
+// ny = 256, Mz even); elsewhere it runs variant 0.  The tensor maps are encoded on the host
+// for every launch (they hold the buffer addresses; a captured graph keeps them by value).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+// FP32 view [planes][rows][2 Mz] of a y-pass buffer, box {16, rows, 1} (8 complex columns of
+// every row of one plane), 64-byte swizzle, zero fill outside
+static cudaError_t plane_map(CUtensorMap* m, const void* p, int Mz, int rows, long long planes) {
+  const EncodeTiledFn enc = encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
+  const cuuint64_t dim[3] = {(cuuint64_t)(2 * Mz), (cuuint64_t)rows, (cuuint64_t)planes};
+  const cuuint64_t stride[2] = {(cuuint64_t)Mz * 8, (cuuint64_t)rows * Mz * 8};
+  const cuuint32_t box[3] = {16, (cuuint32_t)rows, 1};
+  const cuuint32_t estride[3] = {1, 1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(p), dim, stride, box, estride,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+template <bool INV>
+static cudaError_t launch_py_tma(const PassArgs& a, cudaStream_t s) {
+  const int nf = INV ? (a.g.bouss ? 7 : 6) : (a.g.bouss ? 6 : 3);
+  const long long planes = (long long)nf * a.g.nx;
+  CUtensorMap tin, tout;
+  cudaError_t e = plane_map(&tin, a.in, a.g.Mz, INV ? a.g.My : a.g.ny, planes);
+  if (e != cudaSuccess) return e;
+  if ((e = plane_map(&tout, a.out, a.g.Mz, INV ? a.g.ny : a.g.My, planes)) != cudaSuccess) return e;
+  const size_t smem = ytma_smem();
+  if ((e = set_smem(k_py_tma<INV>, smem)) != cudaSuccess) return e;
+  dim3 grid((a.g.Mz + 7) / 8, a.g.nx, nf);
+  k_py_tma<INV><<<grid, 128, smem, s>>>(a, tin, tout);
+  return cudaGetLastError();
+}
 template <typename T, int N, bool INV>
 static cudaError_t launch_py(const PassArgs& a, cudaStream_t s) {
-  return a.var_py ? launch_py_v<T, N, INV, 1>(a, s) : launch_py_v<T, N, INV, 0>(a, s);
+  if constexpr (std::is_same<T, float>::value && N == 256) {
+    if (a.var_py == 2 && ytma_supported(a.g.ny, a.g.Mz)) return launch_py_tma<INV>(a, s);
+  }
+  return a.var_py == 1 ? launch_py_v<T, N, INV, 1>(a, s) : launch_py_v<T, N, INV, 0>(a, s);
 }
 
 template <typename T, int MZ, bool B, int VAR>

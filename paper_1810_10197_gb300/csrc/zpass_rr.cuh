@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(128, 3) k_p3_rr(const PassArgs a) {
   using P = ZrrPlan<N, 128>;
   using RV = typename std::conditional<PAIRED, float2, hf2>::type;
   constexpr int G = P::G, TL = P::TL;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   if (gated_off(a.ctrl, a.gate_k1)) return;
   const Geom& g = a.g;
   const int Mz = g.Mz, Kz = g.Kz;

@@ -33,9 +33,11 @@ def state(shape, L, seed):
     return g, np.concatenate([uh, rh])
 
 
-def gpu_rhs(shape, L, Y, nu, kappa, ri, precision="fp64"):
+def gpu_rhs(shape, L, Y, nu, kappa, ri, precision="fp64", tiles=None):
     from paper_1810_10197_gb300 import Dns
     d = Dns(*shape, nu=nu, precision=precision, lengths=L, boussinesq=(kappa, ri))
+    if tiles is not None:
+        d.set_tiles(*tiles)
     y = to_dev(Y)
     f = torch.empty_like(y)
     d.rhs(y, f)
@@ -57,6 +59,17 @@ def test_boussinesq_rhs(shape, L, precision):
     tol = 1e-13 if precision == "fp64" else 2e-5
     assert rel_max(got[:3], ref[:3]) < tol
     assert rel_max(got[3], ref[3]) < tol
+
+
+@pytest.mark.parametrize("precision", ["fp32_mixed", "fp32"])
+def test_boussinesq_rhs_y_pass_bulk_rows(precision):
+    # y-pass variant 2 at ny = 256: seven inverse planes (u, omega, rho) and six forward ones
+    shape, L = (16, 256, 64), (2 * np.pi, 2 * np.pi, 4 * np.pi)
+    g, Y = state(shape, L, 77)
+    ref = oracle_f(g, 1e-3, 2e-3, 1.0)(Y)
+    got = gpu_rhs(shape, L, Y, 1e-3, 2e-3, 1.0, precision, tiles=(2, 0))
+    assert rel_max(got[:3], ref[:3]) < 2e-5
+    assert rel_max(got[3], ref[3]) < 2e-5
 
 
 def test_boussinesq_hydrostatic_rest_state():

@@ -56,6 +56,21 @@ def test_rhs_random_field(shape, precision):
     assert np.all(got[:, ~g.mask] == 0)
 
 
+@pytest.mark.parametrize("shape", [(32, 256, 64), (16, 256, 48), (24, 256, 32)])
+@pytest.mark.parametrize("precision", ["fp32_mixed", "fp32"])
+def test_rhs_y_pass_variants_at_ny_256(shape, precision):
+    # y-pass variant 2 (bulk row copies, register-resident transforms) applies at ny = 256
+    # with an even number of retained kz planes (Mz = 22, 16 here; the last shape has Mz = 11
+    # and runs variant 0); every variant against the oracle
+    g = sp.Grid(*shape)
+    uh = syn.random_solenoidal_hat(*shape, seed=sum(shape) + 1, k0=4.0)
+    ref = sp.rhs(g, uh, 0.011)
+    for tiles in ((0, 0), (1, 4), (2, 0), (2, 4)):
+        got = run_rhs(shape, uh, 0.011, precision, tiles=tiles)
+        assert rel_max(got, ref) < FP32_TOL, tiles
+        assert np.all(got[:, ~g.mask] == 0)
+
+
 def test_rhs_non_solenoidal_and_noncube_domain():
     shape, L = (16, 16, 32), (2 * np.pi, 2 * np.pi, 4 * np.pi)
     g = sp.Grid(*shape, lengths=L)
@@ -97,9 +112,10 @@ def test_rhs_full_size_256_against_oracle():
         got = run_rhs(shape, uh, nu)
         assert rel_max(got, ref) < FP64_TOL
         # the single-precision forms at this size, with the register-resident z pass (tile
-        # code 4) and with the shared-memory one (code 0)
+        # code 4) and with the shared-memory one (code 0), and the y passes in each variant
+        # (2: bulk row copies)
         for precision in ("fp32_mixed", "fp32"):
-            for tiles in ((0, 4), (1, 0)):
+            for tiles in ((0, 4), (1, 0), (2, 4)):
                 got = run_rhs(shape, uh, nu, precision, tiles=tiles)
                 assert rel_max(got, ref) < FP32_TOL, (precision, tiles)
 
