@@ -71,6 +71,18 @@ def test_rhs_y_pass_variants_at_ny_256(shape, precision):
         assert np.all(got[:, ~g.mask] == 0)
 
 
+@pytest.mark.parametrize("shape,forcing", [((256, 32, 64), None), ((256, 24, 48), (2.5, 0.1))])
+@pytest.mark.parametrize("precision", ["fp32_mixed", "fp32"])
+def test_rhs_nx_256_boxes(shape, forcing, precision):
+    # the benchmark's x-line length on thin boxes, forcing included, against the oracle
+    g = sp.Grid(*shape)
+    uh = syn.random_solenoidal_hat(*shape, seed=sum(shape) + 2, k0=4.0)
+    ref = sp.rhs(g, uh, 0.013, forcing=forcing)
+    got = run_rhs(shape, uh, 0.013, precision, forcing=forcing)
+    assert rel_max(got, ref) < FP32_TOL
+    assert np.all(got[:, ~g.mask] == 0)
+
+
 def test_rhs_non_solenoidal_and_noncube_domain():
     shape, L = (16, 16, 32), (2 * np.pi, 2 * np.pi, 4 * np.pi)
     g = sp.Grid(*shape, lengths=L)
