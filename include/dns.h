@@ -269,29 +269,31 @@ DNS_API dns_status dns_batch_context(dns_batch* batch, int i, dns_ctx** out);
 DNS_API dns_status dns_integrate_batch(dns_batch* batch, int method, const double* t_end, const double* rtol,
                                const double* atol, const double* h0, dns_step_info* info);
 
-/* Autotuner of the FFT tile shapes.  The y passes (columns per CTA) have two compiled tile
- * variants (0: full, 1: half) and, in the single-precision forms at ny = 256 with an even
- * number of retained kz planes, a third (2: the plane's rows moved by bulk copies, the TMA
- * engine, one per row of the tile's 8 columns, into a padded shared-memory stage, line
- * transforms held in registers, rows stored by bulk copies; elsewhere 2 runs variant 0).  The z pass has four codes: bit 0 the tile variant (lines per
- * CTA, full or half), bit 1 set = input rows copied element by element instead of by bulk
- * copies (the TMA engine, completing on a shared-memory barrier; used where a row is a
- * multiple of 16 bytes and the staging fits in shared memory, else element copies anyway).
+/* Autotuner of the FFT tile shapes and kernels.
+ * y argument (var_py): bits 0-1 the y passes' kernel -- 0 full column tile, 1 half tile, 2
+ * (single-precision forms, ny = 256, an even number of retained kz planes; elsewhere it runs
+ * 0) one tensor-map box load and one box store per tile of 8 kz columns of a (field, x) plane
+ * (the TMA engine, a swizzled shared-memory box, line transforms held in registers); bit 2
+ * the x-inverse pass's kernel, set: tensor-map box loads of the stage input and a box store
+ * per output line (single-precision forms, velocity equations, nx = 256, an even number of
+ * retained (ky, kz) columns; elsewhere the shared-memory kernel).  Values 0, 1, 2, 4, 5, 6.
+ * z argument (var_p3): bit 0 the tile variant (lines per CTA, full or half), bit 1 set =
+ * input rows copied element by element instead of by bulk copies (the TMA engine, completing
+ * on a shared-memory barrier; used where a row is a multiple of 16 bytes and the staging fits
+ * in shared memory, else element copies anyway); codes 4 and 5 are the register-resident
+ * FP32 kernel (two real fields per complex line transform held in registers, u x omega
+ * between the transforms without a shared-memory round trip, persistent CTAs fed by bulk
+ * copies that overlap the previous tile's transforms) with fully paired FP32 arithmetic
+ * (FADD2/FMUL2/FFMA2) or paired sums and scalar products; they apply to the single-precision
+ * forms of the velocity equations with nz = 64, 128 or 256 and elsewhere run codes 0 and 1.
  * dns_autotune times `reps` launches of each choice on this context's buffers with CUDA
  * events on its stream, keeps the fastest, and caches the choice per (grid, precision, form)
  * for the process and, if the environment variable DNS_TUNE_CACHE names a file, in that file
- * (read on first use, appended to).  variants (may be NULL) receives {y pass, z pass code}.
- * z pass codes 4 and 5 are the register-resident FP32 kernel (two real fields per complex
- * line transform held in registers, u x omega between the transforms without a
- * shared-memory round trip, persistent CTAs fed by bulk copies that overlap the previous
- * tile's transforms) with fully paired FP32 arithmetic (FADD2/FMUL2/FFMA2) or paired sums and
- * scalar products; it applies to the single-precision forms of the
- * velocity equations with nz = 64, 128 or 256, and where it does not apply codes 4 and 5
- * run codes 0 and 1.
- * dns_create_batch tunes every instance.  dns_set_tiles sets them by hand (var_py 0..2,
- * var_p3 0..5; the default is 2 and 4).  Synchronous.
- * A bulk copy's completion is awaited with a bound (about half a second); a wait that runs
- * out marks the step controller DNS_ERR_TIMEOUT instead of hanging. */
+ * (read on first use, appended to).  variants (may be NULL) receives {y argument, z argument}.
+ * dns_create_batch tunes every instance.  dns_set_tiles sets them by hand (DNS_ERR_ARG for
+ * other values); the default is 6 and 4.  Synchronous.
+ * A bulk or tensor copy's completion is awaited with a bound (about half a second); a wait
+ * that runs out marks the step controller DNS_ERR_TIMEOUT instead of hanging. */
 DNS_API dns_status dns_autotune(dns_ctx* ctx, int reps, int* variants);
 DNS_API dns_status dns_set_tiles(dns_ctx* ctx, int var_py, int var_p3);
 

@@ -121,6 +121,7 @@ struct dns_ctx {
   int var_py = 2, var_p3 = 0;      // tile variants (dns_autotune; y variant 2 runs 0 where it does not apply)
   int p3_bulk = 1;                 // z pass input by bulk copies where possible (dns_autotune)
   int p3_rr = 1;                   // z pass: register-resident FP32 kernel where it applies
+  int x_tma = 1;                   // x-inverse pass: tensor-map FP32 kernel where it applies
   bool stall_pending = false;      // dns_debug_stall: the next host-enqueued z pass stalls
   bool capturing = false;          // building dns_integrate's graph
   size_t bytesA = 0, bytesB = 0;   // sizes of the scratch buffers A and B
@@ -253,6 +254,17 @@ dns_status enqueue_rhs(dns_ctx* c, DnsCtrl* ctrl, int yslot, int kslot, int gate
   a.var_p3 = c->var_p3;
   a.p3_bulk = c->p3_bulk;
   a.p3_rr = c->p3_rr;
+  a.x_tma = c->x_tma;
+  // the buffers the stage-input slot can name (tensor maps of the x-inverse pass)
+  if (ctrl == c->ctrl_rhs) {
+    a.ycand[0] = c->rhs_in;
+  } else if (yslot == SLOT_Y) {
+    a.ycand[0] = c->ystage;
+    a.ycand_f32 = c->precision == DNS_FP32 ? 1 : 0;
+  } else {
+    a.ycand[0] = c->uu[0];
+    a.ycand[1] = c->uu[1];
+  }
   if (c->stall_pending && !c->capturing) {
     a.p3_stall = 16;
     c->stall_pending = false;
@@ -1111,14 +1123,16 @@ dns_status dns_autotune(dns_ctx* c, int reps, int* variants) {
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
       const int z = it->second.second;
-      if (c->var_py != it->second.first || c->var_p3 != (z & 1) || c->p3_bulk != !(z & 2) ||
-          c->p3_rr != ((z & 4) != 0))
+      const int y = it->second.first;
+      if (c->var_py != (y & 3) || c->x_tma != ((y & 4) != 0) || c->var_p3 != (z & 1) ||
+          c->p3_bulk != !(z & 2) || c->p3_rr != ((z & 4) != 0))
         drop_graphs(c);
-      c->var_py = it->second.first;
+      c->var_py = y & 3;
+      c->x_tma = (y & 4) != 0;
       c->var_p3 = z & 1;
       c->p3_bulk = !(z & 2);
       c->p3_rr = (z & 4) != 0;
-      if (variants) { variants[0] = c->var_py; variants[1] = z; }
+      if (variants) { variants[0] = y; variants[1] = z; }
       return DNS_OK;
     }
   }
@@ -1141,16 +1155,24 @@ dns_status dns_autotune(dns_ctx* c, int reps, int* variants) {
   const bool f32 = c->precision == DNS_FP32_MIXED || c->precision == DNS_FP32;
   const bool rr_ok = f32 && p3_rr_applies(a);
   const bool yb_ok = f32 && ytma_supported(c->g.ny, c->g.Mz);
-  float best[2][6] = {{0, 0, 1e30f, 1e30f, 1e30f, 1e30f}, {0, 0, 0, 0, 1e30f, 1e30f}};
-  for (int which = 0; which < 2; ++which) {        // 0: y pass (P2), 1: z pass (P3)
-    for (int v = 0; v < (which == 0 ? (yb_ok ? 3 : 2) : (rr_ok ? 6 : 4)); ++v) {
+  // x-inverse pass, where the tensor-map FP32 kernel applies: k_p1 (0) or that one (1)
+  a.x_tma = 1;
+  a.ycand[0] = c->rhs_in;
+  const bool xt_ok = f32 && x_tma_applies(a);
+  float best[3][6] = {{0, 0, 1e30f, 1e30f, 1e30f, 1e30f}, {0, 0, 0, 0, 1e30f, 1e30f},
+                      {0, 1e30f, 1e30f, 1e30f, 1e30f, 1e30f}};
+  for (int which = 0; which < 3; ++which) {        // 0: y pass (P2), 1: z pass (P3), 2: x pass (P1)
+    const int nv = which == 0 ? (yb_ok ? 3 : 2) : (which == 1 ? (rr_ok ? 6 : 4) : (xt_ok ? 2 : 0));
+    for (int v = 0; v < nv; ++v) {
       a.var_py = which == 0 ? v : 0;
       a.var_p3 = which == 1 ? (v & 1) : 0;
       a.p3_bulk = which == 1 ? !(v & 2) : 1;
       a.p3_rr = which == 1 && (v & 4) != 0;
+      a.x_tma = which == 2 && v == 1;
       if (which == 0) { a.in = c->bufA; a.out = c->bufB; a.tw = c->tw[1]; }
-      else { a.in = c->bufB; a.out = c->bufA; a.tw = c->tw[2]; }
-      const int pass_id = which == 0 ? 2 : 3;
+      else if (which == 1) { a.in = c->bufB; a.out = c->bufA; a.tw = c->tw[2]; }
+      else { a.in = nullptr; a.out = c->bufA; a.tw = c->tw[0]; }   // stage input: the rhs_in slot
+      const int pass_id = which == 0 ? 2 : (which == 1 ? 3 : 1);
       CK(pass(c, pass_id, a), "tune launch");
       CK(cudaEventRecord(e0, c->stream), "event");
       for (int r = 0; r < reps; ++r) CK(pass(c, pass_id, a), "tune launch");
@@ -1164,6 +1186,7 @@ dns_status dns_autotune(dns_ctx* c, int reps, int* variants) {
   drop_graphs(c);
   c->var_py = 0;
   for (int v = 1; v < 3; ++v) if (best[0][v] < best[0][c->var_py]) c->var_py = v;
+  c->x_tma = best[2][1] < best[2][0] ? 1 : 0;
   int z = 0;
   for (int v = 1; v < 6; ++v) if (best[1][v] < best[1][z]) z = v;
   c->var_p3 = z & 1;
@@ -1171,10 +1194,10 @@ dns_status dns_autotune(dns_ctx* c, int reps, int* variants) {
   c->p3_rr = (z & 4) != 0;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[key] = {c->var_py, z};
-    tune_save(key, {c->var_py, z});
+    g_tune[key] = {c->var_py | (c->x_tma ? 4 : 0), z};
+    tune_save(key, {c->var_py | (c->x_tma ? 4 : 0), z});
   }
-  if (variants) { variants[0] = c->var_py; variants[1] = z; }
+  if (variants) { variants[0] = c->var_py | (c->x_tma ? 4 : 0); variants[1] = z; }
   return DNS_OK;
 }
 
@@ -1204,11 +1227,12 @@ dns_status dns_debug_f32_from_f64(const double* x, float* y, long long n, void* 
 }
 
 dns_status dns_set_tiles(dns_ctx* c, int var_py, int var_p3) {
-  if (!c || var_py < 0 || var_py > 2 || var_p3 < 0 || var_p3 > 5) return DNS_ERR_ARG;
-  if (c->var_py != var_py || c->var_p3 != (var_p3 & 1) || c->p3_bulk != !(var_p3 & 2) ||
-      c->p3_rr != ((var_p3 & 4) != 0))
+  if (!c || var_py < 0 || var_py > 6 || (var_py & 3) == 3 || var_p3 < 0 || var_p3 > 5) return DNS_ERR_ARG;
+  if (c->var_py != (var_py & 3) || c->x_tma != ((var_py & 4) != 0) || c->var_p3 != (var_p3 & 1) ||
+      c->p3_bulk != !(var_p3 & 2) || c->p3_rr != ((var_p3 & 4) != 0))
     drop_graphs(c);
-  c->var_py = var_py;
+  c->var_py = var_py & 3;
+  c->x_tma = (var_py & 4) != 0;
   c->var_p3 = var_p3 & 1;
   c->p3_bulk = !(var_p3 & 2);
   c->p3_rr = (var_p3 & 4) != 0;

@@ -43,6 +43,9 @@ struct PassArgs {
   int p3_stall;          // debug: block 0's bulk-copy barrier expects this many extra bytes
   int epi32;             // P5 epilogue (viscous term, forcing) in FP32 (DNS_FP32 form)
   int p3_rr;             // z pass: the register-resident FP32 kernel where it applies (autotuned)
+  int x_tma;             // x-inverse pass: the tensor-map FP32 kernel where it applies (autotuned)
+  const void* ycand[2];  // the buffers the stage-input slot can name (null: unknown), for P1's tensor maps
+  int ycand_f32;         // those buffers hold the FP32 stage-input scratch (DNS_FP32 form)
 };
 
 // The register-resident FP32 z pass (zpass_rr.cuh) handles nz = 64, 128, 256 in the velocity
@@ -58,6 +61,12 @@ inline bool p3_rr_applies(const PassArgs& a) {
 // The FP32 y passes with tensor-map tile copies (ypass_tma.cuh, y-pass variant 2) handle
 // ny = 256 with an even number of retained kz planes (rows of 16-byte multiples).
 __host__ __device__ constexpr bool ytma_supported(int ny, int Mz) { return ny == 256 && Mz % 2 == 0; }
+// The FP32 x-inverse pass with tensor-map tile copies (xpass_tma.cuh) handles nx = 256 in the
+// velocity form with an even number of retained (ky, kz) columns, when the buffers the
+// stage-input slot can name are known.
+inline bool x_tma_applies(const PassArgs& a) {
+  return a.x_tma && !a.g.bouss && a.g.nx == 256 && a.g.MyMz % 2 == 0 && a.ycand[0] != nullptr;
+}
 
 // ---- bulk copies (TMA engine) completing on a CTA-local mbarrier ---------------------------
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }

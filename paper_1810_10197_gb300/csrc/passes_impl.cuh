@@ -5,6 +5,7 @@
 #include "passes.cuh"
 #include "zpass_rr.cuh"
 #include "ypass_tma.cuh"
+#include "xpass_tma.cuh"
 
 namespace dns {
 
@@ -27,9 +28,13 @@ static cudaError_t persistent_grid(K kernel, int threads, size_t smem, long long
   return cudaSuccess;
 }
 
+static cudaError_t launch_p1_tma(const PassArgs& a, cudaStream_t s);
 template <typename T, int N, bool B>
 static cudaError_t launch_p1(const PassArgs& a, cudaStream_t s) {
   using V = v2_t<T>;
+  if constexpr (std::is_same<T, float>::value && N == 256 && !B) {
+    if (x_tma_applies(a)) return launch_p1_tma(a, s);
+  }
   constexpr int TC = p1_cols<T, N>();
   const size_t smem = (size_t)(twiddle_count_xy(N) + 3 * TC * line_ld<V, N>()) * sizeof(V) +
                       (size_t)2 * TC * sizeof(T);
@@ -97,6 +102,37 @@ static cudaError_t plane_map(CUtensorMap* m, const void* p, int Mz, int rows, lo
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
+// x-inverse pass with tensor-map tile copies: grid ceil(MyMz / 8).
+template <bool Y32>
+static cudaError_t launch_p1_tma_t(const PassArgs& a, cudaStream_t s) {
+  const EncodeTiledFn enc = encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
+  const int MyMz = a.g.MyMz, Mx = a.g.Mx;
+  CUtensorMap ty[2], tout;
+  for (int i = 0; i < 2; ++i) {
+    const void* p = a.ycand[i] ? a.ycand[i] : a.ycand[0];
+    const cuuint64_t dim[3] = {(cuuint64_t)(2 * MyMz), (cuuint64_t)Mx, 3};
+    const cuuint64_t stride[2] = {(cuuint64_t)MyMz * (Y32 ? 8 : 16), (cuuint64_t)Mx * MyMz * (Y32 ? 8 : 16)};
+    const cuuint32_t box[3] = {16, (cuuint32_t)Mx, 1};
+    const cuuint32_t estride[3] = {1, 1, 1};
+    if (enc(&ty[i], Y32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<void*>(p), dim,
+            stride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            Y32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  cudaError_t e = plane_map(&tout, a.out, MyMz, a.g.nx, 6);
+  if (e != cudaSuccess) return e;
+  const size_t smem = xtma_p1_smem(Mx, Y32);
+  if ((e = set_smem(k_p1_tma<256, Y32>, smem)) != cudaSuccess) return e;
+  PassArgs b = a;
+  if (!b.ycand[1]) b.ycand[1] = b.ycand[0];
+  k_p1_tma<256, Y32><<<(MyMz + 7) / 8, 128, smem, s>>>(b, ty[0], ty[1], tout);
+  return cudaGetLastError();
+}
+static cudaError_t launch_p1_tma(const PassArgs& a, cudaStream_t s) {
+  return a.ycand_f32 ? launch_p1_tma_t<true>(a, s) : launch_p1_tma_t<false>(a, s);
+}
 template <bool INV>
 static cudaError_t launch_py_tma(const PassArgs& a, cudaStream_t s) {
   const int nf = INV ? (a.g.bouss ? 7 : 6) : (a.g.bouss ? 6 : 3);
@@ -105,7 +141,7 @@ static cudaError_t launch_py_tma(const PassArgs& a, cudaStream_t s) {
   cudaError_t e = plane_map(&tin, a.in, a.g.Mz, INV ? a.g.My : a.g.ny, planes);
   if (e != cudaSuccess) return e;
   if ((e = plane_map(&tout, a.out, a.g.Mz, INV ? a.g.ny : a.g.My, planes)) != cudaSuccess) return e;
-  const size_t smem = ytma_smem();
+  const size_t smem = ytma_smem<INV>();
   if ((e = set_smem(k_py_tma<INV>, smem)) != cudaSuccess) return e;
   dim3 grid((a.g.Mz + 7) / 8, a.g.nx, nf);
   k_py_tma<INV><<<grid, 128, smem, s>>>(a, tin, tout);

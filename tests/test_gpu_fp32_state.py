@@ -103,15 +103,21 @@ def test_error_norm_fp32_arithmetic_matches_fp64_arithmetic():
     assert c.err == pytest.approx(d.err, rel=1e-4)
 
 
+@pytest.mark.parametrize("shape,tiles", [((64, 64, 64), None), ((256, 24, 48), (4, 0)), ((256, 24, 48), (0, 0))])
 @pytest.mark.parametrize("precision", ["fp32_mixed", "fp32"])
-def test_single_precision_adaptive_steps_against_oracle(precision):
+def test_single_precision_adaptive_steps_against_oracle(precision, shape, tiles):
     # ten adaptive attempts; the oracle replays the accepted step sizes from the attempt trace
-    # in FP64, so the difference is the FP32 arithmetic alone (RHS, stage increments)
+    # in FP64, so the difference is the FP32 arithmetic alone (RHS, stage increments).  At
+    # nx = 256 with and without the tensor-map x-inverse kernel (y argument bit 2), whose
+    # stage input alternates between the two state buffers and the stage-input scratch (FP32
+    # in the fp32 form)
     from paper_1810_10197_gb300 import Dns
-    shape, nu, tol = (64, 64, 64), 1e-3, 1e-6
+    nu, tol = 1e-3, 1e-6
     g = sp.Grid(*shape)
     uh = g.dealias(syn.random_solenoidal_hat(*shape, seed=1, k0=4.0))
     d = Dns(*shape, nu=nu, precision=precision)
+    if tiles is not None:
+        d.set_tiles(*tiles)
     d.set_state(to_dev(uh), 0.0)
     d.set_trace(100)
     d.enqueue_attempts(10, "BS5_ADAPTIVE", tol, tol, t_end=1e9, h0=1e-3)

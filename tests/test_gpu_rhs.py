@@ -59,7 +59,7 @@ def test_rhs_random_field(shape, precision):
 @pytest.mark.parametrize("shape", [(32, 256, 64), (16, 256, 48), (24, 256, 32)])
 @pytest.mark.parametrize("precision", ["fp32_mixed", "fp32"])
 def test_rhs_y_pass_variants_at_ny_256(shape, precision):
-    # y-pass variant 2 (bulk row copies, register-resident transforms) applies at ny = 256
+    # y-pass variant 2 (tensor-map tiles, register-resident transforms) applies at ny = 256
     # with an even number of retained kz planes (Mz = 22, 16 here; the last shape has Mz = 11
     # and runs variant 0); every variant against the oracle
     g = sp.Grid(*shape)
@@ -78,9 +78,10 @@ def test_rhs_nx_256_boxes(shape, forcing, precision):
     g = sp.Grid(*shape)
     uh = syn.random_solenoidal_hat(*shape, seed=sum(shape) + 2, k0=4.0)
     ref = sp.rhs(g, uh, 0.013, forcing=forcing)
-    got = run_rhs(shape, uh, 0.013, precision, forcing=forcing)
-    assert rel_max(got, ref) < FP32_TOL
-    assert np.all(got[:, ~g.mask] == 0)
+    for tiles in ((0, 0), (4, 0)):     # k_p1, the tensor-map x-inverse kernel
+        got = run_rhs(shape, uh, 0.013, precision, forcing=forcing, tiles=tiles)
+        assert rel_max(got, ref) < FP32_TOL, tiles
+        assert np.all(got[:, ~g.mask] == 0)
 
 
 def test_rhs_non_solenoidal_and_noncube_domain():
@@ -124,10 +125,10 @@ def test_rhs_full_size_256_against_oracle():
         got = run_rhs(shape, uh, nu)
         assert rel_max(got, ref) < FP64_TOL
         # the single-precision forms at this size, with the register-resident z pass (tile
-        # code 4) and with the shared-memory one (code 0), and the y passes in each variant
-        # (2: bulk row copies)
+        # code 4) and with the shared-memory one (code 0), the y passes in each variant (2:
+        # tensor-map tiles) and the x-inverse pass in each (y argument + 4: tensor-map tiles)
         for precision in ("fp32_mixed", "fp32"):
-            for tiles in ((0, 4), (1, 0), (2, 4)):
+            for tiles in ((0, 4), (1, 0), (2, 4), (6, 4), (4, 0)):
                 got = run_rhs(shape, uh, nu, precision, tiles=tiles)
                 assert rel_max(got, ref) < FP32_TOL, (precision, tiles)
 
