@@ -33,7 +33,11 @@ template <typename T, int N, bool B>
 static cudaError_t launch_p1(const PassArgs& a, cudaStream_t s) {
   using V = v2_t<T>;
   if constexpr (std::is_same<T, float>::value && N == 256 && !B) {
-    if (x_tma_applies(a)) return launch_p1_tma(a, s);
+    if (x_tma_applies(a)) {
+      // a driver without tensor-map encoding (or a view it refuses) runs the shared-memory kernel
+      const cudaError_t e = launch_p1_tma(a, s);
+      if (e != cudaErrorNotSupported) return e;
+    }
   }
   constexpr int TC = p1_cols<T, N>();
   const size_t smem = (size_t)(twiddle_count_xy(N) + 3 * TC * line_ld<V, N>()) * sizeof(V) +
@@ -82,8 +86,10 @@ static EncodeTiledFn encode_tiled() {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
+        q != cudaDriverEntryPointSuccess) {
+      (void)cudaGetLastError();   // not sticky: leave no error for the launch checks that follow
       return nullptr;
+    }
     return reinterpret_cast<EncodeTiledFn>(p);
   }();
   return fn;
@@ -100,7 +106,7 @@ static cudaError_t plane_map(CUtensorMap* m, const void* p, int Mz, int rows, lo
   const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(p), dim, stride, box, estride,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorNotSupported;
 }
 // x-inverse pass with tensor-map tile copies: grid ceil(MyMz / 8).
 template <bool Y32>
@@ -119,7 +125,7 @@ static cudaError_t launch_p1_tma_t(const PassArgs& a, cudaStream_t s) {
             stride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
             Y32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return cudaErrorInvalidValue;
+      return cudaErrorNotSupported;
   }
   cudaError_t e = plane_map(&tout, a.out, MyMz, a.g.nx, 6);
   if (e != cudaSuccess) return e;
@@ -150,7 +156,11 @@ static cudaError_t launch_py_tma(const PassArgs& a, cudaStream_t s) {
 template <typename T, int N, bool INV>
 static cudaError_t launch_py(const PassArgs& a, cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value && N == 256) {
-    if (a.var_py == 2 && ytma_supported(a.g.ny, a.g.Mz)) return launch_py_tma<INV>(a, s);
+    if (a.var_py == 2 && ytma_supported(a.g.ny, a.g.Mz)) {
+      // a driver without tensor-map encoding (or a view it refuses) runs variant 0
+      const cudaError_t e = launch_py_tma<INV>(a, s);
+      if (e != cudaErrorNotSupported) return e;
+    }
   }
   return a.var_py == 1 ? launch_py_v<T, N, INV, 1>(a, s) : launch_py_v<T, N, INV, 0>(a, s);
 }
