@@ -37,7 +37,7 @@ struct PassArgs {
   double kf2;            // forcing band |kappa|^2 <= kf2 (0: no forcing)
   double kappa_d;        // density diffusivity (Boussinesq)
   double ri;             // Richardson number (Boussinesq)
-  int var_py;            // y passes: 0 full tile, 1 half width, 2 tensor-map tiles (FP32, ny = 256), autotuned
+  int var_py;            // y passes: 0 full tile, 1 half width, 2 tensor-map tiles (FP32, ny = 128, 256), autotuned
   int var_p3;            // tile variant of the z pass (0: full, 1: half the lines), autotuned
   int p3_bulk;           // z pass: stage input rows with bulk copies (rows a multiple of 16 B)
   int p3_stall;          // debug: block 0's bulk-copy barrier expects this many extra bytes
@@ -59,8 +59,8 @@ inline bool p3_rr_applies(const PassArgs& a) {
 }
 
 // The FP32 y passes with tensor-map tile copies (ypass_tma.cuh, y-pass variant 2) handle
-// ny = 256 with an even number of retained kz planes (rows of 16-byte multiples).
-__host__ __device__ constexpr bool ytma_supported(int ny, int Mz) { return ny == 256 && Mz % 2 == 0; }
+// ny = 128 and 256 with an even number of retained kz planes (rows of 16-byte multiples).
+__host__ __device__ constexpr bool ytma_supported(int ny, int Mz) { return (ny == 256 || ny == 128) && Mz % 2 == 0; }
 // The FP32 x-inverse pass with tensor-map tile copies (xpass_tma.cuh) handles nx = 256 in the
 // velocity form with an even number of retained (ky, kz) columns, when the buffers the
 // stage-input slot can name are known.

@@ -94,18 +94,18 @@ static EncodeTiledFn encode_tiled() {
   }();
   return fn;
 }
-// FP32 view [planes][rows][2 Mz] of a y-pass buffer, box {16, rows, 1} (8 complex columns of
-// every row of one plane), 64-byte swizzle, zero fill outside
-static cudaError_t plane_map(CUtensorMap* m, const void* p, int Mz, int rows, long long planes) {
+// FP32 view [planes][rows][2 Mz] of a pass buffer, box {2 cols, rows, 1} (cols complex columns
+// of every row of one plane: 8 or 16, with the 64- or 128-byte swizzle), zero fill outside
+static cudaError_t plane_map(CUtensorMap* m, const void* p, int Mz, int rows, long long planes, int cols = 8) {
   const EncodeTiledFn enc = encode_tiled();
   if (!enc) return cudaErrorNotSupported;
   const cuuint64_t dim[3] = {(cuuint64_t)(2 * Mz), (cuuint64_t)rows, (cuuint64_t)planes};
   const cuuint64_t stride[2] = {(cuuint64_t)Mz * 8, (cuuint64_t)rows * Mz * 8};
-  const cuuint32_t box[3] = {16, (cuuint32_t)rows, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)(2 * cols), (cuuint32_t)rows, 1};
   const cuuint32_t estride[3] = {1, 1, 1};
   const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(p), dim, stride, box, estride,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, cols == 16 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorNotSupported;
 }
 // x-inverse pass with tensor-map tile copies: grid ceil(MyMz / 8).
@@ -139,26 +139,27 @@ static cudaError_t launch_p1_tma_t(const PassArgs& a, cudaStream_t s) {
 static cudaError_t launch_p1_tma(const PassArgs& a, cudaStream_t s) {
   return a.ycand_f32 ? launch_p1_tma_t<true>(a, s) : launch_p1_tma_t<false>(a, s);
 }
-template <bool INV>
+template <int N, bool INV>
 static cudaError_t launch_py_tma(const PassArgs& a, cudaStream_t s) {
+  constexpr int TZ = YtmaTile<N>::TZ;
   const int nf = INV ? (a.g.bouss ? 7 : 6) : (a.g.bouss ? 6 : 3);
   const long long planes = (long long)nf * a.g.nx;
   CUtensorMap tin, tout;
-  cudaError_t e = plane_map(&tin, a.in, a.g.Mz, INV ? a.g.My : a.g.ny, planes);
+  cudaError_t e = plane_map(&tin, a.in, a.g.Mz, INV ? a.g.My : a.g.ny, planes, TZ);
   if (e != cudaSuccess) return e;
-  if ((e = plane_map(&tout, a.out, a.g.Mz, INV ? a.g.ny : a.g.My, planes)) != cudaSuccess) return e;
-  const size_t smem = ytma_smem<INV>();
-  if ((e = set_smem(k_py_tma<INV>, smem)) != cudaSuccess) return e;
-  dim3 grid((a.g.Mz + 7) / 8, a.g.nx, nf);
-  k_py_tma<INV><<<grid, 128, smem, s>>>(a, tin, tout);
+  if ((e = plane_map(&tout, a.out, a.g.Mz, INV ? a.g.ny : a.g.My, planes, TZ)) != cudaSuccess) return e;
+  const size_t smem = ytma_smem<N, INV>();
+  if ((e = set_smem(k_py_tma<N, INV>, smem)) != cudaSuccess) return e;
+  dim3 grid((a.g.Mz + TZ - 1) / TZ, a.g.nx, nf);
+  k_py_tma<N, INV><<<grid, 128, smem, s>>>(a, tin, tout);
   return cudaGetLastError();
 }
 template <typename T, int N, bool INV>
 static cudaError_t launch_py(const PassArgs& a, cudaStream_t s) {
-  if constexpr (std::is_same<T, float>::value && N == 256) {
+  if constexpr (std::is_same<T, float>::value && (N == 256 || N == 128)) {
     if (a.var_py == 2 && ytma_supported(a.g.ny, a.g.Mz)) {
       // a driver without tensor-map encoding (or a view it refuses) runs variant 0
-      const cudaError_t e = launch_py_tma<INV>(a, s);
+      const cudaError_t e = launch_py_tma<N, INV>(a, s);
       if (e != cudaErrorNotSupported) return e;
     }
   }

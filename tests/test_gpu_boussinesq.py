@@ -61,10 +61,12 @@ def test_boussinesq_rhs(shape, L, precision):
     assert rel_max(got[3], ref[3]) < tol
 
 
+@pytest.mark.parametrize("shape", [(16, 256, 64), (16, 128, 64)])
 @pytest.mark.parametrize("precision", ["fp32_mixed", "fp32"])
-def test_boussinesq_rhs_y_pass_bulk_rows(precision):
-    # y-pass variant 2 at ny = 256: seven inverse planes (u, omega, rho) and six forward ones
-    shape, L = (16, 256, 64), (2 * np.pi, 2 * np.pi, 4 * np.pi)
+def test_boussinesq_rhs_y_pass_tensor_map(shape, precision):
+    # y-pass variant 2 at ny = 256 and 128: seven inverse planes (u, omega, rho) and six
+    # forward ones
+    L = (2 * np.pi, 2 * np.pi, 4 * np.pi)
     g, Y = state(shape, L, 77)
     ref = oracle_f(g, 1e-3, 2e-3, 1.0)(Y)
     got = gpu_rhs(shape, L, Y, 1e-3, 2e-3, 1.0, precision, tiles=(2, 0))

@@ -56,12 +56,13 @@ def test_rhs_random_field(shape, precision):
     assert np.all(got[:, ~g.mask] == 0)
 
 
-@pytest.mark.parametrize("shape", [(32, 256, 64), (16, 256, 48), (24, 256, 32)])
+@pytest.mark.parametrize("shape", [(32, 256, 64), (16, 256, 48), (24, 256, 32),
+                                   (32, 128, 64), (24, 128, 48), (16, 128, 32), (32, 128, 256)])
 @pytest.mark.parametrize("precision", ["fp32_mixed", "fp32"])
-def test_rhs_y_pass_variants_at_ny_256(shape, precision):
+def test_rhs_y_pass_variants_at_ny_256_and_128(shape, precision):
     # y-pass variant 2 (tensor-map tiles, register-resident transforms) applies at ny = 256
-    # with an even number of retained kz planes (Mz = 22, 16 here; the last shape has Mz = 11
-    # and runs variant 0); every variant against the oracle
+    # and 128 with an even number of retained kz planes (Mz = 22, 16, 86; the shapes with
+    # nz = 32 have Mz = 11 and run variant 0); every variant against the oracle
     g = sp.Grid(*shape)
     uh = syn.random_solenoidal_hat(*shape, seed=sum(shape) + 1, k0=4.0)
     ref = sp.rhs(g, uh, 0.011)
