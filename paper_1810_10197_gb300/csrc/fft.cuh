@@ -187,6 +187,98 @@ template <int SIGN, typename V> struct Dft<16, SIGN, V> {
   }
 };
 
+// FP64 16- and 8-point DFTs with the twiddles of the second radix-4 layer factored for
+// fused multiply-adds (the FP64 forms are bound by the FP64 pipe's issue rate, so every
+// instruction counts): with W = exp(SIGN i pi / 8) = c (1 + SIGN i t), t = tan(pi / 8),
+//   W^3 = SIGN i c (1 - SIGN i t),  W^9 = -c (1 + SIGN i t),  W^2 = r (1 + SIGN i),
+//   W^6 = r (-1 + SIGN i),  r = 1 / sqrt(2),
+// the common scale (c or r) of a column's twiddled terms is applied once, inside the fused
+// multiply-adds of its output butterflies: 144 instead of 160 FP64 instructions per 16-point
+// DFT, 52 instead of 56 per 8-point DFT.  Same values as the generic forms up to rounding.
+namespace fma_dft {
+__device__ __forceinline__ double2 rot(double2 a, int S) { return make_double2(-S * a.y, S * a.x); }   // S i a
+// (X, Y) outputs of a radix-4 column whose odd terms share the scale k: s02 + k S, s02 - k S,
+// d02 + k S i D, d02 - k S i D with S = p + q, D = p - q
+template <int SIGN>
+__device__ __forceinline__ void out4(double2 s02, double2 d02, double2 p, double2 q, double k, double2* X0,
+                                     double2* X1, double2* X2, double2* X3) {
+  const double2 S = make_double2(p.x + q.x, p.y + q.y), D = make_double2(p.x - q.x, p.y - q.y);
+  *X0 = make_double2(fma(k, S.x, s02.x), fma(k, S.y, s02.y));
+  *X2 = make_double2(fma(-k, S.x, s02.x), fma(-k, S.y, s02.y));
+  // S i D = (-SIGN D.y, SIGN D.x)
+  *X1 = make_double2(fma(-SIGN * k, D.y, d02.x), fma(SIGN * k, D.x, d02.y));
+  *X3 = make_double2(fma(SIGN * k, D.y, d02.x), fma(-SIGN * k, D.x, d02.y));
+}
+}  // namespace fma_dft
+
+template <int SIGN> struct Dft<16, SIGN, double2> {
+  static __device__ __forceinline__ void run(double2* v) {
+    using namespace fma_dft;
+    constexpr double c = 0.92387953251128675613, t = 0.41421356237309504880, r = 0.70710678118654752440;
+    constexpr double St = SIGN * t;
+    double2 y[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+      y[n2][0] = v[n2]; y[n2][1] = v[4 + n2]; y[n2][2] = v[8 + n2]; y[n2][3] = v[12 + n2];
+      Dft<4, SIGN, double2>::run(y[n2]);
+    }
+    double2 z[4];
+    // k1 = 0: no twiddles
+    z[0] = y[0][0]; z[1] = y[1][0]; z[2] = y[2][0]; z[3] = y[3][0];
+    Dft<4, SIGN, double2>::run(z);
+    v[0] = z[0]; v[4] = z[1]; v[8] = z[2]; v[12] = z[3];
+    {  // k1 = 1: W^1 = c (1 + S i t), W^2 = r (1 + S i), W^3 = S i c (1 - S i t)
+      const double2 a1 = y[1][1], a2 = y[2][1], a3 = y[3][1], z0 = y[0][1];
+      const double2 p = make_double2(fma(-St, a1.y, a1.x), fma(St, a1.x, a1.y));
+      const double2 q = rot(make_double2(fma(St, a3.y, a3.x), fma(-St, a3.x, a3.y)), SIGN);
+      const double2 A = make_double2(a2.x - SIGN * a2.y, a2.y + SIGN * a2.x);
+      const double2 s02 = make_double2(fma(r, A.x, z0.x), fma(r, A.y, z0.y));
+      const double2 d02 = make_double2(fma(-r, A.x, z0.x), fma(-r, A.y, z0.y));
+      out4<SIGN>(s02, d02, p, q, c, &v[1], &v[5], &v[9], &v[13]);
+    }
+    {  // k1 = 2: W^2 = r (1 + S i), W^4 = S i, W^6 = r (-1 + S i)
+      const double2 a1 = y[1][2], a2 = y[2][2], a3 = y[3][2], z0 = y[0][2];
+      const double2 p = make_double2(a1.x - SIGN * a1.y, a1.y + SIGN * a1.x);
+      const double2 q = make_double2(-a3.x - SIGN * a3.y, SIGN * a3.x - a3.y);
+      const double2 z2 = rot(a2, SIGN);
+      const double2 s02 = make_double2(z0.x + z2.x, z0.y + z2.y), d02 = make_double2(z0.x - z2.x, z0.y - z2.y);
+      out4<SIGN>(s02, d02, p, q, r, &v[2], &v[6], &v[10], &v[14]);
+    }
+    {  // k1 = 3: W^3 = S i c (1 - S i t), W^6 = r (-1 + S i), W^9 = -c (1 + S i t)
+      const double2 a1 = y[1][3], a2 = y[2][3], a3 = y[3][3], z0 = y[0][3];
+      const double2 p = rot(make_double2(fma(St, a1.y, a1.x), fma(-St, a1.x, a1.y)), SIGN);
+      const double2 q = make_double2(fma(St, a3.y, -a3.x), fma(-St, a3.x, -a3.y));
+      const double2 A = make_double2(-a2.x - SIGN * a2.y, SIGN * a2.x - a2.y);
+      const double2 s02 = make_double2(fma(r, A.x, z0.x), fma(r, A.y, z0.y));
+      const double2 d02 = make_double2(fma(-r, A.x, z0.x), fma(-r, A.y, z0.y));
+      out4<SIGN>(s02, d02, p, q, c, &v[3], &v[7], &v[11], &v[15]);
+    }
+  }
+};
+
+template <int SIGN> struct Dft<8, SIGN, double2> {
+  // 8 = 4 x 2 (n = 2 n1 + n2, k = k1 + 4 k2): W8^1 = r (1 + S i), W8^3 = r (-1 + S i)
+  static __device__ __forceinline__ void run(double2* v) {
+    using namespace fma_dft;
+    constexpr double r = 0.70710678118654752440;
+    double2 e[4] = {v[0], v[2], v[4], v[6]};
+    double2 o[4] = {v[1], v[3], v[5], v[7]};
+    Dft<4, SIGN, double2>::run(e);
+    Dft<4, SIGN, double2>::run(o);
+    const double2 A1 = make_double2(o[1].x - SIGN * o[1].y, o[1].y + SIGN * o[1].x);
+    const double2 A3 = make_double2(-o[3].x - SIGN * o[3].y, SIGN * o[3].x - o[3].y);
+    const double2 o2 = rot(o[2], SIGN);
+    v[0] = make_double2(e[0].x + o[0].x, e[0].y + o[0].y);
+    v[4] = make_double2(e[0].x - o[0].x, e[0].y - o[0].y);
+    v[1] = make_double2(fma(r, A1.x, e[1].x), fma(r, A1.y, e[1].y));
+    v[5] = make_double2(fma(-r, A1.x, e[1].x), fma(-r, A1.y, e[1].y));
+    v[2] = make_double2(e[2].x + o2.x, e[2].y + o2.y);
+    v[6] = make_double2(e[2].x - o2.x, e[2].y - o2.y);
+    v[3] = make_double2(fma(r, A3.x, e[3].x), fma(r, A3.y, e[3].y));
+    v[7] = make_double2(fma(-r, A3.x, e[3].x), fma(-r, A3.y, e[3].y));
+  }
+};
+
 // ---- one Stockham stage and the whole line transform ------------------------------------
 
 // Linear padded indexing.  A stage reads j + r B (j < B) and writes q + r NS with
