@@ -279,6 +279,65 @@ template <int SIGN> struct Dft<8, SIGN, double2> {
   }
 };
 
+// The same factoring for FP32 values as paired instructions (FFMA2 / FADD2): the register-
+// resident transforms are bound by instruction issue.
+namespace fma_dft {
+__device__ __forceinline__ float2 swp(float2 a) { return make_float2(a.y, a.x); }
+template <int SIGN>
+__device__ __forceinline__ void out4(float2 s02, float2 d02, float2 p, float2 q, float k, float2* X0, float2* X1,
+                                     float2* X2, float2* X3) {
+  const float2 S = __fadd2_rn(p, q), D = __fadd2_rn(p, make_float2(-q.x, -q.y));
+  *X0 = __ffma2_rn(make_float2(k, k), S, s02);
+  *X2 = __ffma2_rn(make_float2(-k, -k), S, s02);
+  const float2 Ds = swp(D);   // S i D = (-SIGN D.y, SIGN D.x)
+  *X1 = __ffma2_rn(make_float2(-SIGN * k, SIGN * k), Ds, d02);
+  *X3 = __ffma2_rn(make_float2(SIGN * k, -SIGN * k), Ds, d02);
+}
+}  // namespace fma_dft
+
+template <int SIGN> struct Dft<16, SIGN, float2> {
+  static __device__ __forceinline__ void run(float2* v) {
+    using namespace fma_dft;
+    constexpr float c = 0.92387953251128675613f, t = 0.41421356237309504880f, r = 0.70710678118654752440f;
+    constexpr float St = SIGN * t;
+    float2 y[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+      y[n2][0] = v[n2]; y[n2][1] = v[4 + n2]; y[n2][2] = v[8 + n2]; y[n2][3] = v[12 + n2];
+      Dft<4, SIGN, float2>::run(y[n2]);
+    }
+    float2 z[4] = {y[0][0], y[1][0], y[2][0], y[3][0]};
+    Dft<4, SIGN, float2>::run(z);
+    v[0] = z[0]; v[4] = z[1]; v[8] = z[2]; v[12] = z[3];
+    {  // k1 = 1: W^1 = c (1 + S i t), W^2 = r (1 + S i), W^3 = S i c (1 - S i t)
+      const float2 a1 = y[1][1], a2 = y[2][1], a3 = y[3][1], z0 = y[0][1];
+      const float2 p = __ffma2_rn(make_float2(-St, St), swp(a1), a1);
+      const float2 R = __ffma2_rn(make_float2(St, -St), swp(a3), a3);
+      const float2 q = make_float2(-SIGN * R.y, SIGN * R.x);
+      const float2 A = __ffma2_rn(make_float2(-(float)SIGN, (float)SIGN), swp(a2), a2);
+      out4<SIGN>(__ffma2_rn(make_float2(r, r), A, z0), __ffma2_rn(make_float2(-r, -r), A, z0), p, q, c,
+                 &v[1], &v[5], &v[9], &v[13]);
+    }
+    {  // k1 = 2: W^2 = r (1 + S i), W^4 = S i, W^6 = r (-1 + S i)
+      const float2 a1 = y[1][2], a2 = y[2][2], a3 = y[3][2], z0 = y[0][2];
+      const float2 p = __ffma2_rn(make_float2(-(float)SIGN, (float)SIGN), swp(a1), a1);
+      const float2 q = __ffma2_rn(make_float2(-(float)SIGN, (float)SIGN), swp(a3), make_float2(-a3.x, -a3.y));
+      const float2 z2 = make_float2(-SIGN * a2.y, SIGN * a2.x);
+      out4<SIGN>(__fadd2_rn(z0, z2), __fadd2_rn(z0, make_float2(-z2.x, -z2.y)), p, q, r, &v[2], &v[6], &v[10],
+                 &v[14]);
+    }
+    {  // k1 = 3: W^3 = S i c (1 - S i t), W^6 = r (-1 + S i), W^9 = -c (1 + S i t)
+      const float2 a1 = y[1][3], a2 = y[2][3], a3 = y[3][3], z0 = y[0][3];
+      const float2 R = __ffma2_rn(make_float2(St, -St), swp(a1), a1);
+      const float2 p = make_float2(-SIGN * R.y, SIGN * R.x);
+      const float2 q = __ffma2_rn(make_float2(St, -St), swp(a3), make_float2(-a3.x, -a3.y));
+      const float2 A = __ffma2_rn(make_float2(-(float)SIGN, (float)SIGN), swp(a2), make_float2(-a2.x, -a2.y));
+      out4<SIGN>(__ffma2_rn(make_float2(r, r), A, z0), __ffma2_rn(make_float2(-r, -r), A, z0), p, q, c,
+                 &v[3], &v[7], &v[11], &v[15]);
+    }
+  }
+};
+
 // ---- one Stockham stage and the whole line transform ------------------------------------
 
 // Linear padded indexing.  A stage reads j + r B (j < B) and writes q + r NS with
