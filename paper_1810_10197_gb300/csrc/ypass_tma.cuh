@@ -8,12 +8,11 @@
 // row width (the 16-byte chunks of a row permuted by bits 7-8 or 7-9 of its address) so that
 // the rows a half-warp reads in one column fall on distinct bank groups; the copy completes
 // on an mbarrier.  A group of G = ny / 16 threads owns one column: thread t takes the points
-// y = t + G r (r = 0..15) into registers
-// (the band between the retained ky of an inverse transform is zero), runs the 16 x 16
-// transform of the register-resident z pass (one exchange through a padded per-column
-// buffer; in the forward pass it shares the box's shared memory), writes the points it then
-// holds (t + G m) into the box, and one tensor-map box store copies the tile to the output
-// plane.  Columns past Mz are zero-filled by the load
+// y = t + G r (r = 0..15) into registers (the band between the retained ky of an inverse
+// transform is zero), runs the 16 x G transform of the register-resident z pass (one
+// exchange through a padded per-column buffer; in the forward pass it shares the box's
+// shared memory), writes the points it then holds (t + G m) into the box, and one tensor-map
+// box store copies the tile to the output plane.  Columns past Mz are zero-filled by the load
 // and skipped by the store.  Global loads and stores leave the LSU path: the element-wise
 // copies and the shared-memory Stockham stages of k_py keep the L1TEX unit about 80% busy at
 // 256^3.
